@@ -1,0 +1,175 @@
+"""Pins of the oracle's LNV energy, gradient and CG (Sec. 2.3.2, Eq. 8).
+
+Each pin uses something other than the oracle itself: finite
+differences, a dense eigensolver (the exact-diagonalisation density
+matrix of Sec. 2.3.1, Eqs. 6-7, at the Gamma point), dense matrix
+algebra, or inequalities the method guarantees.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle
+from oracle import lnv as OL
+from synth import diamond_si_positions, sk_blocks, config_seed
+
+MU = -2.0
+
+
+def _problem(n=2, sigma=0.05, seed=config_seed(0), R_L=8.0, mu=MU):
+    pos, cell = diamond_si_positions(n, sigma, seed)
+    m = OL.System(pos, cell)
+    pH = m.pattern(6.6)
+    H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
+    Hb, Sb = oracle.Bsr(pH, 4, H), oracle.Bsr(pH, 4, S)
+    return m, Hb, Sb, OL.Lnv(m, Sb, Hb, R_L, mu)
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    m, H, S, lnv = _problem()
+    L0 = OL.onsite_inverse_half(S, lnv.pat_L)
+    L3, _ = OL.minimise(lnv, L0, 3)
+    return m, H, S, lnv, L3
+
+
+def test_energy_matches_dense_mcweeny(cfg0):
+    m, H, S, lnv, L = cfg0
+    Ld, Sd, Hd = L.dense(), S.dense(), H.dense()
+    K = 3 * Ld @ Sd @ Ld - 2 * Ld @ Sd @ Ld @ Sd @ Ld
+    om, ne = lnv.energy(L)
+    assert np.isclose(om, 2 * np.trace(K @ (Hd - MU * Sd)), rtol=1e-12)
+    assert np.isclose(ne, 2 * np.trace(K @ Sd), rtol=1e-12)
+
+
+def test_gradient_central_differences(cfg0):
+    m, H, S, lnv, L = cfg0
+    G = lnv.gradient(L)
+    rng = np.random.default_rng(2002)
+    gmax = np.abs(G.val).max()
+    # h balances the O(h^2) truncation error against rounding of Omega
+    # (|Omega| ~ 600 eV, so about 1e-13 / h); at h = 1e-4 both are < 1e-7.
+    h = 1e-4
+    for flat in rng.choice(L.val.size, size=24, replace=False):
+        Lp, Lm = L.copy(), L.copy()
+        Lp.val.flat[flat] += h
+        Lm.val.flat[flat] -= h
+        fd = (lnv.energy(Lp)[0] - lnv.energy(Lm)[0]) / (2 * h)
+        assert abs(fd - G.val.flat[flat]) <= 1e-7 * gmax
+
+
+def test_gradient_is_symmetric_at_symmetric_L(cfg0):
+    m, H, S, lnv, L = cfg0
+    G = lnv.gradient(L)
+    Gd = G.dense()
+    assert np.abs(Gd - Gd.T).max() <= 1e-10 * np.abs(Gd).max()
+
+
+def test_cubic_equals_direct_energy(cfg0):
+    m, H, S, lnv, L = cfg0
+    rng = np.random.default_rng(7)
+    D = oracle.Bsr(L.pat, 4, rng.standard_normal(L.val.shape))
+    D = 0.5 * (D + oracle.transpose(D, L.pat))
+    G = lnv.gradient(L)
+    c1, c2, c3 = lnv.cubic(L, D, G)
+    om0, _ = lnv.energy(L)
+    for a in (1e-3, 1e-2, 5e-2):
+        om, _ = lnv.energy(L + a * D)
+        pred = c1 * a + c2 * a * a + c3 * a ** 3
+        assert abs((om - om0) - pred) <= 1e-9 * max(1.0, abs(om0))
+
+
+def test_electron_count_is_minus_domega_dmu(cfg0):
+    m, H, S, lnv, L = cfg0
+    h = 1e-5
+    op = OL.Lnv(m, S, H, 8.0, MU + h).energy(L)[0]
+    omn = OL.Lnv(m, S, H, 8.0, MU - h).energy(L)[0]
+    _, ne = lnv.energy(L)
+    assert abs(-(op - omn) / (2 * h) - ne) < 1e-7 * ne
+
+
+def test_domega_dh_is_twice_k(cfg0):
+    """Omega is linear in H: dOmega/dH_ab = 2 K_ba with K = 3LSL - 2LSLSL."""
+    m, H, S, lnv, L = cfg0
+    Ld, Sd = L.dense(), S.dense()
+    K = 3 * Ld @ Sd @ Ld - 2 * Ld @ Sd @ Ld @ Sd @ Ld
+    rng = np.random.default_rng(3)
+    om0, _ = lnv.energy(L)
+    for flat in rng.choice(H.val.size, size=6, replace=False):
+        Hp = H.copy()
+        Hp.val.flat[flat] += 1e-3
+        om1, _ = OL.Lnv(m, S, Hp, 8.0, MU).energy(L)
+        p, r, c = np.unravel_index(flat, H.val.shape)
+        i, j = H.pat.rows()[p], H.pat.col[p]
+        assert np.isclose((om1 - om0) / 1e-3, 2 * K[4 * j + c, 4 * i + r], rtol=1e-6, atol=1e-9)
+
+
+def test_cg_monotone_and_exact_line_prediction():
+    m, H, S, lnv = _problem()
+    L0 = OL.onsite_inverse_half(S, lnv.pat_L)
+    L, hist = OL.minimise(lnv, L0, 20)
+    om = [h["omega"] for h in hist]
+    assert all(b <= a for a, b in zip(om, om[1:]))
+    for k in range(len(hist) - 1):
+        assert abs(hist[k]["omega_next"] - hist[k + 1]["omega"]) <= 1e-9 * abs(om[k])
+        assert hist[k]["alpha"] > 0
+
+
+@pytest.fixture(scope="module")
+def full_range():
+    """64 atoms, L range 12 A (beyond the largest minimum-image distance, 9.4 A)."""
+    m, H, S, lnv = _problem(R_L=12.0)
+    assert np.all(np.diff(lnv.pat_L.ptr) == m.n)
+    L0 = OL.onsite_inverse_half(S, lnv.pat_L)
+    L, hist = OL.minimise(lnv, L0, 120)
+    w, C = sl.eigh((H - MU * S).dense(), S.dense())
+    return m, H, S, lnv, L, hist, w, C
+
+
+def test_full_range_reaches_diagonalisation_energy(full_range):
+    m, H, S, lnv, L, hist, w, C = full_range
+    occ = w < 0.0
+    assert w[occ].max() < -0.3 and w[~occ].min() > 0.3        # mu in a gap
+    om_exact = 2.0 * np.sum(w[occ])
+    om, ne = lnv.energy(L)
+    assert abs(om - om_exact) <= 1e-10 * abs(om_exact)
+    assert abs(ne - 2 * occ.sum()) < 1e-8
+
+
+def test_full_range_density_matrix_and_idempotency(full_range):
+    m, H, S, lnv, L, hist, w, C = full_range
+    occ = w < 0.0
+    K_exact = C[:, occ] @ C[:, occ].T
+    Ld, Sd = L.dense(), S.dense()
+    # Omega is stationary at the minimum, so L converges only about as the
+    # square root of the energy error; 120 steps bring it below 1e-7.
+    assert np.abs(Ld - K_exact).max() < 1e-6
+    assert np.abs(Ld @ Sd @ Ld - Ld).max() < 1e-6                # LSL = L
+    ev = np.sort(np.linalg.eigvals(Ld @ Sd).real)
+    assert np.all(np.minimum(np.abs(ev), np.abs(ev - 1)) < 1e-6)  # eigenvalues of LS in {0, 1}
+    assert np.isclose(2 * np.trace(Ld @ Sd), 2 * occ.sum(), atol=1e-6)
+
+
+def test_truncated_energy_above_exact_and_improves_with_range():
+    """Variational: a shorter L range gives a higher minimum (Sec. 2.3.2:
+    the range of L sets the accuracy)."""
+    res = []
+    for R_L in (2.5, 4.0, 6.0):
+        m, H, S, lnv = _problem(R_L=R_L)
+        L0 = OL.onsite_inverse_half(S, lnv.pat_L)
+        L, hist = OL.minimise(lnv, L0, 60, tol_ha_per_atom=1e-11)
+        res.append(hist[-1]["omega_next"])
+    w = sl.eigh((H - MU * S).dense(), S.dense(), eigvals_only=True)
+    om_exact = 2.0 * np.sum(w[w < 0])
+    assert res[0] > res[1] > res[2] > om_exact
+
+
+def test_line_minimum_cases():
+    # pure quadratic: a = -c1 / (2 c2)
+    assert np.isclose(OL.line_minimum(-2.0, 4.0, 0.0), 0.25)
+    # cubic with a local minimum: check p'(a) = 0 and p''(a) > 0
+    c1, c2, c3 = -1.0, 0.5, -0.01
+    a = OL.line_minimum(c1, c2, c3)
+    assert abs(3 * c3 * a * a + 2 * c2 * a + c1) < 1e-12 and 6 * c3 * a + 2 * c2 > 0
+    # no local minimum (monotone decreasing cubic)
+    assert OL.line_minimum(-1.0, -1.0, -1.0) is None
