@@ -1,0 +1,211 @@
+/*
+ * lsq.h -- C ABI of the GB300 linear-scaling density-matrix library.
+ *
+ * The library implements, on one GPU, the hot path of the O(N) density-
+ * matrix method of the CONQUEST paper (arXiv 2002.07704, Sec. 2.3.2,
+ * "Density matrix: linear scaling"):
+ *   - range patterns of atom-pair matrices: element (i alpha, j beta) is
+ *     kept iff the inter-atomic distance R_ij does not exceed the range;
+ *   - the truncated atom-block product C = A.B restricted to C's range;
+ *   - the LNV grand potential Omega = 2 Tr[(3LSL - 2LSLSL)(H - mu S)]
+ *     (McWeeny form of K, Eq. 8; E_band = 2 Tr[K H]), its gradient with
+ *     respect to L, and its conjugate-gradient minimisation.
+ *
+ * Conventions (every entry point):
+ *   - Return value: LSQ_OK (0) or an LSQ_ERR_* code; lsq_last_error()
+ *     gives a message (thread-local).  On error no output is valid.
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or from
+ *     PyTorch); they are borrowed for the duration of the call and never
+ *     freed by the library.  Host pointers are named *_host or are
+ *     scalars/structs.
+ *   - Block storage ("BSR"): a matrix on range pattern r holds
+ *     nnzb(r) blocks of b x b values, row-major inside a block, blocks in
+ *     the pattern's order (rows ascending, columns ascending in a row).
+ *     Blocks hold float64 (LSQ_F64) or float32 (LSQ_F32) values.
+ *   - stream is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is enqueued asynchronously unless the function returns
+ *     host scalars, in which case it synchronises the stream.
+ *   - Positions are in Angstrom in an orthorhombic periodic cell
+ *     [0, Lx) x [0, Ly) x [0, Lz); energies in eV.
+ */
+#ifndef LSQ_H
+#define LSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------- */
+#define LSQ_OK                 0
+#define LSQ_ERR_INVALID_ARG    1   /* bad argument (null, size, range id, dtype) */
+#define LSQ_ERR_PATTERN        2   /* a pattern does not fit the operation */
+#define LSQ_ERR_OOM            3   /* device allocation failed */
+#define LSQ_ERR_CUDA           4   /* a CUDA runtime call or kernel failed */
+#define LSQ_ERR_UNSTABLE       5   /* LNV: no local minimum along the line */
+#define LSQ_ERR_NOT_CONVERGED  6   /* LNV: iteration limit reached (L holds the last iterate) */
+#define LSQ_ERR_UNSUPPORTED    7   /* size beyond a documented kernel limit */
+
+/* ---- precisions of block products ----------------------------------- */
+#define LSQ_F64    0   /* float64 storage, FP64 FMA */
+#define LSQ_F32    1   /* float32 storage, FP32 FMA */
+
+typedef struct lsq_geom_s *lsq_geom;
+typedef struct lsq_lnv_s *lsq_lnv;
+
+/* Copies the message of the last error on this thread into buf (always
+ * NUL-terminated when len > 0).  Returns the code of that error. */
+int lsq_last_error(char *buf, size_t len);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int lsq_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads).  Host-only; for counting launches in a region. */
+int lsq_launch_count(int64_t *out_host);
+
+/* ---- geometry and range patterns (Sec. 2.3.2) ------------------------ */
+
+/*
+ * Builds, on the GPU, the range pattern of every requested range: all
+ * ordered atom pairs (i, j), self pairs included, whose minimum-image
+ * distance satisfies d^2 <= R^2 (the paper zeroes elements with R_ij
+ * greater than the cutoff).  d = r_j - r_i, each component folded as
+ * s - L rint(s / L), d^2 = (dx dx + dy dy) + dz dz, every operation
+ * correctly rounded and none fused, so the set is reproducible bit for
+ * bit on any IEEE host.
+ *
+ * pos_dev    [n_atoms][3] float64 device array (copied; may be freed after).
+ * cell_host  [3] cell lengths; every R must be > 0.
+ * ranges_host[n_ranges] cutoffs; the range id of ranges_host[k] is k.
+ * out        receives a new handle; release with lsq_geom_destroy.
+ * Limits: n_atoms <= 2^30; at most 8192 atoms within the largest range of
+ * any atom (LSQ_ERR_UNSUPPORTED otherwise).  Synchronises the stream.
+ */
+int lsq_build_neighbour_lists(const double *pos_dev, int n_atoms, const double *cell_host,
+                              const double *ranges_host, int n_ranges, lsq_geom *out,
+                              void *stream);
+
+int lsq_geom_destroy(lsq_geom g);
+
+/* Number of atoms and of ranges of a geometry. */
+int lsq_geom_info(lsq_geom g, int *n_atoms, int *n_ranges);
+
+/*
+ * Device views of pattern range_id: row_ptr_dev [n_atoms+1] int64,
+ * col_dev [nnzb] int32 (sorted ascending within a row).  Owned by the
+ * geometry; valid until lsq_geom_destroy.  nnzb is returned on the host.
+ */
+int lsq_pattern(lsq_geom g, int range_id, const int64_t **row_ptr_dev, const int32_t **col_dev,
+                int64_t *nnzb);
+
+/* Copies pattern range_id into caller-owned device arrays row_ptr_dev
+ * [n_atoms+1] int64 and col_dev [nnzb] int32 (enqueued on stream). */
+int lsq_pattern_copy(lsq_geom g, int range_id, int64_t *row_ptr_dev, int32_t *col_dev,
+                     void *stream);
+
+/* ---- truncated block-sparse product ----------------------------------- */
+
+/*
+ * C = alpha * op(A) . op(B) + beta * C, evaluated only on the stored
+ * blocks of C's pattern (Sec. 2.3.2: the product restricted to the range
+ * of C; every matrix of the method is sparse by range):
+ *     C_ij = alpha * sum_k op(A)_ik op(B)_kj + beta * C_ij
+ * over all k with (i, k) stored in op(A)'s pattern and (k, j) in op(B)'s.
+ * op(X) = X, or X^T when trans_x != 0 (all patterns are symmetric, so
+ * X^T lives on the same pattern, with (X^T)_ik = (X_ki)^T).
+ *
+ * A_dev, B_dev, C_dev: block arrays on patterns range_a, range_b, range_c
+ * of g with block size b (1..16), dtype given by precision.  C must not
+ * alias A or B.  The first call for a (range_a, range_b, range_c, trans)
+ * combination builds and caches a product plan (allocates device memory,
+ * synchronises); later calls allocate nothing.  n_triples_host (optional)
+ * receives the number of block triples (i, k, j) of the product; the
+ * algorithmic flop count is 2 b^3 times that number.
+ */
+int lsq_block_matmul(lsq_geom g, int b, int precision,
+                     int range_a, int trans_a, const void *A_dev,
+                     int range_b, int trans_b, const void *B_dev,
+                     int range_c, void *C_dev, double alpha, double beta,
+                     int64_t *n_triples_host, void *stream);
+
+/* Tr[X Y] = sum over stored (i, j) of X, with (j, i) stored in Y, of
+ * <X_ij, (Y_ji)^T>, accumulated in float64.  Synchronises the stream. */
+int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
+              int range_y, const void *Y_dev, double *out_host, void *stream);
+
+/* ---- LNV grand-potential minimisation (Sec. 2.3.2, Eq. 8) ----------- */
+
+typedef struct {
+    int max_iter;              /* CG steps (default 100) */
+    double tol_ha_per_atom;    /* stop when |Omega_new - Omega| / N < tol (Hartree); 0: run max_iter */
+    int cg_reset;              /* restart the CG direction every cg_reset steps (default 40) */
+    int precision;             /* LSQ_F64, or LSQ_F32 for the mixed-precision path */
+    int refine_iter;           /* mixed path: FP64 CG steps after the FP32 ones converge (default 2) */
+    double spin;               /* spin degeneracy factor of Omega and N_e (default 2) */
+} lsq_lnv_opts;
+
+typedef struct {
+    int iterations;            /* CG steps taken (FP32 + FP64) */
+    int iterations_fp64;       /* of which FP64 steps */
+    int status;                /* LSQ_OK, LSQ_ERR_NOT_CONVERGED or LSQ_ERR_UNSTABLE */
+    double omega_ev;           /* Omega(L) of the returned L, evaluated in FP64 */
+    double ne;                 /* N_e = 2 Tr[K S] of the returned L, FP64 */
+    double omega_ha_per_atom;  /* omega_ev / 27.211386245988 / n_atoms */
+    double last_domega_ha_per_atom;
+    double seconds;            /* wall time of the minimisation */
+} lsq_lnv_report;
+
+/* Fills opts with the defaults listed above. */
+int lsq_lnv_default_opts(lsq_lnv_opts *opts);
+
+/*
+ * The ranges an LNV context needs in its geometry, in this order:
+ * R_S, R_H, R_L, R_L + R_S (LS), R_L + R_S + R_L (LSL), R_H + R_L + R_S
+ * (H'LS), each computed in float64 exactly as written.  out_host[6].
+ */
+int lsq_lnv_required_ranges(double R_S, double R_H, double R_L, double *out_host);
+
+/*
+ * Creates an LNV context (workspace for all products of one CG step) on
+ * geometry g, whose ranges must include lsq_lnv_required_ranges(...)
+ * (looked up by exact value).  Requires R_S <= R_H.  b: orbitals per atom.
+ * Allocates device memory once; no later LNV call allocates.
+ */
+int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double R_L, lsq_lnv *out);
+int lsq_lnv_destroy(lsq_lnv ctx);
+
+/* Initial L = 1/2 (S_ii)^-1 on the diagonal blocks, zero elsewhere
+ * (symmetrised).  S_dev on R_S's pattern, L_dev on R_L's, float64. */
+int lsq_lnv_init_L(lsq_lnv ctx, const double *S_dev, double *L_dev, void *stream);
+
+/*
+ * Omega = spin Tr[K (H - mu S)], N_e = spin Tr[K S], K = 3LSL - 2LSLSL on
+ * H's range, and G_ab = dOmega/dL_ab on L's range (symmetrised), for
+ * float64 L_dev (R_L), S_dev (R_S), H_dev (R_H).  precision LSQ_F64 or
+ * LSQ_F32 (products in FP32, traces accumulated in float64).  G_dev may
+ * be NULL.  Synchronises the stream (returns host scalars).
+ */
+int lsq_lnv_energy_gradient(lsq_lnv ctx, const double *L_dev, const double *S_dev,
+                            const double *H_dev, double mu, double spin, int precision,
+                            double *omega_host, double *ne_host, double *G_dev, void *stream);
+
+/*
+ * Conjugate-gradient minimisation of Omega over symmetric L on L's range:
+ * Polak-Ribiere direction (beta = max(0, beta_PR)) restarted every
+ * cg_reset steps, exact line minimisation of the cubic Omega(L + a D).
+ * L_dev (float64, R_L) holds the start on entry and the result on exit.
+ * Returns LSQ_OK when converged (or max_iter steps were taken with
+ * tol = 0), LSQ_ERR_NOT_CONVERGED, or LSQ_ERR_UNSTABLE; rep (optional)
+ * receives the report in every case.
+ */
+int lsq_lnv_minimise(lsq_lnv ctx, double *L_dev, const double *S_dev, const double *H_dev,
+                     double mu, const lsq_lnv_opts *opts, lsq_lnv_report *rep, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSQ_H */

@@ -1,0 +1,267 @@
+"""GB300-native linear-scaling density-matrix minimisation (LNV).
+
+Thin Python binding of ``liblsq.so``, whose C ABI is declared in
+``include/lsq.h``.  This module only marshals arguments: every step of
+the computation (range patterns, truncated atom-block products, traces,
+the gradient and the conjugate-gradient minimisation) runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.
+
+There is no CPU fallback: if the library is not built, or no CUDA device
+is present, the calls raise.
+"""
+import ctypes
+import os
+
+from ._build import LIB, build  # noqa: F401
+
+F64 = 0
+F32 = 1
+HARTREE_EV = 27.211386245988
+
+ERRORS = {1: "INVALID_ARG", 2: "PATTERN", 3: "OOM", 4: "CUDA", 5: "UNSTABLE",
+          6: "NOT_CONVERGED", 7: "UNSUPPORTED"}
+
+_lib = None
+
+
+class LsqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lsq error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+class LnvOpts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("tol_ha_per_atom", ctypes.c_double),
+                ("cg_reset", ctypes.c_int), ("precision", ctypes.c_int),
+                ("refine_iter", ctypes.c_int), ("spin", ctypes.c_double)]
+
+
+class LnvReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("iterations_fp64", ctypes.c_int),
+                ("status", ctypes.c_int), ("omega_ev", ctypes.c_double), ("ne", ctypes.c_double),
+                ("omega_ha_per_atom", ctypes.c_double),
+                ("last_domega_ha_per_atom", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path():
+    return LIB
+
+
+def load():
+    """Loads liblsq.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError("liblsq.so is not built; call paper_2002_07704_gb300.build()")
+    lib = ctypes.CDLL(LIB)
+    P, I, D, L64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sig = {
+        "lsq_last_error": (I, [ctypes.c_char_p, ctypes.c_size_t]),
+        "lsq_version": (I, []),
+        "lsq_launch_count": (I, [P]),
+        "lsq_build_neighbour_lists": (I, [P, I, P, P, I, P, P]),
+        "lsq_geom_destroy": (I, [P]),
+        "lsq_geom_info": (I, [P, P, P]),
+        "lsq_pattern": (I, [P, I, P, P, P]),
+        "lsq_pattern_copy": (I, [P, I, P, P, P]),
+        "lsq_block_matmul": (I, [P, I, I, I, I, P, I, I, P, I, P, D, D, P, P]),
+        "lsq_trace": (I, [P, I, I, I, P, I, P, P, P]),
+        "lsq_lnv_default_opts": (I, [P]),
+        "lsq_lnv_required_ranges": (I, [D, D, D, P]),
+        "lsq_lnv_create": (I, [P, I, D, D, D, P]),
+        "lsq_lnv_destroy": (I, [P]),
+        "lsq_lnv_init_L": (I, [P, P, P, P]),
+        "lsq_lnv_energy_gradient": (I, [P, P, P, P, D, D, I, P, P, P, P]),
+        "lsq_lnv_minimise": (I, [P, P, P, P, D, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    del L64
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares."""
+    return ["lsq_last_error", "lsq_version", "lsq_launch_count", "lsq_build_neighbour_lists", "lsq_geom_destroy",
+            "lsq_geom_info", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_trace",
+            "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
+            "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise"]
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    n = ctypes.c_int64()
+    _check(load().lsq_launch_count(ctypes.byref(n)))
+    return n.value
+
+
+def _check(rc):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(512)
+        _lib.lsq_last_error(buf, 512)
+        raise LsqError(rc, buf.value.decode(errors="replace"))
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _darr(vals):
+    vals = [float(v) for v in vals]
+    return (ctypes.c_double * len(vals))(*vals)
+
+
+class Geometry:
+    """Range patterns of one atomic geometry (lsq_build_neighbour_lists)."""
+
+    def __init__(self, pos, cell, ranges, stream=None):
+        import torch
+        lib = load()
+        pos = pos.to(device="cuda", dtype=torch.float64).contiguous()
+        self.ranges = [float(r) for r in ranges]
+        self.cell = [float(c) for c in cell]
+        h = ctypes.c_void_p()
+        _check(lib.lsq_build_neighbour_lists(_dev(pos), pos.shape[0], _darr(self.cell),
+                                             _darr(self.ranges), len(self.ranges),
+                                             ctypes.byref(h), _stream(stream)))
+        self.handle = h
+        self.n_atoms = int(pos.shape[0])
+
+    def range_id(self, R):
+        return self.ranges.index(float(R))
+
+    def nnzb(self, r):
+        n = ctypes.c_int64()
+        _check(_lib.lsq_pattern(self.handle, r, None, None, ctypes.byref(n)))
+        return n.value
+
+    def pattern(self, r, stream=None):
+        """(row_ptr int64 [n+1], col int32 [nnzb]) as new CUDA tensors."""
+        import torch
+        nnzb = self.nnzb(r)
+        rp = torch.empty(self.n_atoms + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(nnzb, 1), dtype=torch.int32, device="cuda")
+        _check(_lib.lsq_pattern_copy(self.handle, r, _dev(rp), _dev(col), _stream(stream)))
+        return rp, col[:nnzb]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.lsq_geom_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_neighbour_lists(pos, cell, ranges, stream=None):
+    return Geometry(pos, cell, ranges, stream)
+
+
+def block_matmul(geom, b, A, range_a, B, range_b, C, range_c, precision=F64, trans_a=False,
+                 trans_b=False, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha op(A) op(B) + beta C on C's range pattern; returns the triple count."""
+    import torch
+    dt = torch.float64 if precision == F64 else torch.float32
+    nt = ctypes.c_int64()
+    _check(load().lsq_block_matmul(geom.handle, b, precision, range_a, int(trans_a), _dev(A, dt),
+                                   range_b, int(trans_b), _dev(B, dt), range_c, _dev(C, dt),
+                                   float(alpha), float(beta), ctypes.byref(nt), _stream(stream)))
+    return nt.value
+
+
+def trace(geom, b, X, range_x, Y, range_y, precision=F64, stream=None):
+    import torch
+    dt = torch.float64 if precision == F64 else torch.float32
+    out = ctypes.c_double()
+    _check(load().lsq_trace(geom.handle, b, precision, range_x, _dev(X, dt), range_y, _dev(Y, dt),
+                            ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def lnv_required_ranges(R_S, R_H, R_L):
+    out = (ctypes.c_double * 6)()
+    _check(load().lsq_lnv_required_ranges(float(R_S), float(R_H), float(R_L), out))
+    return list(out)
+
+
+class Lnv:
+    """LNV context: workspace for the products of one CG step (lsq_lnv_create)."""
+
+    def __init__(self, geom, b, R_S, R_H, R_L):
+        h = ctypes.c_void_p()
+        _check(load().lsq_lnv_create(geom.handle, b, float(R_S), float(R_H), float(R_L),
+                                     ctypes.byref(h)))
+        self.handle = h
+        self.geom = geom
+        self.b = b
+
+    def init_L(self, S, L, stream=None):
+        import torch
+        _check(_lib.lsq_lnv_init_L(self.handle, _dev(S, torch.float64), _dev(L, torch.float64),
+                                   _stream(stream)))
+
+    def energy_gradient(self, L, S, H, mu, spin=2.0, precision=F64, G=None, stream=None):
+        import torch
+        om, ne = ctypes.c_double(), ctypes.c_double()
+        f = torch.float64
+        _check(_lib.lsq_lnv_energy_gradient(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),
+                                            float(mu), float(spin), precision, ctypes.byref(om),
+                                            ctypes.byref(ne), _dev(G, f), _stream(stream)))
+        return om.value, ne.value
+
+    def minimise(self, L, S, H, mu, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
+                 precision=F64, refine_iter=2, spin=2.0, stream=None, raise_on_status=False):
+        import torch
+        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin)
+        rep = LnvReport()
+        f = torch.float64
+        rc = _lib.lsq_lnv_minimise(self.handle, _dev(L, f), _dev(S, f), _dev(H, f), float(mu),
+                                   ctypes.byref(o), ctypes.byref(rep), _stream(stream))
+        if rc != 0 and (raise_on_status or rc not in (5, 6)):
+            _check(rc)
+        return rep.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.lsq_lnv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lnv_create(geom, b, R_S, R_H, R_L):
+    return Lnv(geom, b, R_S, R_H, R_L)
+
+
+def lnv_energy_gradient(ctx, L, S, H, mu, **kw):
+    return ctx.energy_gradient(L, S, H, mu, **kw)
+
+
+def lnv_minimise(ctx, L, S, H, mu, **kw):
+    return ctx.minimise(L, S, H, mu, **kw)

@@ -1,0 +1,511 @@
+// LNV grand-potential minimisation on the GPU (Sec. 2.3.2 of the paper).
+//
+// K = 3LSL - 2LSLSL (the McWeeny form, Eq. 8) drives the density matrix
+// towards weak idempotency; K has the range of H while L's range is
+// restricted; E_band = 2 Tr[K H] is minimised with respect to L, the
+// electron number held by a chemical potential mu.  With H' = H - mu S:
+//
+//   Omega = 2 Tr[K H'],  N_e = 2 Tr[K S]
+//   G     = 2 [3 (Q + Q^T) - 2 (G1 + G1^T + G2)] on L's range,
+//           Q = H'LS, G1 = Q.LS, G2 = Q^T.LS (= SLH'LS)
+//
+// Products per energy + gradient (ranges in brackets):
+//   LS = L.S [R_L+R_S], LSL = LS.L [2R_L+R_S], LSLSL|R_H = LSL.(LS)^T,
+//   Q = H'.LS [R_H+R_L+R_S], G1 = (Q.LS)|R_L, G2 = (Q^T.LS)|R_L.
+// Exact line search along D: Omega(L + a D) = Omega + c1 a + c2 a^2 + c3 a^3,
+//   c1 = <G, D>,  c2 = 2 (3 t2 - 2 (2 t3a + t3b)),  c3 = -4 t4, with
+//   P = D.S, QD = H'.P, F = (P.D)|[R_H+R_L+R_S] (= DSD), Z = (QD^T.P)|R_L,
+//   t2 = Tr[F H'] = Tr[DSDH'], t3a = <F, Q> = Tr[DSDSLH'] (= Tr[LSDSDH']),
+//   t3b = <L, Z> = Tr[DSLSDH'], t4 = <F, QD> = Tr[DSDSDH'],
+// using the symmetry of S, H', L and D and the cyclic property of the trace.
+// All matrices are symmetric; the CG keeps L exactly symmetric.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <string>
+
+#include "lsq_internal.h"
+
+namespace lsq {
+
+constexpr double kHartreeEv = 27.211386245988;
+
+// ---- elementwise kernels ---------------------------------------------------
+__global__ void k_to_f32(int64_t m, const double *__restrict__ x, float *__restrict__ y) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = (float)x[e];
+}
+
+// H' = H - mu S_H and S_H (S placed on H's pattern; zero where S has no block).
+__global__ void k_hprime(int64_t nnzb, int bb, const double *__restrict__ H,
+                         const double *__restrict__ S, const int64_t *__restrict__ pos_s, double mu,
+                         double *__restrict__ Hp, double *__restrict__ Sh) {
+    int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / bb;
+        int rc = (int)(e - p * bb);
+        int64_t q = pos_s[p];
+        double s = q >= 0 ? S[q * bb + rc] : 0.0;
+        Sh[e] = s;
+        Hp[e] = H[e] - mu * s;
+    }
+}
+
+// G_ij[r][c] = spin (3 (Q_ij[r][c] + Q_ji[c][r]) - 2 (G1_ij[r][c] + G1_ji[c][r]
+//              + (G2_ij[r][c] + G2_ji[c][r]) / 2)); each pair summed commutatively, so G is
+// symmetric to the last bit.
+template <typename T>
+__global__ void k_grad_combine(int64_t nnzb, int b, double spin, const int64_t *__restrict__ pq,
+                               const int64_t *__restrict__ pqt, const int64_t *__restrict__ tmL,
+                               const T *__restrict__ Q, const T *__restrict__ G1,
+                               const T *__restrict__ G2, double *__restrict__ G) {
+    const int bb = b * b;
+    int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / bb;
+        int rc = (int)(e - p * bb);
+        int r = rc / b, c = rc - r * b;
+        int64_t tr = c * b + r;
+        int64_t a = pq[p], at = pqt[p], t = tmL[p];
+        double q = (a >= 0 ? (double)Q[a * bb + rc] : 0.0) + (at >= 0 ? (double)Q[at * bb + tr] : 0.0);
+        double g1 = (double)G1[p * bb + rc] + (double)G1[t * bb + tr];
+        double g2 = (double)G2[p * bb + rc] + (double)G2[t * bb + tr];
+        G[e] = spin * (3.0 * q - 2.0 * (g1 + 0.5 * g2));
+    }
+}
+
+__global__ void k_cg_dir(int64_t m, double beta, const double *__restrict__ G, double *__restrict__ D) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        D[e] = beta == 0.0 ? -G[e] : -G[e] + beta * D[e];
+}
+
+__global__ void k_axpy(int64_t m, double a, const double *__restrict__ x, double *__restrict__ y) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = y[e] + a * x[e];
+}
+
+// L_ii = (inv(S_ii) + inv(S_ii)^T) / 4, by Gauss-Jordan elimination with partial pivoting.
+__global__ void k_onsite_inverse(int n, int b, const int64_t *__restrict__ sp,
+                                 const int32_t *__restrict__ sc, const double *__restrict__ S,
+                                 const int64_t *__restrict__ lp, const int32_t *__restrict__ lc,
+                                 double *__restrict__ L, int *__restrict__ bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    auto find = [](const int64_t *ptr, const int32_t *col, int row, int key) -> int64_t {
+        int64_t lo = ptr[row], hi = ptr[row + 1], end = hi;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (col[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        return (lo < end && col[lo] == key) ? lo : -1;
+    };
+    int64_t ps = find(sp, sc, i, i), pl = find(lp, lc, i, i);
+    if (ps < 0 || pl < 0) {
+        atomicExch(bad, 1);
+        return;
+    }
+    double a[16][32];
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < 2 * b; ++c)
+            a[r][c] = c < b ? S[ps * b * b + r * b + c] : (c - b == r ? 1.0 : 0.0);
+    for (int col = 0; col < b; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < b; ++r)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (a[piv][col] == 0.0) {
+            atomicExch(bad, 1);
+            return;
+        }
+        if (piv != col)
+            for (int c = 0; c < 2 * b; ++c) {
+                double t = a[col][c];
+                a[col][c] = a[piv][c];
+                a[piv][c] = t;
+            }
+        double inv = 1.0 / a[col][col];
+        for (int c = 0; c < 2 * b; ++c) a[col][c] *= inv;
+        for (int r = 0; r < b; ++r)
+            if (r != col) {
+                double f = a[r][col];
+                if (f != 0.0)
+                    for (int c = 0; c < 2 * b; ++c) a[r][c] -= f * a[col][c];
+            }
+    }
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) L[pl * b * b + r * b + c] = 0.25 * (a[r][b + c] + a[c][b + r]);
+}
+
+static int grid_for(int64_t m) {
+    int64_t g = (m + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8192));
+}
+
+}  // namespace lsq
+
+using namespace lsq;
+
+struct lsq_lnv_s {
+    lsq_geom g = nullptr;
+    int b = 4;
+    int rS = -1, rH = -1, rL = -1, r1 = -1, r2 = -1, r3 = -1;
+    // float64 working set
+    DevBuf<double> Hp, Sh, G, Gp, D;
+    // product buffers, sized for float64 and reused for float32
+    DevBuf<char> LS, LSL, LSLSLH, Q, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
+    const int64_t *pos_s_in_h = nullptr;
+};
+
+static int64_t nvals(lsq_lnv c, int r) { return c->g->pats[r].nnzb * c->b * c->b; }
+
+extern "C" int lsq_lnv_default_opts(lsq_lnv_opts *o) {
+    clear_error();
+    if (!o) return set_error(LSQ_ERR_INVALID_ARG, "opts is null");
+    o->max_iter = 100;
+    o->tol_ha_per_atom = 0.0;
+    o->cg_reset = 40;
+    o->precision = LSQ_F64;
+    o->refine_iter = 2;
+    o->spin = 2.0;
+    return LSQ_OK;
+}
+
+extern "C" int lsq_lnv_required_ranges(double R_S, double R_H, double R_L, double *out) {
+    clear_error();
+    if (!out) return set_error(LSQ_ERR_INVALID_ARG, "out is null");
+    out[0] = R_S;
+    out[1] = R_H;
+    out[2] = R_L;
+    out[3] = R_L + R_S;
+    out[4] = R_L + R_S + R_L;
+    out[5] = R_H + R_L + R_S;
+    return LSQ_OK;
+}
+
+extern "C" int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double R_L, lsq_lnv *out) {
+    clear_error();
+    if (!g || !out) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
+    if (!(R_S <= R_H)) return set_error(LSQ_ERR_INVALID_ARG, "R_S must not exceed R_H");
+    double need[6];
+    lsq_lnv_required_ranges(R_S, R_H, R_L, need);
+    int id[6];
+    for (int k = 0; k < 6; ++k) {
+        id[k] = find_range(g, need[k]);
+        if (id[k] < 0)
+            return set_error(LSQ_ERR_INVALID_ARG,
+                             "geometry lacks range " + std::to_string(need[k]) +
+                                 " (see lsq_lnv_required_ranges)");
+    }
+    lsq_lnv c = new lsq_lnv_s();
+    c->g = g;
+    c->b = b;
+    c->rS = id[0];
+    c->rH = id[1];
+    c->rL = id[2];
+    c->r1 = id[3];
+    c->r2 = id[4];
+    c->r3 = id[5];
+    auto fail = [&](int rc) {
+        delete c;
+        return rc;
+    };
+    int rc;
+    size_t d = sizeof(double);
+    if ((rc = c->Hp.alloc(nvals(c, c->rH))) || (rc = c->Sh.alloc(nvals(c, c->rH))) ||
+        (rc = c->G.alloc(nvals(c, c->rL))) || (rc = c->Gp.alloc(nvals(c, c->rL))) ||
+        (rc = c->D.alloc(nvals(c, c->rL))) || (rc = c->LS.alloc(d * nvals(c, c->r1))) ||
+        (rc = c->LSL.alloc(d * nvals(c, c->r2))) || (rc = c->LSLSLH.alloc(d * nvals(c, c->rH))) ||
+        (rc = c->Q.alloc(d * nvals(c, c->r3))) || (rc = c->QD.alloc(d * nvals(c, c->r3))) ||
+        (rc = c->G1.alloc(d * nvals(c, c->rL))) || (rc = c->G2.alloc(d * nvals(c, c->rL))) ||
+        (rc = c->Lc.alloc(4 * nvals(c, c->rL))) || (rc = c->Dc.alloc(4 * nvals(c, c->rL))) ||
+        (rc = c->Hpc.alloc(4 * nvals(c, c->rH))) || (rc = c->Shc.alloc(4 * nvals(c, c->rH))) ||
+        (rc = c->Sc.alloc(4 * nvals(c, c->rS))))
+        return fail(rc);
+    if ((rc = get_posmap(g, c->rH, c->rS, 0, &c->pos_s_in_h, 0))) return fail(rc);
+    if ((rc = ensure_tmap(g, c->rL, 0))) return fail(rc);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(set_error(LSQ_ERR_CUDA, "sync failed"));
+    *out = c;
+    return LSQ_OK;
+}
+
+extern "C" int lsq_lnv_destroy(lsq_lnv c) {
+    clear_error();
+    if (!c) return LSQ_OK;
+    cudaDeviceSynchronize();
+    delete c;
+    return LSQ_OK;
+}
+
+extern "C" int lsq_lnv_init_L(lsq_lnv c, const double *S, double *L, void *stream) {
+    clear_error();
+    if (!c || !S || !L) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    lsq_geom g = c->g;
+    LSQ_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(double) * nvals(c, c->rL), s));
+    DevBuf<int> bad;
+    LSQ_TRY(bad.alloc(1));
+    LSQ_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
+    if (g->n > 0)
+        note_launch();
+        k_onsite_inverse<<<(g->n + 127) / 128, 128, 0, s>>>(
+            g->n, c->b, g->pats[c->rS].row_ptr.p, g->pats[c->rS].col.p, S,
+            g->pats[c->rL].row_ptr.p, g->pats[c->rL].col.p, L, bad.p);
+    LSQ_CHECK_LAUNCH();
+    int hbad = 0;
+    LSQ_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) return set_error(LSQ_ERR_INVALID_ARG, "an on-site block of S is singular or missing");
+    return LSQ_OK;
+}
+
+namespace {
+
+// Prepares H', S_H (float64) and the reduced-precision copies for 'prec'.
+int prepare_hs(lsq_lnv c, const double *S, const double *H, double mu, int prec, cudaStream_t s) {
+    int64_t nh = nvals(c, c->rH);
+    note_launch();
+    k_hprime<<<grid_for(nh), 256, 0, s>>>(c->g->pats[c->rH].nnzb, c->b * c->b, H, S, c->pos_s_in_h,
+                                          mu, c->Hp.p, c->Sh.p);
+    if (prec == LSQ_F32) {
+        note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Hp.p, (float *)c->Hpc.p);
+        note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Sh.p, (float *)c->Shc.p);
+        int64_t ns = nvals(c, c->rS);
+        note_launch();
+        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p);
+    }
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
+struct Ops {
+    const void *L, *S, *Hp, *Sh;
+};
+
+Ops operands(lsq_lnv c, const double *L, const double *S, int prec, cudaStream_t s) {
+    Ops o;
+    if (prec == LSQ_F32) {
+        int64_t nl = nvals(c, c->rL);
+        note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p);
+        o.L = c->Lc.p;
+        o.S = c->Sc.p;
+        o.Hp = c->Hpc.p;
+        o.Sh = c->Shc.p;
+    } else {
+        o.L = L;
+        o.S = S;
+        o.Hp = c->Hp.p;
+        o.Sh = c->Sh.p;
+    }
+    return o;
+}
+
+// Omega, N_e (scalars slots 0..3 hold the four traces) and, if G != null, the gradient.
+int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *G,
+                    double *omega, double *ne, cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int b = c->b;
+    Ops o = operands(c, L, S, prec, s);
+    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 0, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 0, o.L, c->r2, c->LSL.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r2, 0, c->LSL.p, c->r1, 1, c->LS.p, c->rH, c->LSLSLH.p, 1.0, 0.0,
+                         nullptr, s));
+    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r2, c->LSL.p, 0, s));
+    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->rH, c->LSLSLH.p, 1, s));
+    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->r2, c->LSL.p, 2, s));
+    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->rH, c->LSLSLH.p, 3, s));
+    if (G) {
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, c->LS.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, 0, c->LS.p, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->Q.p, c->r1, 0, c->LS.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s));
+        const int64_t *pq = nullptr, *pqt = nullptr;
+        LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
+        LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
+        int64_t nl = nvals(c, c->rL);
+        if (prec == LSQ_F64)
+            note_launch();
+            k_grad_combine<double><<<grid_for(nl), 256, 0, s>>>(
+                g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const double *)c->Q.p,
+                (const double *)c->G1.p, (const double *)c->G2.p, G);
+        else
+            note_launch();
+            k_grad_combine<float><<<grid_for(nl), 256, 0, s>>>(
+                g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const float *)c->Q.p,
+                (const float *)c->G1.p, (const float *)c->G2.p, G);
+        LSQ_CHECK_LAUNCH();
+    }
+    if (omega || ne) {
+        double t[4];
+        LSQ_TRY(fetch_scalars(g, 4, t, s));
+        if (omega) *omega = spin * (3.0 * t[0] - 2.0 * t[1]);
+        if (ne) *ne = spin * (3.0 * t[2] - 2.0 * t[3]);
+    }
+    return LSQ_OK;
+}
+
+// c1 = <G, D> (float64), c2, c3 from the products listed at the top of the file.
+int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *c123,
+                cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int b = c->b;
+    Ops o = operands(c, L, S, prec, s);
+    const void *D = c->D.p;
+    if (prec == LSQ_F32) {
+        int64_t nl = nvals(c, c->rL);
+        note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, c->D.p, (float *)c->Dc.p);
+        D = c->Dc.p;
+    }
+    void *P = c->LS.p, *F = c->LSL.p, *Z = c->G2.p;
+    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, D, c->rS, 0, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 0, D, c->r3, F, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->QD.p, c->r1, 0, P, c->rL, Z, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
+    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, F, 5, s));
+    LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->Q.p, 6, s));
+    LSQ_TRY(dot_into(g, b, prec, c->rL, o.L, Z, 7, s));
+    LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->QD.p, 8, s));
+    double t[9];
+    LSQ_TRY(fetch_scalars(g, 9, t, s));
+    c123[0] = t[4];
+    c123[1] = spin * (3.0 * t[5] - 2.0 * (2.0 * t[6] + t[7]));
+    c123[2] = -2.0 * spin * t[8];
+    return LSQ_OK;
+}
+
+bool line_minimum(double c1, double c2, double c3, double *a) {
+    double disc = c2 * c2 - 3.0 * c1 * c3;
+    if (!(disc >= 0.0)) return false;
+    double den = c2 + std::sqrt(disc);
+    if (!(den > 0.0)) return false;
+    *a = -c1 / den;
+    return std::isfinite(*a);
+}
+
+}  // namespace
+
+extern "C" int lsq_lnv_energy_gradient(lsq_lnv c, const double *L, const double *S, const double *H,
+                                       double mu, double spin, int prec, double *omega, double *ne,
+                                       double *G, void *stream) {
+    clear_error();
+    if (!c || !L || !S || !H) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    if (prec != LSQ_F64 && prec != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    cudaStream_t s = (cudaStream_t)stream;
+    LSQ_TRY(prepare_hs(c, S, H, mu, prec, s));
+    double om = 0, n_e = 0;
+    LSQ_TRY(energy_gradient(c, L, S, spin, prec, G, &om, &n_e, s));
+    if (omega) *omega = om;
+    if (ne) *ne = n_e;
+    return LSQ_OK;
+}
+
+extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const double *H, double mu,
+                                const lsq_lnv_opts *opts, lsq_lnv_report *rep, void *stream) {
+    clear_error();
+    if (!c || !L || !S || !H) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    lsq_lnv_opts o;
+    lsq_lnv_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != LSQ_F64 && o.precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    if (o.max_iter < 0 || o.cg_reset < 1 || o.refine_iter < 0)
+        return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = c->g->n;
+    const int64_t nl = nvals(c, c->rL);
+    LSQ_TRY(prepare_hs(c, S, H, mu, LSQ_F64, s));
+    if (o.precision == LSQ_F32) LSQ_TRY(prepare_hs(c, S, H, mu, LSQ_F32, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->Gp.p, 0, sizeof(double) * nl, s));
+    // Phase 0: the requested precision for max_iter steps (or until converged);
+    // phase 1 (mixed path only): refine_iter float64 steps from a fresh direction.
+    int status = (o.tol_ha_per_atom > 0.0) ? LSQ_ERR_NOT_CONVERGED : LSQ_OK;
+    int iters = 0, iters64 = 0;
+    double last_d = 0.0;
+    const int nphase = o.precision == LSQ_F32 ? 2 : 1;
+    for (int phase = 0; phase < nphase && status != LSQ_ERR_UNSTABLE; ++phase) {
+        const int prec = phase == 0 ? o.precision : LSQ_F64;
+        const int budget = phase == 0 ? o.max_iter : o.refine_iter;
+        double gg_prev = 0.0;
+        bool converged = false;
+        for (int it = 0; it < budget; ++it) {
+            LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, c->G.p, nullptr, nullptr, s));
+            LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
+            LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
+            double t[12];
+            LSQ_TRY(fetch_scalars(c->g, 12, t, s));
+            const double om = o.spin * (3.0 * t[0] - 2.0 * t[1]);
+            const double gg = t[10], ggp = t[11];
+            if (gg == 0.0) {  // exact stationary point
+                converged = true;
+                break;
+            }
+            double beta = 0.0;
+            if (it % o.cg_reset != 0 && gg_prev > 0.0) beta = std::max(0.0, (gg - ggp) / gg_prev);
+            note_launch();
+            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, c->G.p, c->D.p);
+            LSQ_CHECK_LAUNCH();
+            double cc[3];
+            LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
+            if (cc[0] >= 0.0 && beta != 0.0) {  // not a descent direction: restart
+                note_launch();
+                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, c->G.p, c->D.p);
+                LSQ_CHECK_LAUNCH();
+                LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
+            }
+            double a = 0.0;
+            if (!(cc[0] < 0.0) || !line_minimum(cc[0], cc[1], cc[2], &a)) {
+                status = LSQ_ERR_UNSTABLE;
+                break;
+            }
+            note_launch();
+            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L);
+            LSQ_CHECK_LAUNCH();
+            std::swap(c->G.p, c->Gp.p);
+            gg_prev = gg;
+            ++iters;
+            if (prec == LSQ_F64) ++iters64;
+            const double dom = cc[0] * a + cc[1] * a * a + cc[2] * a * a * a;
+            last_d = std::fabs(dom) / kHartreeEv / std::max(n, 1);
+            (void)om;
+            if (o.tol_ha_per_atom > 0.0 && last_d < o.tol_ha_per_atom) {
+                converged = true;
+                break;
+            }
+        }
+        if (status == LSQ_ERR_UNSTABLE) break;
+        if (phase == nphase - 1 && o.tol_ha_per_atom > 0.0) {
+            // converged if the last phase converged, or (mixed path) the FP64 steps stayed below tol
+            if (converged || (nphase == 2 && iters64 > 0 && last_d < o.tol_ha_per_atom))
+                status = LSQ_OK;
+        }
+    }
+    double om = 0, ne = 0;
+    LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, &om, &ne, s));
+    auto t1 = std::chrono::steady_clock::now();
+    if (rep) {
+        rep->iterations = iters;
+        rep->iterations_fp64 = iters64;
+        rep->status = status;
+        rep->omega_ev = om;
+        rep->ne = ne;
+        rep->omega_ha_per_atom = om / kHartreeEv / std::max(n, 1);
+        rep->last_domega_ha_per_atom = last_d;
+        rep->seconds = std::chrono::duration<double>(t1 - t0).count();
+    }
+    if (status == LSQ_ERR_UNSTABLE) return set_error(status, "no local minimum along the CG direction");
+    if (status == LSQ_ERR_NOT_CONVERGED) return set_error(status, "iteration limit reached");
+    return LSQ_OK;
+}

@@ -1,0 +1,136 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lsq.h"
+
+namespace lsq {
+
+// ---- kernel launch counter (every launch site calls note_launch) -----------
+extern std::atomic<long long> g_launch_count;
+void note_launch();
+
+// ---- errors -------------------------------------------------------------
+int set_error(int code, const std::string &msg);
+void clear_error();
+
+#define LSQ_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::lsq::set_error(e_ == cudaErrorMemoryAllocation ? LSQ_ERR_OOM       \
+                                                                    : LSQ_ERR_CUDA,     \
+                                    std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LSQ_TRY(expr)                  \
+    do {                               \
+        int rc_ = (expr);              \
+        if (rc_ != LSQ_OK) return rc_; \
+    } while (0)
+
+#define LSQ_CHECK_LAUNCH() LSQ_CUDA_TRY(cudaGetLastError())
+
+// ---- device buffers owned by the library --------------------------------
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    int alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return set_error(LSQ_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        n = count;
+        return LSQ_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+};
+
+// One range pattern: CSR of atom blocks, plus lazily built position maps.
+struct Pattern {
+    double R = 0.0;
+    int64_t nnzb = 0;
+    int max_row = 0;
+    DevBuf<int64_t> row_ptr;  // [n + 1]
+    DevBuf<int32_t> col;      // [nnzb]
+    DevBuf<int64_t> tmap;     // [nnzb] position of (j, i) for entry (i, j); built on demand
+};
+
+// Plan of a truncated product: the kernel mode and its exact triple count.
+enum { MODE_ROWS = 0, MODE_INNER = 1 };
+struct Plan {
+    int mode = MODE_ROWS;
+    int chunk = 0;
+    int64_t triples = 0;
+};
+
+struct Reducer {
+    DevBuf<double> partial;   // per-block partial sums
+    DevBuf<double> scalars;   // result slots
+    double *host = nullptr;   // pinned mirror of scalars
+    int nblocks = 0;
+};
+
+}  // namespace lsq
+
+struct lsq_geom_s {
+    int n = 0;
+    int n_ranges = 0;
+    double cell[3] = {0, 0, 0};
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    lsq::DevBuf<double> pos;
+    std::vector<lsq::Pattern> pats;
+    // key: (range_a, trans_a, range_b, trans_b, range_c, b, dtype)
+    std::map<std::tuple<int, int, int, int, int, int, int>, lsq::Plan> plans;
+    // key: (pattern p, pattern q, transposed): position in q of (i, j) or (j, i) for each entry of p
+    std::map<std::tuple<int, int, int>, lsq::DevBuf<int64_t>> posmaps;
+    lsq::Reducer red;
+};
+
+namespace lsq {
+
+int geom_check(lsq_geom g, int range_id);
+int ensure_tmap(lsq_geom g, int r, cudaStream_t s);
+// Position map from pattern p to pattern q (see posmaps).  Returned pointer owned by g.
+int get_posmap(lsq_geom g, int p, int q, int transposed, const int64_t **out, cudaStream_t s);
+int find_range(lsq_geom g, double R);
+
+// Truncated product C = alpha op(A) op(B) + beta C (see lsq_block_matmul).
+int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
+                 const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
+                 cudaStream_t s);
+
+// Reductions into g->red.scalars[slot] (float64), enqueued on s.
+int trace_into(lsq_geom g, int b, int dtype, int rx, const void *X, int ry, const void *Y, int slot,
+               cudaStream_t s);
+int dot_into(lsq_geom g, int b, int dtype, int r, const void *X, const void *Y, int slot,
+             cudaStream_t s);
+int reducer_ensure(lsq_geom g, int nslots);
+int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s);
+
+inline size_t dtype_size(int dtype) { return dtype == LSQ_F64 ? 8 : 4; }
+
+}  // namespace lsq

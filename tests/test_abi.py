@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point include/lsq.h declares.
+
+No compute call is made (there may be no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2002_07704_gb300 as lsq
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"^int\s+(lsq_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lsq.build()
+    return ctypes.CDLL(lsq.library_path())
+
+
+def test_header_declares_the_paths_calls():
+    d = _declared()
+    for name in ("lsq_build_neighbour_lists", "lsq_block_matmul", "lsq_lnv_energy_gradient",
+                 "lsq_lnv_minimise"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_symbol():
+    assert set(lsq.exported_symbols()) == _declared()
+
+
+def test_host_only_calls(lib):
+    lsq.load()
+    assert lsq.load().lsq_version() == 100
+    out = (ctypes.c_double * 6)()
+    assert lsq.load().lsq_lnv_required_ranges(6.6, 6.6, 10.0, out) == 0
+    assert list(out) == [6.6, 6.6, 10.0, 10.0 + 6.6, 10.0 + 6.6 + 10.0, 6.6 + 10.0 + 6.6]
+    o = lsq.LnvOpts()
+    assert lsq.load().lsq_lnv_default_opts(ctypes.byref(o)) == 0
+    assert o.cg_reset == 40 and o.spin == 2.0
+
+
+def test_invalid_arguments_are_rejected_without_gpu(lib):
+    L = lsq.load()
+    h = ctypes.c_void_p()
+    # null output handle, bad range count, non-positive range: all rejected on the host
+    assert L.lsq_build_neighbour_lists(None, 0, None, None, 0, None, None) == 1
+    cell = (ctypes.c_double * 3)(10.0, 10.0, 10.0)
+    rng = (ctypes.c_double * 1)(-1.0)
+    assert L.lsq_build_neighbour_lists(None, 0, cell, rng, 1, ctypes.byref(h), None) == 1
+    buf = ctypes.create_string_buffer(256)
+    assert L.lsq_last_error(buf, 256) == 1 and b"positive" in buf.value
+    assert L.lsq_block_matmul(None, 4, 0, 0, 0, None, 0, 0, None, 0, None, 1.0, 0.0, None, None) == 1

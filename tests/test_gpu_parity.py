@@ -1,0 +1,206 @@
+"""Parity of the CUDA path against the CPU oracle on the same seeded inputs.
+
+Tolerances: range patterns bit-exact; float64 products within 1e-12 of
+the oracle (max-norm, relative to the largest reference element); float32
+products within 1e-5 of max |A|.|B| (inputs rounded to 24 bits and sums
+of up to ~10^4 terms); LNV energies in float64 within 1e-11 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import lnv as OL
+import paper_2002_07704_gb300 as lsq
+from gpu_common import cuda, gpu_geometry, gpu_pattern, rel_err, si, si_hs
+from synth import config_seed
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lsq.build()
+    lsq.load()
+
+
+@pytest.mark.parametrize("n,sigma,ranges", [
+    (1, 0.05, [2.0, 6.6, 10.0, 30.0]),
+    (2, 0.05, [6.6, 8.0, 14.6, 22.6, 21.2]),
+    (3, 0.15, [6.6, 10.0, 16.6, 26.6, 23.2]),
+    (8, 0.05, [6.6, 10.0, 16.6, 26.6, 23.2]),
+])
+def test_patterns_bit_exact(n, sigma, ranges):
+    pos, cell = si(n, sigma, config_seed(1) + n)
+    g = gpu_geometry(pos, cell, ranges)
+    for r, R in enumerate(ranges):
+        assert gpu_pattern(g, r) == oracle.neighbour_list(pos, cell, R, "cell")
+
+
+def test_pattern_empty_and_single_atom():
+    g = gpu_geometry(np.zeros((0, 3)), [10.0, 10.0, 10.0], [3.0])
+    assert g.nnzb(0) == 0
+    g1 = gpu_geometry(np.array([[1.0, 2.0, 3.0]]), [10.0, 10.0, 10.0], [3.0])
+    p = gpu_pattern(g1, 0)
+    assert p.nnzb == 1 and p.col[0] == 0
+
+
+def _rand(pat, b, rng):
+    return rng.standard_normal((pat.nnzb, b, b))
+
+
+@pytest.mark.parametrize("n,b,ra,rb,rc,ta,tb", [
+    (2, 4, 10.0, 6.6, 16.6, 0, 0),    # L.S at its natural range (row form)
+    (2, 4, 16.6, 10.0, 26.6, 0, 0),   # LS.L
+    (2, 4, 26.6, 16.6, 6.6, 0, 1),    # LSL.(LS)^T truncated to R_H (inner form)
+    (2, 4, 23.2, 16.6, 10.0, 1, 0),   # Q^T.LS truncated to R_L
+    (3, 4, 6.6, 10.0, 8.0, 1, 1),     # both transposed, truncated
+    (3, 4, 10.0, 6.6, 16.6, 0, 0),
+    (1, 13, 3.0, 2.5, 4.0, 0, 0),     # 13 x 13 blocks (generic kernel)
+    (1, 13, 3.0, 2.5, 5.5, 1, 1),
+    (2, 7, 4.0, 4.0, 6.0, 0, 1),      # ragged block size
+])
+@pytest.mark.parametrize("prec", [lsq.F64, lsq.F32])
+def test_block_matmul_matches_oracle(n, b, ra, rb, rc, ta, tb, prec):
+    pos, cell = si(n, 0.1, config_seed(0) + 31 * n + b)
+    ranges = sorted(set([ra, rb, rc]))
+    g = gpu_geometry(pos, cell, ranges)
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in ranges}
+    rng = np.random.default_rng(100 + b)
+    A = oracle.Bsr(P[ra], b, _rand(P[ra], b, rng))
+    B = oracle.Bsr(P[rb], b, _rand(P[rb], b, rng))
+    C0 = oracle.Bsr(P[rc], b, _rand(P[rc], b, rng))
+    opA = oracle.transpose(A, P[ra]) if ta else A
+    opB = oracle.transpose(B, P[rb]) if tb else B
+    ref, triples = oracle.matmul(opA, opB, P[rc])
+    alpha, beta = 0.75, -0.5
+    ref_val = alpha * ref.val + beta * C0.val
+    dt = torch.float64 if prec == lsq.F64 else torch.float32
+    Cg = cuda(C0.val, dt)
+    t = lsq.block_matmul(g, b, cuda(A.val, dt), g.range_id(ra), cuda(B.val, dt), g.range_id(rb),
+                         Cg, g.range_id(rc), precision=prec, trans_a=ta, trans_b=tb,
+                         alpha=alpha, beta=beta)
+    torch.cuda.synchronize()
+    assert t == triples
+    got = Cg.double().cpu().numpy()
+    if prec == lsq.F64:
+        assert rel_err(got, ref_val) <= 1e-12
+    else:
+        absA = oracle.Bsr(P[ra], b, np.abs(opA.val))
+        absB = oracle.Bsr(P[rb], b, np.abs(opB.val))
+        bound, _ = oracle.matmul(absA, absB, P[rc])
+        scale = abs(alpha) * bound.val.max() + abs(beta) * np.abs(C0.val).max()
+        assert np.abs(got - ref_val).max() <= 1e-5 * scale
+
+
+def test_block_matmul_full_size_sampled_rows():
+    """4096-atom Si, LS.L (natural range 26.6 A) in float64: sampled rows against the oracle."""
+    pos, cell = si(8, 0.05, config_seed(1))
+    ranges = [6.6, 10.0, 16.6, 26.6]
+    g = gpu_geometry(pos, cell, ranges)
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in ranges}
+    rng = np.random.default_rng(7)
+    A = oracle.Bsr(P[16.6], 4, _rand(P[16.6], 4, rng))
+    B = oracle.Bsr(P[10.0], 4, _rand(P[10.0], 4, rng))
+    Cg = torch.zeros((P[26.6].nnzb, 4, 4), dtype=torch.float64, device="cuda")
+    t = lsq.block_matmul(g, 4, cuda(A.val), 2, cuda(B.val), 1, Cg, 3)
+    rows = np.array([0, 1, 777, 2048, 4095])
+    ref, _ = oracle.matmul(A, B, P[26.6], rows=rows)
+    got = Cg.cpu().numpy()
+    for i in rows:
+        s = slice(P[26.6].ptr[i], P[26.6].ptr[i + 1])
+        assert rel_err(got[s], ref.val[s]) <= 1e-12
+    assert t > 0
+
+
+def test_trace_matches_oracle():
+    pos, cell = si(2, 0.1, 5)
+    g = gpu_geometry(pos, cell, [6.6, 10.0])
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in (6.6, 10.0)}
+    rng = np.random.default_rng(9)
+    X = oracle.Bsr(P[6.6], 4, _rand(P[6.6], 4, rng))
+    Y = oracle.Bsr(P[10.0], 4, _rand(P[10.0], 4, rng))
+    got = lsq.trace(g, 4, cuda(X.val), 0, cuda(Y.val), 1)
+    ref = oracle.trace(X, Y)
+    assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+# ---- LNV ---------------------------------------------------------------------
+R_S = R_H = 6.6
+MU = -2.0
+
+
+def _lnv_setup(n, sigma, seed, R_L, b=4):
+    pos, cell = si(n, sigma, seed)
+    ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
+    g = gpu_geometry(pos, cell, ranges)
+    m = OL.System(pos, cell)
+    pH = m.pattern(R_H)
+    assert gpu_pattern(g, 1) == pH
+    H, S = si_hs(pos, cell, pH, b)
+    Hb, Sb = oracle.Bsr(pH, b, H), oracle.Bsr(pH, b, S)
+    ref = OL.Lnv(m, Sb, Hb, R_L, MU)
+    ctx = lsq.Lnv(g, b, R_S, R_H, R_L)
+    return g, ctx, ref, Hb, Sb
+
+
+def test_lnv_init_energy_gradient_float64():
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    L1, _ = OL.minimise(ref, L0, 3)
+    Lg = torch.zeros((ref.pat_L.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+    ctx.init_L(cuda(Sb.val), Lg)
+    torch.cuda.synchronize()
+    assert rel_err(Lg.cpu().numpy(), L0.val) <= 1e-13
+    G = torch.zeros_like(Lg)
+    om, ne = ctx.energy_gradient(cuda(L1.val), cuda(Sb.val), cuda(Hb.val), MU, G=G)
+    om_ref, ne_ref = ref.energy(L1)
+    assert abs(om - om_ref) <= 1e-11 * abs(om_ref)
+    assert abs(ne - ne_ref) <= 1e-11 * abs(ne_ref)
+    Gr = ref.gradient(L1)
+    Gr = 0.5 * (Gr + oracle.transpose(Gr, Gr.pat))
+    assert rel_err(G.cpu().numpy(), Gr.val) <= 1e-11
+    Gh = G.cpu().numpy()
+    assert np.array_equal(Gh, oracle.transpose(oracle.Bsr(ref.pat_L, 4, Gh), ref.pat_L).val)
+
+
+def test_lnv_energy_float32_within_tolerance():
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    L1, _ = OL.minimise(ref, L0, 3)
+    G = torch.zeros((ref.pat_L.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+    om, ne = ctx.energy_gradient(cuda(L1.val), cuda(Sb.val), cuda(Hb.val), MU, G=G,
+                                 precision=lsq.F32)
+    om_ref, _ = ref.energy(L1)
+    assert abs(om - om_ref) / lsq.HARTREE_EV / 64 < 1e-6
+    Gr = ref.gradient(L1)
+    assert rel_err(G.cpu().numpy(), 0.5 * (Gr.val + oracle.transpose(Gr, Gr.pat).val)) < 1e-5
+
+
+def test_lnv_minimise_float64_matches_oracle_trajectory():
+    """The 64-atom configuration: 20 CG steps, L range 8 A, mu = -2 eV."""
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    Lr, hist = OL.minimise(ref, L0, 20)
+    Lg = cuda(L0.val)
+    rep = ctx.minimise(Lg, cuda(Sb.val), cuda(Hb.val), MU, max_iter=20)
+    om_ref, ne_ref = ref.energy(Lr)
+    assert rep["iterations"] == 20
+    assert abs(rep["omega_ev"] - om_ref) <= 1e-9 * abs(om_ref)
+    assert abs(rep["ne"] - ne_ref) <= 1e-9 * abs(ne_ref)
+    assert rel_err(Lg.cpu().numpy(), Lr.val) <= 1e-7
+
+
+def test_lnv_mixed_precision_reaches_float64_minimum():
+    """Mixed path (float32 products, float64 traces and refinement) vs the oracle's minimum."""
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    Lr, hist = OL.minimise(ref, L0, 150, tol_ha_per_atom=1e-10)
+    om_ref = ref.energy(Lr)[0]
+    Lg = cuda(L0.val)
+    rep = ctx.minimise(Lg, cuda(Sb.val), cuda(Hb.val), MU, max_iter=150, tol_ha_per_atom=1e-9,
+                       precision=lsq.F32, refine_iter=3)
+    assert abs(rep["omega_ev"] - om_ref) / lsq.HARTREE_EV / 64 < 1e-6
+    # the returned Omega is a float64 evaluation of the returned L
+    om_chk, _ = ref.energy(oracle.Bsr(ref.pat_L, 4, Lg.cpu().numpy()))
+    assert abs(rep["omega_ev"] - om_chk) <= 1e-10 * abs(om_chk)
