@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the LNV hot path on 4096-atom Si (8x8x8 diamond cells).
+
+One "step" is one conjugate-gradient step of the LNV minimisation: the
+energy and gradient (six truncated block products, traces, the gradient
+combine), the exact cubic line search (four more products and traces)
+and the update of L.  The headline value is mixed-precision (float32
+products, float64 traces and CG) steps per second; the float64 path, the
+dominant product kernel's roofline, an end-to-end number through the
+public API with host buffers, and the CPU oracle timed on a row sample
+of the same workload are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload on its own GPU (the path has no exchange step).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import config_seed, diamond_si_positions, sk_blocks  # noqa: E402
+
+N_CELLS = 8
+SIGMA = 0.05
+R_S = R_H = 6.6
+R_L = 10.0
+MU = -2.0
+B = 4
+METRIC = "LNV steps/s & bsGEMM GFLOP/s, 4096-atom Si, mixed vs FP64 @1e-6 Ha/atom"
+WORKLOAD = ("4096-atom Si (8x8x8 diamond cells, a=5.431 A, sigma=0.05 A, seed 2002077041), "
+            "sp3 Slater-Koster H/S, 4x4 blocks, R_S=R_H=6.6 A, R_L=10 A, mu=-2 eV")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--cpu-sample-rows", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--only-product", action="store_true",
+                   help="run only the dominant product (LS.L|R3, float32) three times; for profilers")
+    return p.parse_args()
+
+
+# ---- the CPU oracle on a row sample ------------------------------------------
+def oracle_step_seconds(pos, cell, rows_per_step, seed):
+    """Seconds of one oracle CG step (energy, gradient, cubic coefficients) at full size,
+    estimated from a sample: every block product restricted to `rows_per_step` random
+    rows (scaled by n / rows), all other work timed in full."""
+    import oracle
+    from oracle import lnv as OL
+    m = OL.System(pos, cell)
+    pH = m.pattern(R_H)
+    H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
+    Hb, Sb = oracle.Bsr(pH, B, H), oracle.Bsr(pH, B, S)
+    lnv = OL.Lnv(m, Sb, Hb, R_L, MU)
+    L = OL.onsite_inverse_half(Sb, lnv.pat_L)
+    n = pos.shape[0]
+    rows = np.sort(np.random.default_rng(seed).choice(n, size=rows_per_step, replace=False))
+    t0 = time.perf_counter()
+    with OL.row_sample(rows) as smp:
+        lnv.energy(L)
+        G = lnv.gradient(L)
+        G = 0.5 * (G + oracle.transpose(G, G.pat))
+        D = -1.0 * G
+        lnv.cubic(L, D, G)
+    total = time.perf_counter() - t0
+    mm = smp.mm_seconds
+    return mm * n / rows_per_step + (total - mm), total
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pos, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1))
+    import oracle
+    oracle.build()
+    rows = max(1, args.cpu_sample_rows // 4)
+    for w in range(args.warmup):
+        oracle_step_seconds(pos, cell, rows, 1000 + w)
+    est, wall = [], 0.0
+    for k in range(args.steps):
+        e, t = oracle_step_seconds(pos, cell, rows, 2000 + k)
+        est.append(e)
+        wall += t
+    sec = float(np.mean(est))
+    v = 1.0 / sec
+    sample = ("oracle CG step with each block product restricted to %d of 4096 rows "
+              "(scaled by 4096/%d), other work in full; %d steps" % (rows, rows, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "float64 oracle (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---- clocks during the timed region -----------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "lsq_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- our arm -------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2002_07704_gb300 as lsq
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lsq.build()
+    lsq.load()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- workload (one replica per rank) ---
+    pos, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1) + 1000 * rank)
+    ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
+    geom = lsq.Geometry(torch.from_numpy(pos).cuda(), cell, ranges)
+    rp, col = geom.pattern(1)
+    rp, col = rp.cpu().numpy(), col.cpu().numpy()
+    rows = np.repeat(np.arange(geom.n_atoms), np.diff(rp))
+    H, S = sk_blocks(pos, cell, rows, col)
+    Hd = torch.from_numpy(H).cuda()
+    Sd = torch.from_numpy(S).cuda()
+    ctx = lsq.Lnv(geom, B, R_S, R_H, R_L)
+    L0 = torch.zeros((geom.nnzb(2), B, B), dtype=torch.float64, device="cuda")
+    ctx.init_L(Sd, L0)
+
+    if args.only_product:
+        Lc, Sc = L0.float(), Sd.float()
+        LS = torch.zeros((geom.nnzb(3), B, B), dtype=torch.float32, device="cuda")
+        LSL = torch.zeros((geom.nnzb(5), B, B), dtype=torch.float32, device="cuda")
+        lsq.block_matmul(geom, B, Lc, 2, Sc, 0, LS, 3, precision=lsq.F32, trans_b=True)
+        for _ in range(3):
+            lsq.block_matmul(geom, B, LS, 3, Lc, 2, LSL, 5, precision=lsq.F32, trans_b=True)
+        torch.cuda.synchronize()
+        print("only-product done")
+        return
+
+    def steps(L, k, prec):
+        return ctx.minimise(L, Sd, Hd, MU, max_iter=k, precision=prec, refine_iter=0,
+                            final_eval=False)
+
+    # --- mixed precision: warm-up, then the timed steps ---
+    L = L0.clone()
+    steps(L, args.warmup, lsq.F32)
+    L = L0.clone()
+    clk = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    n0 = lsq.launch_count()
+    clk.start()
+    e0.record(stream)
+    rep = steps(L, args.steps, lsq.F32)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    launches = lsq.launch_count() - n0
+    done = int(rep["iterations"])
+    if done != args.steps:
+        print("warning: the timed minimisation stopped after %d of %d steps (status %d)"
+              % (done, args.steps, rep["status"]), file=sys.stderr)
+    ms = e0.elapsed_time(e1) / max(done, 1)
+    ms_all = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * 1000.0 / ms_all
+
+    # --- float64 path, same steps from the same start ---
+    L64 = L0.clone()
+    steps(L64, 1, lsq.F64)
+    L64 = L0.clone()
+    barrier()
+    e0.record(stream)
+    rep64 = steps(L64, args.fp64_steps, lsq.F64)
+    e1.record(stream)
+    barrier()
+    ms64 = e0.elapsed_time(e1) / max(int(rep64["iterations"]), 1)
+    # accuracy of the mixed path: float64 Omega of both iterates after the same number of steps
+    Lm = L0.clone()
+    steps(Lm, args.fp64_steps, lsq.F32)
+    om_m, _ = ctx.energy_gradient(Lm, Sd, Hd, MU)
+    om_d, _ = ctx.energy_gradient(L64, Sd, Hd, MU)
+    acc = abs(om_m - om_d) / lsq.HARTREE_EV / geom.n_atoms
+
+    # --- dominant kernel: LS.L (row form) timed alone on the same stream ---
+    dt = torch.float32
+    Lc = L.to(dt)
+    Sc = Sd.to(dt)
+    LS = torch.zeros((geom.nnzb(3), B, B), dtype=dt, device="cuda")
+    LSL = torch.zeros((geom.nnzb(5), B, B), dtype=dt, device="cuda")
+    lsq.block_matmul(geom, B, Lc, 2, Sc, 0, LS, 3, precision=lsq.F32, trans_b=True)
+    trip = lsq.block_matmul(geom, B, LS, 3, Lc, 2, LSL, 5, precision=lsq.F32, trans_b=True)
+    reps = 5
+    barrier()
+    e0.record(stream)
+    for _ in range(reps):
+        lsq.block_matmul(geom, B, LS, 3, Lc, 2, LSL, 5, precision=lsq.F32, trans_b=True)
+    e1.record(stream)
+    barrier()
+    kms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * B ** 3 * trip
+    abytes = (geom.nnzb(3) + geom.nnzb(2) + geom.nnzb(5)) * B * B * 4
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            import hashlib
+            src = open(os.path.join(ROOT, "paper_2002_07704_gb300", "csrc", "mm.cu"), "rb").read()
+            if tj.get("mm_cu_sha256") == hashlib.sha256(src).hexdigest():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # --- end to end through the public API, host buffers ---
+    Lh = L0.cpu().pin_memory()
+    Sh = Sd.cpu().pin_memory()
+    Hh = Hd.cpu().pin_memory()
+    Lout = torch.empty_like(Lh).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    Ldev = Lh.to("cuda", non_blocking=True)
+    Sdev = Sh.to("cuda", non_blocking=True)
+    Hdev = Hh.to("cuda", non_blocking=True)
+    rep_e2e = ctx.minimise(Ldev, Sdev, Hdev, MU, max_iter=args.steps, precision=lsq.F32,
+                           refine_iter=0, final_eval=True)
+    Lout.copy_(Ldev, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": world * args.steps / t_e2e, "unit": "steps/s",
+           "h2d_bytes_per_step": int((Lh.numel() + Sh.numel() + Hh.numel()) * 8 / args.steps),
+           "d2h_bytes_per_step": int(Lout.numel() * 8 / args.steps),
+           "definition": ("one lnv_minimise call of %d mixed steps from pinned host L, S, H, "
+                          "with the float64 evaluation of the result and the copy of L back"
+                          % args.steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sec, wall = oracle_step_seconds(pos, cell, args.cpu_sample_rows, 7)
+        cpu = {"value": 1.0 / sec, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": ("one oracle CG step (energy, gradient, cubic) with every block product "
+                          "restricted to %d random rows of 4096 and scaled by 4096/%d, other "
+                          "work timed in full; %.1f s of CPU" % (args.cpu_sample_rows,
+                                                                 args.cpu_sample_rows, wall))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "float32 products, float64 traces/CG",
+                       "l2": "inputs larger than L2 (LSL alone is 885 MB in float32)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "fp64": {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64, "steps": args.fp64_steps},
+            "mixed_vs_fp64_omega_ha_per_atom": acc,
+            "bsgemm": {"product": "LS.L truncated to 23.2 A (the step's largest product)",
+                       "triples": trip,
+                       "gflops": flops / kms / 1e6, "ms": kms},
+            "roofline": {"bound": "alu", "achieved": flops / kms / 1e9, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": flops / kms / 1e9 / fp32_peak,
+                         "traffic": traffic, "kernel": "k_mm_plan_b4<float>",
+                         "hbm_frac": abytes / kms / 1e6 / 6687.5,
+                         "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"},
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "last_report": {"mixed": rep, "fp64": rep64, "e2e": rep_e2e},
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,9 @@ typedef struct {
     int precision;             /* LSQ_F64, or LSQ_F32 for the mixed-precision path */
     int refine_iter;           /* mixed path: FP64 CG steps after the FP32 ones converge (default 2) */
     double spin;               /* spin degeneracy factor of Omega and N_e (default 2) */
+    int final_eval;            /* 1 (default): evaluate Omega and N_e of the returned L in
+                                  float64 for the report; 0: report the last step's prediction */
+    int verbose;               /* 1: print one line per CG step to stderr (default 0) */
 } lsq_lnv_opts;
 
 typedef struct {

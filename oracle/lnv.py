@@ -29,6 +29,8 @@ Intermediate products are kept at their natural range (the sum of their
 factors' ranges), so no truncation enters beyond L's own range and the
 final restriction of each trace to H's range.
 """
+import time
+
 import numpy as np
 
 from . import Bsr, Pattern, dot, matmul, neighbour_list, restrict, trace, transpose
@@ -52,11 +54,37 @@ class System:
         return self._pats[R]
 
 
+_sample = {"rows": None, "mm_seconds": 0.0}
+
+
+class row_sample:
+    """Context manager for timing a sample of a large workload: inside it,
+    every block product of the LNV steps is evaluated on the given rows of
+    its result only (other rows stay zero) and the time spent in products
+    is accumulated.  Results are not meaningful inside the context."""
+
+    def __init__(self, rows):
+        self.rows = np.ascontiguousarray(rows, dtype=np.int32)
+
+    def __enter__(self):
+        _sample["rows"] = self.rows
+        _sample["mm_seconds"] = 0.0
+        return self
+
+    def __exit__(self, *exc):
+        self.mm_seconds = _sample["mm_seconds"]
+        _sample["rows"] = None
+        return False
+
+
 def mm(sysm, A, B, R=None):
     """A.B on its natural range R_A + R_B, or truncated to range R."""
     if R is None:
         R = A.pat.R + B.pat.R
-    C, _ = matmul(A, B, sysm.pattern(R))
+    pat = sysm.pattern(R)
+    t0 = time.perf_counter()
+    C, _ = matmul(A, B, pat, rows=_sample["rows"])
+    _sample["mm_seconds"] += time.perf_counter() - t0
     return C
 
 
@@ -138,18 +166,22 @@ class Lnv:
 
 
 def line_minimum(c1, c2, c3):
-    """Local minimum a > 0 of c1 a + c2 a^2 + c3 a^3 (c1 < 0), or None.
+    """Step a > 0 along a descent direction (c1 < 0) for c1 a + c2 a^2 + c3 a^3, or None.
 
     The stationary points solve 3 c3 a^2 + 2 c2 a + c1 = 0; the one with
-    positive curvature is a = -c1 / (c2 + sqrt(c2^2 - 3 c1 c3)).
+    positive curvature is a = -c1 / (c2 + sqrt(c2^2 - 3 c1 c3)).  When the
+    cubic has no local minimum (negative discriminant) but positive
+    curvature at a = 0 (c2 > 0), the minimum of its quadratic part,
+    a = -c1 / (2 c2), is taken; otherwise there is no safe step.
     """
     disc = c2 * c2 - 3.0 * c1 * c3
-    if disc < 0.0:
-        return None
-    den = c2 + np.sqrt(disc)
-    if den <= 0.0:
-        return None
-    return -c1 / den
+    if disc >= 0.0:
+        den = c2 + np.sqrt(disc)
+        if den > 0.0:
+            return -c1 / den
+    if c2 > 0.0:
+        return -c1 / (2.0 * c2)
+    return None
 
 
 def minimise(lnv, L0, n_iter, reset=40, tol_ha_per_atom=None):

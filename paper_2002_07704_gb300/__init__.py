@@ -33,7 +33,8 @@ class LsqError(RuntimeError):
 class LnvOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_ha_per_atom", ctypes.c_double),
                 ("cg_reset", ctypes.c_int), ("precision", ctypes.c_int),
-                ("refine_iter", ctypes.c_int), ("spin", ctypes.c_double)]
+                ("refine_iter", ctypes.c_int), ("spin", ctypes.c_double),
+                ("final_eval", ctypes.c_int), ("verbose", ctypes.c_int)]
 
 
 class LnvReport(ctypes.Structure):
@@ -232,9 +233,11 @@ class Lnv:
         return om.value, ne.value
 
     def minimise(self, L, S, H, mu, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
-                 precision=F64, refine_iter=2, spin=2.0, stream=None, raise_on_status=False):
+                 precision=F64, refine_iter=2, spin=2.0, final_eval=True, verbose=False,
+                 stream=None, raise_on_status=False):
         import torch
-        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin)
+        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
+                    int(bool(final_eval)), int(bool(verbose)))
         rep = LnvReport()
         f = torch.float64
         rc = _lib.lsq_lnv_minimise(self.handle, _dev(L, f), _dev(S, f), _dev(H, f), float(mu),

@@ -9,9 +9,11 @@
 //   G     = 2 [3 (Q + Q^T) - 2 (G1 + G1^T + G2)] on L's range,
 //           Q = H'LS, G1 = Q.LS, G2 = Q^T.LS (= SLH'LS)
 //
-// Products per energy + gradient (ranges in brackets):
-//   LS = L.S [R_L+R_S], LSL = LS.L [2R_L+R_S], LSLSL|R_H = LSL.(LS)^T,
-//   Q = H'.LS [R_H+R_L+R_S], G1 = (Q.LS)|R_L, G2 = (Q^T.LS)|R_L.
+// Products per energy + gradient (ranges in brackets, R3 = R_H+R_L+R_S):
+//   LS = L.S [R_L+R_S], LSL = (LS.L)|R3, Q = H'.LS [R3],
+//   G1 = (Q.LS)|R_L, G2 = (Q^T.LS)|R_L;
+//   Omega = 2 (3 Tr[H' LSL] - 2 <LSL, Q>), since Tr[LSLSLH'] = Tr[LSL (SLH')] and
+//   SLH' = Q^T; N_e = 2 (3 Tr[S LSL] - 2 <LSL, SLS>) with SLS = S.LS [R3].
 // Exact line search along D: Omega(L + a D) = Omega + c1 a + c2 a^2 + c3 a^3,
 //   c1 = <G, D>,  c2 = 2 (3 t2 - 2 (2 t3a + t3b)),  c3 = -4 t4, with
 //   P = D.S, QD = H'.P, F = (P.D)|[R_H+R_L+R_S] (= DSD), Z = (QD^T.P)|R_L,
@@ -22,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <string>
 
@@ -147,6 +150,8 @@ static int grid_for(int64_t m) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8192));
 }
 
+
+
 }  // namespace lsq
 
 using namespace lsq;
@@ -158,7 +163,7 @@ struct lsq_lnv_s {
     // float64 working set
     DevBuf<double> Hp, Sh, G, Gp, D;
     // product buffers, sized for float64 and reused for float32
-    DevBuf<char> LS, LSL, LSLSLH, Q, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
+    DevBuf<char> LS, SL, LSL, Q, QT, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
     const int64_t *pos_s_in_h = nullptr;
 };
 
@@ -173,6 +178,8 @@ extern "C" int lsq_lnv_default_opts(lsq_lnv_opts *o) {
     o->precision = LSQ_F64;
     o->refine_iter = 2;
     o->spin = 2.0;
+    o->final_eval = 1;
+    o->verbose = 0;
     return LSQ_OK;
 }
 
@@ -222,7 +229,8 @@ extern "C" int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double 
     if ((rc = c->Hp.alloc(nvals(c, c->rH))) || (rc = c->Sh.alloc(nvals(c, c->rH))) ||
         (rc = c->G.alloc(nvals(c, c->rL))) || (rc = c->Gp.alloc(nvals(c, c->rL))) ||
         (rc = c->D.alloc(nvals(c, c->rL))) || (rc = c->LS.alloc(d * nvals(c, c->r1))) ||
-        (rc = c->LSL.alloc(d * nvals(c, c->r2))) || (rc = c->LSLSLH.alloc(d * nvals(c, c->rH))) ||
+        (rc = c->LSL.alloc(d * nvals(c, c->r3))) || (rc = c->SL.alloc(d * nvals(c, c->r1))) ||
+        (rc = c->QT.alloc(d * nvals(c, c->r3))) ||
         (rc = c->Q.alloc(d * nvals(c, c->r3))) || (rc = c->QD.alloc(d * nvals(c, c->r3))) ||
         (rc = c->G1.alloc(d * nvals(c, c->rL))) || (rc = c->G2.alloc(d * nvals(c, c->rL))) ||
         (rc = c->Lc.alloc(4 * nvals(c, c->rL))) || (rc = c->Dc.alloc(4 * nvals(c, c->rL))) ||
@@ -254,10 +262,10 @@ extern "C" int lsq_lnv_init_L(lsq_lnv c, const double *S, double *L, void *strea
     LSQ_TRY(bad.alloc(1));
     LSQ_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
     if (g->n > 0)
-        note_launch();
+        { note_launch();
         k_onsite_inverse<<<(g->n + 127) / 128, 128, 0, s>>>(
             g->n, c->b, g->pats[c->rS].row_ptr.p, g->pats[c->rS].col.p, S,
-            g->pats[c->rL].row_ptr.p, g->pats[c->rL].col.p, L, bad.p);
+            g->pats[c->rL].row_ptr.p, g->pats[c->rL].col.p, L, bad.p); }
     LSQ_CHECK_LAUNCH();
     int hbad = 0;
     LSQ_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -271,17 +279,17 @@ namespace {
 // Prepares H', S_H (float64) and the reduced-precision copies for 'prec'.
 int prepare_hs(lsq_lnv c, const double *S, const double *H, double mu, int prec, cudaStream_t s) {
     int64_t nh = nvals(c, c->rH);
-    note_launch();
+    { note_launch();
     k_hprime<<<grid_for(nh), 256, 0, s>>>(c->g->pats[c->rH].nnzb, c->b * c->b, H, S, c->pos_s_in_h,
-                                          mu, c->Hp.p, c->Sh.p);
+                                          mu, c->Hp.p, c->Sh.p); }
     if (prec == LSQ_F32) {
-        note_launch();
-        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Hp.p, (float *)c->Hpc.p);
-        note_launch();
-        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Sh.p, (float *)c->Shc.p);
+        { note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Hp.p, (float *)c->Hpc.p); }
+        { note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Sh.p, (float *)c->Shc.p); }
         int64_t ns = nvals(c, c->rS);
-        note_launch();
-        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p);
+        { note_launch();
+        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p); }
     }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
@@ -295,8 +303,8 @@ Ops operands(lsq_lnv c, const double *L, const double *S, int prec, cudaStream_t
     Ops o;
     if (prec == LSQ_F32) {
         int64_t nl = nvals(c, c->rL);
-        note_launch();
-        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p);
+        { note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p); }
         o.L = c->Lc.p;
         o.S = c->Sc.p;
         o.Hp = c->Hpc.p;
@@ -316,37 +324,45 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
+    // scalar slots: 0 = Tr[H' LSL], 1 = <LSL, Q>, 2 = Tr[S LSL], 3 = <LSL, SLS>
     LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 0, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 0, o.L, c->r2, c->LSL.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r2, 0, c->LSL.p, c->r1, 1, c->LS.p, c->rH, c->LSLSLH.p, 1.0, 0.0,
-                         nullptr, s));
-    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r2, c->LSL.p, 0, s));
-    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->rH, c->LSLSLH.p, 1, s));
-    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->r2, c->LSL.p, 2, s));
-    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->rH, c->LSLSLH.p, 3, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 0, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, c->LS.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, c->LSL.p, 0, s));
+    LSQ_TRY(dot_into(g, b, prec, c->r3, c->LSL.p, c->Q.p, 1, s));
+    if (ne) {
+        void *SLS = c->QD.p;
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, 0, c->LS.p, c->r3, SLS, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->r3, c->LSL.p, 2, s));
+        LSQ_TRY(dot_into(g, b, prec, c->r3, c->LSL.p, SLS, 3, s));
+    }
     if (G) {
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, c->LS.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, 0, c->LS.p, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->Q.p, c->r1, 0, c->LS.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s));
+        // G1 = Q.LS = Q.(SL)^T and G2 = Q^T.LS, with SL and Q^T materialised so both
+        // operands are read row by row
+        LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
+        LSQ_TRY(transpose_on(g, c->r3, b, prec, c->Q.p, c->QT.p, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, 1, c->SL.p, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->QT.p, c->r1, 1, c->SL.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s));
         const int64_t *pq = nullptr, *pqt = nullptr;
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
         int64_t nl = nvals(c, c->rL);
-        if (prec == LSQ_F64)
+        if (prec == LSQ_F64) {
             note_launch();
             k_grad_combine<double><<<grid_for(nl), 256, 0, s>>>(
                 g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const double *)c->Q.p,
                 (const double *)c->G1.p, (const double *)c->G2.p, G);
-        else
+        } else {
             note_launch();
             k_grad_combine<float><<<grid_for(nl), 256, 0, s>>>(
                 g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const float *)c->Q.p,
                 (const float *)c->G1.p, (const float *)c->G2.p, G);
+        }
         LSQ_CHECK_LAUNCH();
     }
     if (omega || ne) {
         double t[4];
-        LSQ_TRY(fetch_scalars(g, 4, t, s));
+        LSQ_TRY(fetch_scalars(g, ne ? 4 : 2, t, s));
         if (omega) *omega = spin * (3.0 * t[0] - 2.0 * t[1]);
         if (ne) *ne = spin * (3.0 * t[2] - 2.0 * t[3]);
     }
@@ -362,15 +378,17 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     const void *D = c->D.p;
     if (prec == LSQ_F32) {
         int64_t nl = nvals(c, c->rL);
-        note_launch();
-        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, c->D.p, (float *)c->Dc.p);
+        { note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, c->D.p, (float *)c->Dc.p); }
         D = c->Dc.p;
     }
-    void *P = c->LS.p, *F = c->LSL.p, *Z = c->G2.p;
+    void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
     LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, D, c->rS, 0, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
     LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 0, D, c->r3, F, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->QD.p, c->r1, 0, P, c->rL, Z, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(transpose_on(g, c->r1, b, prec, P, PT, s));
+    LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s));
     LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
     LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, F, 5, s));
     LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->Q.p, 6, s));
@@ -384,13 +402,23 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     return LSQ_OK;
 }
 
+// Step a > 0 along a descent direction (c1 < 0): the local minimum of the cubic,
+// a = -c1 / (c2 + sqrt(c2^2 - 3 c1 c3)); if the cubic has none but c2 > 0, the minimum of
+// its quadratic part, -c1 / (2 c2); otherwise no step (false).
 bool line_minimum(double c1, double c2, double c3, double *a) {
     double disc = c2 * c2 - 3.0 * c1 * c3;
-    if (!(disc >= 0.0)) return false;
-    double den = c2 + std::sqrt(disc);
-    if (!(den > 0.0)) return false;
-    *a = -c1 / den;
-    return std::isfinite(*a);
+    if (disc >= 0.0) {
+        double den = c2 + std::sqrt(disc);
+        if (den > 0.0) {
+            *a = -c1 / den;
+            return std::isfinite(*a);
+        }
+    }
+    if (c2 > 0.0) {
+        *a = -c1 / (2.0 * c2);
+        return std::isfinite(*a);
+    }
+    return false;
 }
 
 }  // namespace
@@ -435,6 +463,7 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
     int iters = 0, iters64 = 0;
     double last_d = 0.0;
     const int nphase = o.precision == LSQ_F32 ? 2 : 1;
+    double om_pred = 0.0, ne_last = std::nan("");
     for (int phase = 0; phase < nphase && status != LSQ_ERR_UNSTABLE; ++phase) {
         const int prec = phase == 0 ? o.precision : LSQ_F64;
         const int budget = phase == 0 ? o.max_iter : o.refine_iter;
@@ -454,32 +483,41 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
             }
             double beta = 0.0;
             if (it % o.cg_reset != 0 && gg_prev > 0.0) beta = std::max(0.0, (gg - ggp) / gg_prev);
-            note_launch();
-            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, c->G.p, c->D.p);
+            { note_launch();
+            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, c->G.p, c->D.p); }
             LSQ_CHECK_LAUNCH();
             double cc[3];
             LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
             if (cc[0] >= 0.0 && beta != 0.0) {  // not a descent direction: restart
-                note_launch();
-                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, c->G.p, c->D.p);
+                { note_launch();
+                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, c->G.p, c->D.p); }
                 LSQ_CHECK_LAUNCH();
                 LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
             }
             double a = 0.0;
             if (!(cc[0] < 0.0) || !line_minimum(cc[0], cc[1], cc[2], &a)) {
+                if (o.verbose)
+                    std::fprintf(stderr, "lnv step %d: no local minimum, c1 %.6e c2 %.6e c3 %.6e\n", iters,
+                                 cc[0], cc[1], cc[2]);
                 status = LSQ_ERR_UNSTABLE;
                 break;
             }
-            note_launch();
-            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L);
+            { note_launch();
+            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L); }
             LSQ_CHECK_LAUNCH();
             std::swap(c->G.p, c->Gp.p);
             gg_prev = gg;
             ++iters;
             if (prec == LSQ_F64) ++iters64;
             const double dom = cc[0] * a + cc[1] * a * a + cc[2] * a * a * a;
+            if (o.verbose)
+                std::fprintf(stderr,
+                             "lnv step %d %s omega %.12e eV |G|^2 %.6e c1 %.6e c2 %.6e c3 %.6e "
+                             "alpha %.6e beta %.6e\n",
+                             iters - 1, prec == LSQ_F64 ? "f64" : "f32", om, gg, cc[0], cc[1], cc[2], a,
+                             beta);
             last_d = std::fabs(dom) / kHartreeEv / std::max(n, 1);
-            (void)om;
+            om_pred = om + dom;
             if (o.tol_ha_per_atom > 0.0 && last_d < o.tol_ha_per_atom) {
                 converged = true;
                 break;
@@ -492,8 +530,8 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
                 status = LSQ_OK;
         }
     }
-    double om = 0, ne = 0;
-    LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, &om, &ne, s));
+    double om = om_pred, ne = ne_last;
+    if (o.final_eval) LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, &om, &ne, s));
     auto t1 = std::chrono::steady_clock::now();
     if (rep) {
         rep->iterations = iters;

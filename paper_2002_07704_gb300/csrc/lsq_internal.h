@@ -85,6 +85,22 @@ struct Plan {
     int64_t triples = 0;
 };
 
+// Symbolic product stored as a plan (see plan.cu).
+struct ProductPlan {
+    int64_t triples = 0;
+    int64_t ngroups = 0;
+    int64_t nitems = 0;
+    DevBuf<int32_t> g_row;
+    DevBuf<int64_t> g_first;
+    DevBuf<int32_t> g_nvalid;
+    DevBuf<int64_t> g_off;
+    DevBuf<int64_t> perm;
+    DevBuf<int32_t> cnt;
+    DevBuf<uint32_t> items;
+    ProductPlan() = default;
+    ProductPlan(ProductPlan &&) = default;
+};
+
 struct Reducer {
     DevBuf<double> partial;   // per-block partial sums
     DevBuf<double> scalars;   // result slots
@@ -107,6 +123,10 @@ struct lsq_geom_s {
     std::map<std::tuple<int, int, int, int, int, int, int>, lsq::Plan> plans;
     // key: (pattern p, pattern q, transposed): position in q of (i, j) or (j, i) for each entry of p
     std::map<std::tuple<int, int, int>, lsq::DevBuf<int64_t>> posmaps;
+    // product plans keyed by (range_a, range_b, range_c)
+    std::map<std::tuple<int, int, int>, lsq::ProductPlan> pplans;
+    // scratch for transposed operands of lsq_block_matmul (grown on demand)
+    lsq::DevBuf<char> scratch_a, scratch_x;
     lsq::Reducer red;
 };
 
@@ -122,6 +142,12 @@ int find_range(lsq_geom g, double R);
 int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
                  const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
                  cudaStream_t s);
+
+int plan_build(lsq_geom g, int ra, int rb, int rc, ProductPlan **out, cudaStream_t s);
+int plan_launch(lsq_geom g, int dtype, const ProductPlan &p, int ra, int rb, int rc, const void *Aop,
+                const void *X, void *C, double alpha, double beta, cudaStream_t s);
+// out = X^T on the (symmetric) pattern r: out_ij = (X_ji)^T.
+int transpose_on(lsq_geom g, int r, int b, int dtype, const void *X, void *out, cudaStream_t s);
 
 // Reductions into g->red.scalars[slot] (float64), enqueued on s.
 int trace_into(lsq_geom g, int b, int dtype, int rx, const void *X, int ry, const void *Y, int slot,

@@ -9,7 +9,8 @@
 //  * MODE_ROWS ("row Gustavson"): a persistent block owns one row i of C
 //    at a time, keeps a chunk of C_i's blocks in shared memory with a
 //    shared atom -> slot map, and streams, for every k of row i of A, the
-//    blocks B_kj of row k of B into the slots (shared-memory atomics).
+//    blocks B_kj of row k of B into the slots; each warp owns a disjoint
+//    range of slots, so the accumulation needs no atomics.
 //    Index work ~ sum_{k in A_i} |B_k|: ideal when C holds the natural
 //    range of the product (L.S, LS.L, H'.LS).
 //  * MODE_INNER: a block owns row i of C with an atom -> position map of
@@ -92,10 +93,34 @@ struct MMArgs {
 };
 
 // ---- MODE_ROWS, b = 4 --------------------------------------------------------
+// First position q in [q0, q1) of a sorted column list with col[q] >= key (whole warp, two
+// rounds of 32 probes for rows up to 1024 entries, repeated for longer rows).
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t *__restrict__ col, int64_t q0,
+                                                    int64_t q1, int key, int lane) {
+    while (q1 - q0 > 32) {
+        const int64_t len = q1 - q0;
+        const int64_t step = (len + 31) >> 5;
+        const int64_t last = q0 + min(len - 1, (int64_t)lane * step + step - 1);
+        const bool below = ((int64_t)lane * step < len) && col[last] < key;
+        const int nb = __popc(__ballot_sync(0xffffffffu, below));
+        const int64_t nq0 = q0 + nb * step;
+        q1 = min(q1, nq0 + step);
+        q0 = nq0;
+    }
+    const int64_t pos = q0 + lane;
+    const bool below = pos < q1 && col[pos] < key;
+    return q0 + __popc(__ballot_sync(0xffffffffu, below));
+}
+
+// A persistent block owns row i of C (in chunks of C's blocks kept in shared memory).  Warp w
+// owns a contiguous 1/nwarps share of the chunk's slots, i.e. a range [jlo, jhi] of atom
+// indices; it walks every k of row i of op(A) and, for each, the segment of row k of op(B)
+// inside its j-range, adding A_ik B_kj into its own slots.  Slots are private to a warp and
+// distinct within one k, so plain shared-memory read-modify-write suffices (no atomics).
 template <typename T, bool TA, bool TB, bool COUNT>
 __global__ void __launch_bounds__(512) k_mm_rows_b4(MMArgs g, int chunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *acc = reinterpret_cast<T *>(smem_raw);                       // [chunk][16]
+    T *acc = reinterpret_cast<T *>(smem_raw);                          // [chunk][16]
     short *map = reinterpret_cast<short *>(acc + (size_t)chunk * 16);  // [n]
     const T *__restrict__ A = static_cast<const T *>(g.A);
     const T *__restrict__ B = static_cast<const T *>(g.B);
@@ -113,35 +138,43 @@ __global__ void __launch_bounds__(512) k_mm_rows_b4(MMArgs g, int chunk) {
             for (int s = tid; s < nch; s += nth) map[g.c_col[s0 + s]] = (short)s;
             if (!COUNT)
                 for (int e = tid; e < nch * 16; e += nth) acc[e] = T(0);
-            const int jlo = g.c_col[s0], jhi = g.c_col[s0 + nch - 1];
             __syncthreads();
-            for (int64_t pa = a0 + warp; pa < a1; pa += nwarps) {
-                const int k = g.a_col[pa];
-                T a[16];
-                if (!COUNT) ld_blk_t<TA>(A + 16 * (TA ? g.a_tm[pa] : pa), a);
-                const int64_t q1 = g.b_ptr[k + 1];
-                for (int64_t q = g.b_ptr[k] + lane; q < q1; q += 32) {
-                    const int j = g.b_col[q];
-                    if (j < jlo || j > jhi) continue;
-                    const int slot = map[j];
-                    if (slot < 0) continue;
-                    if (COUNT) {
-                        ++cnt;
-                        continue;
-                    }
-                    T b[16];
-                    ld_blk_t<TB>(B + 16 * (TB ? g.b_tm[q] : q), b);
-                    T *dst = acc + 16 * slot;
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            T v = a[r * 4 + 0] * b[0 * 4 + c];
-                            v = fma(a[r * 4 + 1], b[1 * 4 + c], v);
-                            v = fma(a[r * 4 + 2], b[2 * 4 + c], v);
-                            v = fma(a[r * 4 + 3], b[3 * 4 + c], v);
-                            atomicAdd(dst + r * 4 + c, v);
+            const int lo = (int)(((int64_t)warp * nch) / nwarps);
+            const int hi = (int)(((int64_t)(warp + 1) * nch) / nwarps);
+            if (lo < hi) {
+                const int jlo = g.c_col[s0 + lo], jhi = g.c_col[s0 + hi - 1];
+                for (int64_t pa = a0; pa < a1; ++pa) {
+                    const int k = g.a_col[pa];
+                    const int64_t qb = g.b_ptr[k], qe = g.b_ptr[k + 1];
+                    const int64_t q0 = warp_lower_bound(g.b_col, qb, qe, jlo, lane);
+                    if (q0 >= qe || g.b_col[q0] > jhi) continue;
+                    T a[16];
+                    if (!COUNT) ld_blk_t<TA>(A + 16 * (TA ? g.a_tm[pa] : pa), a);
+                    for (int64_t q = q0 + lane; q < qe; q += 32) {
+                        const int j = g.b_col[q];
+                        if (j > jhi) break;
+                        const int slot = map[j];
+                        if (slot < 0) continue;
+                        if (COUNT) {
+                            ++cnt;
+                            continue;
                         }
+                        T b[16];
+                        ld_blk_t<TB>(B + 16 * (TB ? g.b_tm[q] : q), b);
+                        T *dst = acc + 16 * slot;
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                T v = dst[r * 4 + c];
+                                v = fma(a[r * 4 + 0], b[0 * 4 + c], v);
+                                v = fma(a[r * 4 + 1], b[1 * 4 + c], v);
+                                v = fma(a[r * 4 + 2], b[2 * 4 + c], v);
+                                v = fma(a[r * 4 + 3], b[3 * 4 + c], v);
+                                dst[r * 4 + c] = v;
+                            }
+                    }
+                    __syncwarp();
                 }
             }
             __syncthreads();
@@ -309,6 +342,39 @@ __global__ void __launch_bounds__(256) k_mm_inner_gen(MMArgs g, int b) {
     if (COUNT) warp_sum_u64<T>(cnt, g.triples);
 }
 
+// out_ij = (X_ji)^T on one symmetric pattern (tm = transpose map of the pattern).
+template <typename T>
+__global__ void k_transpose_pattern(int64_t nnzb, int b, const int64_t *__restrict__ tm,
+                                    const T *__restrict__ X, T *__restrict__ out) {
+    const int bb = b * b;
+    int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / bb;
+        int rc = (int)(e - p * bb);
+        int r = rc / b, c = rc - r * b;
+        out[e] = X[tm[p] * bb + c * b + r];
+    }
+}
+
+static int tgrid(int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 8192)); }
+
+// X^T on pattern r (materialised so that later products read it row by row).
+int transpose_on(lsq_geom g, int r, int b, int prec, const void *X, void *out,
+                        cudaStream_t s) {
+    LSQ_TRY(ensure_tmap(g, r, s));
+    int64_t m = g->pats[r].nnzb * b * b;
+    note_launch();
+    if (prec == LSQ_F64)
+        k_transpose_pattern<double><<<tgrid(m), 256, 0, s>>>(
+            g->pats[r].nnzb, b, g->pats[r].tmap.p, (const double *)X, (double *)out);
+    else
+        k_transpose_pattern<float><<<tgrid(m), 256, 0, s>>>(
+            g->pats[r].nnzb, b, g->pats[r].tmap.p, (const float *)X, (float *)out);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
 // ---- index-cost estimate of the two forms ---------------------------------
 __global__ void k_mm_cost(int n, const int64_t *__restrict__ a_ptr, const int32_t *__restrict__ a_col,
                           const int64_t *__restrict__ b_ptr, const int64_t *__restrict__ c_ptr,
@@ -364,24 +430,24 @@ static int launch_typed(lsq_geom g, int b, int mode, int chunk, const MMArgs &a,
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int threads = 512;
         int grid = occupancy_grid(g, kern, threads, smem);
-        note_launch();
-        kern<<<grid, threads, smem, s>>>(a, chunk);
+        { note_launch();
+        kern<<<grid, threads, smem, s>>>(a, chunk); }
     } else if (b == 4) {
         auto kern = k_mm_inner_b4<T, TA, TB, COUNT>;
         size_t smem = (size_t)g->n * sizeof(int);
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int threads = 512;
         int grid = occupancy_grid(g, kern, threads, smem);
-        note_launch();
-        kern<<<grid, threads, smem, s>>>(a);
+        { note_launch();
+        kern<<<grid, threads, smem, s>>>(a); }
     } else {
         auto kern = k_mm_inner_gen<T, TA, TB, COUNT>;
         size_t smem = (size_t)g->n * sizeof(int);
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int threads = 256;
         int grid = occupancy_grid(g, kern, threads, smem);
-        note_launch();
-        kern<<<grid, threads, smem, s>>>(a, b);
+        { note_launch();
+        kern<<<grid, threads, smem, s>>>(a, b); }
     }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
@@ -414,9 +480,9 @@ static int get_plan(lsq_geom g, int b, int dtype, int ra, int ta, int rb, int tb
     if (g->n > 0) {
         int threads = 256;
         int blocks = (int)(((int64_t)g->n * 32 + threads - 1) / threads);
-        note_launch();
+        { note_launch();
         k_mm_cost<<<blocks, threads, 0, s>>>(g->n, PA.row_ptr.p, PA.col.p, PB.row_ptr.p,
-                                             PC.row_ptr.p, PC.col.p, std::max(p.chunk, 1), cnt.p);
+                                             PC.row_ptr.p, PC.col.p, std::max(p.chunk, 1), cnt.p); }
         LSQ_CHECK_LAUNCH();
         LSQ_CUDA_TRY(cudaMemcpyAsync(h, cnt.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -472,6 +538,33 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     a.alpha = alpha;
     a.beta = beta;
     a.triples = nullptr;
+    if (b == 4) {
+        // plan-driven form: op(A) rows and op(B)^T rows, transposing into scratch if needed
+        ProductPlan *pp = nullptr;
+        int prc = plan_build(g, ra, rb, rc, &pp, s);
+        if (prc == LSQ_OK) {
+            if (triples) *triples = pp->triples;
+            if (g->n == 0 || g->pats[rc].nnzb == 0) return LSQ_OK;
+            const size_t es = 16 * dtype_size(dtype);
+            const void *Aop = A, *X = B;
+            if (ta) {
+                size_t need = es * (size_t)g->pats[ra].nnzb;
+                if (g->scratch_a.n < need) LSQ_TRY(g->scratch_a.alloc(need));
+                LSQ_TRY(transpose_on(g, ra, b, dtype, A, g->scratch_a.p, s));
+                Aop = g->scratch_a.p;
+            }
+            if (!tb) {
+                size_t need = es * (size_t)g->pats[rb].nnzb;
+                if (g->scratch_x.n < need) LSQ_TRY(g->scratch_x.alloc(need));
+                LSQ_TRY(transpose_on(g, rb, b, dtype, B, g->scratch_x.p, s));
+                X = g->scratch_x.p;
+            }
+            return plan_launch(g, dtype, *pp, ra, rb, rc, Aop, X, C, alpha, beta, s);
+        }
+        if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
+        (void)cudaGetLastError();  // a failed allocation is not sticky; drop it
+        clear_error();             // and fall back to the plan-free forms below
+    }
     Plan *p = nullptr;
     LSQ_TRY(get_plan(g, b, dtype, ra, ta, rb, tb, rc, a, &p, s));
     if (triples) *triples = p->triples;
@@ -555,15 +648,15 @@ int trace_into(lsq_geom g, int b, int dtype, int rx, const void *X, int ry, cons
     LSQ_TRY(get_posmap(g, rx, ry, 1, &pm, s));
     int64_t nnzb = g->pats[rx].nnzb;
     if (dtype == LSQ_F64)
-        note_launch();
+        { note_launch();
         k_trace<double><<<kRedBlocks, kRedThreads, 0, s>>>(nnzb, b, (const double *)X,
-                                                           (const double *)Y, pm, g->red.partial.p);
+                                                           (const double *)Y, pm, g->red.partial.p); }
     else
-        note_launch();
+        { note_launch();
         k_trace<float><<<kRedBlocks, kRedThreads, 0, s>>>(nnzb, b, (const float *)X,
-                                                          (const float *)Y, pm, g->red.partial.p);
-    note_launch();
-    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot);
+                                                          (const float *)Y, pm, g->red.partial.p); }
+    { note_launch();
+    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot); }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -573,15 +666,15 @@ int dot_into(lsq_geom g, int b, int dtype, int r, const void *X, const void *Y, 
     LSQ_TRY(reducer_ensure(g, slot + 1));
     int64_t total = g->pats[r].nnzb * b * b;
     if (dtype == LSQ_F64)
-        note_launch();
+        { note_launch();
         k_dot<double><<<kRedBlocks, kRedThreads, 0, s>>>(total, (const double *)X, (const double *)Y,
-                                                         g->red.partial.p);
+                                                         g->red.partial.p); }
     else
-        note_launch();
+        { note_launch();
         k_dot<float><<<kRedBlocks, kRedThreads, 0, s>>>(total, (const float *)X, (const float *)Y,
-                                                        g->red.partial.p);
-    note_launch();
-    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot);
+                                                        g->red.partial.p); }
+    { note_launch();
+    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot); }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }

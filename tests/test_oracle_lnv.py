@@ -171,5 +171,9 @@ def test_line_minimum_cases():
     c1, c2, c3 = -1.0, 0.5, -0.01
     a = OL.line_minimum(c1, c2, c3)
     assert abs(3 * c3 * a * a + 2 * c2 * a + c1) < 1e-12 and 6 * c3 * a + 2 * c2 > 0
-    # no local minimum (monotone decreasing cubic)
+    # no local minimum (monotone decreasing cubic) and negative curvature: no step
     assert OL.line_minimum(-1.0, -1.0, -1.0) is None
+    # no local minimum but positive curvature at 0: minimum of the quadratic part
+    c1, c2, c3 = -8.5e5, 1.0e8, -4.2e9
+    assert c2 * c2 - 3 * c1 * c3 < 0
+    assert np.isclose(OL.line_minimum(c1, c2, c3), -c1 / (2 * c2))
