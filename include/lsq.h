@@ -131,10 +131,18 @@ int lsq_block_matmul(lsq_geom g, int b, int precision,
                      int range_c, void *C_dev, double alpha, double beta,
                      int64_t *n_triples_host, void *stream);
 
+/* out = alpha X^T on pattern range_out: out_ij = alpha (X_ji)^T where (j, i)
+ * is stored in X's pattern, zero elsewhere (the adjoint of a trace and of a
+ * truncation, Sec. 2.3.2).  out must not alias X.  Enqueued on stream; the
+ * first call for a (range_x, range_out) pair builds a position map. */
+int lsq_transpose(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
+                  int range_out, void *out_dev, double alpha, void *stream);
+
 /* Tr[X Y] = sum over stored (i, j) of X, with (j, i) stored in Y, of
  * <X_ij, (Y_ji)^T>, accumulated in float64.  Synchronises the stream. */
 int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
               int range_y, const void *Y_dev, double *out_host, void *stream);
+
 
 /* ---- LNV grand-potential minimisation (Sec. 2.3.2, Eq. 8) ----------- */
 

@@ -364,6 +364,8 @@ extern "C" int lsq_build_neighbour_lists(const double *pos_dev, int n, const dou
     };
     g->n = n;
     g->n_ranges = nr;
+    g->n_sys = 1;
+    g->sys_atom_off = {0, (int64_t)n};
     for (int c = 0; c < 3; ++c) g->cell[c] = cell[c];
     if (cudaGetDevice(&g->device) != cudaSuccess) return fail(set_error(LSQ_ERR_CUDA, "no device"));
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
@@ -535,5 +537,117 @@ extern "C" int lsq_pattern_copy(lsq_geom g, int r, int64_t *row_ptr, int32_t *co
     if (g->pats[r].nnzb > 0)
         LSQ_CUDA_TRY(cudaMemcpyAsync(col, g->pats[r].col.p, sizeof(int32_t) * g->pats[r].nnzb,
                                      cudaMemcpyDeviceToDevice, s));
+    return LSQ_OK;
+}
+
+// ---- block-diagonal concatenation of independent systems --------------------
+namespace lsq {
+
+__global__ void k_concat_rows(int n, const int64_t *__restrict__ rp, int64_t row_off, int64_t nnz_off,
+                              int64_t *__restrict__ out_rp) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out_rp[row_off + i] = rp[i] + nnz_off;
+}
+
+__global__ void k_concat_cols(int64_t m, const int32_t *__restrict__ col, int atom_off,
+                              int32_t *__restrict__ out_col) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) out_col[e] = col[e] + atom_off;
+}
+
+__global__ void k_fill_sys(int n, int sys, int *__restrict__ atom_sys) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atom_sys[i] = sys;
+}
+
+}  // namespace lsq
+
+extern "C" int lsq_geom_concat(int n_sys, const lsq_geom *geoms, lsq_geom *out, void *stream) {
+    clear_error();
+    if (!out || !geoms || n_sys < 1) return set_error(LSQ_ERR_INVALID_ARG, "bad arguments");
+    *out = nullptr;
+    const int nr = geoms[0] ? geoms[0]->n_ranges : 0;
+    int64_t ntot = 0;
+    for (int k = 0; k < n_sys; ++k) {
+        if (!geoms[k]) return set_error(LSQ_ERR_INVALID_ARG, "null geometry in the list");
+        if (geoms[k]->n_ranges != nr)
+            return set_error(LSQ_ERR_INVALID_ARG, "all geometries must have the same ranges");
+        for (int r = 0; r < nr; ++r)
+            if (geoms[k]->pats[r].R != geoms[0]->pats[r].R)
+                return set_error(LSQ_ERR_INVALID_ARG, "all geometries must have the same ranges");
+        ntot += geoms[k]->n;
+    }
+    if (ntot > (1 << 30)) return set_error(LSQ_ERR_INVALID_ARG, "too many atoms");
+    cudaStream_t s = (cudaStream_t)stream;
+    lsq_geom g = new lsq_geom_s();
+    auto fail = [&](int rc) {
+        delete g;
+        return rc;
+    };
+    g->n = (int)ntot;
+    g->n_ranges = nr;
+    g->device = geoms[0]->device;
+    g->num_sms = geoms[0]->num_sms;
+    g->smem_optin = geoms[0]->smem_optin;
+    g->pats.resize(nr);
+    g->n_sys = n_sys;
+    g->sys_atom_off.assign((size_t)n_sys + 1, 0);
+    for (int k = 0; k < n_sys; ++k) g->sys_atom_off[k + 1] = g->sys_atom_off[k] + geoms[k]->n;
+    int rc;
+    if ((rc = g->atom_sys.alloc((size_t)std::max<int64_t>(ntot, 1)))) return fail(rc);
+    if ((rc = g->pos.alloc((size_t)3 * std::max<int64_t>(ntot, 1)))) return fail(rc);
+    for (int k = 0; k < n_sys; ++k) {
+        const int nk = geoms[k]->n;
+        if (nk == 0) continue;
+        note_launch();
+        k_fill_sys<<<(nk + 255) / 256, 256, 0, s>>>(nk, k, g->atom_sys.p + g->sys_atom_off[k]);
+        cudaMemcpyAsync(g->pos.p + 3 * g->sys_atom_off[k], geoms[k]->pos.p, sizeof(double) * 3 * nk,
+                        cudaMemcpyDeviceToDevice, s);
+    }
+    for (int r = 0; r < nr; ++r) {
+        Pattern &P = g->pats[r];
+        P.R = geoms[0]->pats[r].R;
+        int64_t nnz = 0;
+        int mr = 0;
+        for (int k = 0; k < n_sys; ++k) {
+            nnz += geoms[k]->pats[r].nnzb;
+            mr = std::max(mr, geoms[k]->pats[r].max_row);
+        }
+        P.nnzb = nnz;
+        P.max_row = mr;
+        if ((rc = P.row_ptr.alloc((size_t)ntot + 1)) || (rc = P.col.alloc((size_t)std::max<int64_t>(nnz, 1))))
+            return fail(rc);
+        int64_t off = 0;
+        for (int k = 0; k < n_sys; ++k) {
+            const Pattern &Q = geoms[k]->pats[r];
+            const int nk = geoms[k]->n;
+            if (nk > 0) {
+                note_launch();
+                k_concat_rows<<<(nk + 255) / 256, 256, 0, s>>>(nk, Q.row_ptr.p, g->sys_atom_off[k], off,
+                                                               P.row_ptr.p);
+            }
+            if (Q.nnzb > 0) {
+                note_launch();
+                k_concat_cols<<<(int)((Q.nnzb + 255) / 256), 256, 0, s>>>(Q.nnzb, Q.col.p,
+                                                                          (int)g->sys_atom_off[k],
+                                                                          P.col.p + off);
+            }
+            off += Q.nnzb;
+        }
+        cudaMemcpyAsync(P.row_ptr.p + ntot, &P.nnzb, sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(set_error(LSQ_ERR_CUDA, cudaGetErrorString(e)));
+    if ((rc = reducer_ensure(g, 16))) return fail(rc);
+    *out = g;
+    return LSQ_OK;
+}
+
+extern "C" int lsq_geom_systems(lsq_geom g, int *n_sys, int64_t *atom_off_host) {
+    clear_error();
+    if (!g) return set_error(LSQ_ERR_INVALID_ARG, "null geometry handle");
+    if (n_sys) *n_sys = g->n_sys;
+    if (atom_off_host)
+        for (int k = 0; k <= g->n_sys; ++k) atom_off_host[k] = g->sys_atom_off[k];
     return LSQ_OK;
 }

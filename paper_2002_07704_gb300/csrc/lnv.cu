@@ -325,24 +325,24 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
     // scalar slots: 0 = Tr[H' LSL], 1 = <LSL, Q>, 2 = Tr[S LSL], 3 = <LSL, SLS>
-    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 0, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 0, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, c->LS.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 1, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
+    LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, c->SL.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
     LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, c->LSL.p, 0, s));
     LSQ_TRY(dot_into(g, b, prec, c->r3, c->LSL.p, c->Q.p, 1, s));
     if (ne) {
         void *SLS = c->QD.p;
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, 0, c->LS.p, c->r3, SLS, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, 1, c->SL.p, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
         LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->r3, c->LSL.p, 2, s));
         LSQ_TRY(dot_into(g, b, prec, c->r3, c->LSL.p, SLS, 3, s));
     }
     if (G) {
         // G1 = Q.LS = Q.(SL)^T and G2 = Q^T.LS, with SL and Q^T materialised so both
         // operands are read row by row
-        LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
         LSQ_TRY(transpose_on(g, c->r3, b, prec, c->Q.p, c->QT.p, s));
         LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, 1, c->SL.p, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->QT.p, c->r1, 1, c->SL.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->QT.p, c->r1, 1, c->SL.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 1));
         const int64_t *pq = nullptr, *pqt = nullptr;
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
@@ -383,12 +383,12 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
         D = c->Dc.p;
     }
     void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
-    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, D, c->rS, 0, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 0, D, c->r3, F, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
     LSQ_TRY(transpose_on(g, c->r1, b, prec, P, PT, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, PT, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
     LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
     LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
     LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, F, 5, s));
     LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->Q.p, 6, s));

@@ -87,15 +87,16 @@ struct Plan {
 
 // Symbolic product stored as a plan (see plan.cu).
 struct ProductPlan {
-    int64_t triples = 0;
-    int64_t ngroups = 0;
+    int64_t triples = 0;   // block triples the plan executes
+    int64_t nblocks = 0;
     int64_t nitems = 0;
-    DevBuf<int32_t> g_row;
-    DevBuf<int64_t> g_first;
-    DevBuf<int32_t> g_nvalid;
-    DevBuf<int64_t> g_off;
-    DevBuf<int64_t> perm;
-    DevBuf<int32_t> cnt;
+    int upper = 0;         // only blocks with j >= i are computed; the rest mirrored
+    int variant[2] = {-1, -1};      // kernel schedule picked by the autotuner (f64, f32)
+    float tuned_ms[2] = {0.f, 0.f};
+    DevBuf<int64_t> perm;      // blocks of C in processing order (sorted by list length per row)
+    DevBuf<int32_t> cnt;       // list length per block of C
+    DevBuf<int64_t> item_ptr;  // [nblocks + 1] start of each block's list
+    DevBuf<int64_t> c_row;     // row of each block of C
     DevBuf<uint32_t> items;
     ProductPlan() = default;
     ProductPlan(ProductPlan &&) = default;
@@ -119,6 +120,10 @@ struct lsq_geom_s {
     size_t smem_optin = 0;
     lsq::DevBuf<double> pos;
     std::vector<lsq::Pattern> pats;
+    // independent systems held block-diagonally (1 for an ordinary geometry)
+    int n_sys = 1;
+    std::vector<int64_t> sys_atom_off;   // [n_sys + 1] first atom of each system
+    lsq::DevBuf<int32_t> atom_sys;       // [n] system of each atom (batched geometries only)
     // key: (range_a, trans_a, range_b, trans_b, range_c, b, dtype)
     std::map<std::tuple<int, int, int, int, int, int, int>, lsq::Plan> plans;
     // key: (pattern p, pattern q, transposed): position in q of (i, j) or (j, i) for each entry of p
@@ -138,12 +143,14 @@ int ensure_tmap(lsq_geom g, int r, cudaStream_t s);
 int get_posmap(lsq_geom g, int p, int q, int transposed, const int64_t **out, cudaStream_t s);
 int find_range(lsq_geom g, double R);
 
-// Truncated product C = alpha op(A) op(B) + beta C (see lsq_block_matmul).
+// Truncated product C = alpha op(A) op(B) + beta C (see lsq_block_matmul).  sym != 0
+// declares the result symmetric (C = C^T in exact arithmetic): only blocks with j >= i
+// are computed and the others are their transposes.
 int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
                  const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
-                 cudaStream_t s);
+                 cudaStream_t s, int sym = 0);
 
-int plan_build(lsq_geom g, int ra, int rb, int rc, ProductPlan **out, cudaStream_t s);
+int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out, cudaStream_t s);
 int plan_launch(lsq_geom g, int dtype, const ProductPlan &p, int ra, int rb, int rc, const void *Aop,
                 const void *X, void *C, double alpha, double beta, cudaStream_t s);
 // out = X^T on the (symmetric) pattern r: out_ij = (X_ji)^T.

@@ -510,7 +510,7 @@ static int get_plan(lsq_geom g, int b, int dtype, int ra, int ta, int rb, int tb
 
 int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
                  const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
-                 cudaStream_t s) {
+                 cudaStream_t s, int sym) {
     LSQ_TRY(geom_check(g, ra));
     LSQ_TRY(geom_check(g, rb));
     LSQ_TRY(geom_check(g, rc));
@@ -541,7 +541,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     if (b == 4) {
         // plan-driven form: op(A) rows and op(B)^T rows, transposing into scratch if needed
         ProductPlan *pp = nullptr;
-        int prc = plan_build(g, ra, rb, rc, &pp, s);
+        int prc = plan_build(g, ra, rb, rc, (sym && beta == 0.0) ? 1 : 0, &pp, s);
         if (prc == LSQ_OK) {
             if (triples) *triples = pp->triples;
             if (g->n == 0 || g->pats[rc].nnzb == 0) return LSQ_OK;
@@ -711,4 +711,50 @@ extern "C" int lsq_trace(lsq_geom g, int b, int precision, int range_x, const vo
     cudaStream_t s = (cudaStream_t)stream;
     LSQ_TRY(trace_into(g, b, precision, range_x, X, range_y, Y, 0, s));
     return fetch_scalars(g, 1, out, s);
+}
+
+namespace lsq {
+
+// out_ij = alpha (X_ji)^T where (j, i) is stored in X's pattern, else 0 (pm: transposed posmap).
+template <typename T>
+__global__ void k_transpose_into(int64_t nnzb, int b, const int64_t *__restrict__ pm, T alpha,
+                                 const T *__restrict__ X, T *__restrict__ out) {
+    const int bb = b * b;
+    const int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        const int r = rc / b, c = rc - r * b;
+        const int64_t q = pm[p];
+        out[e] = q >= 0 ? alpha * X[q * bb + c * b + r] : T(0);
+    }
+}
+
+}  // namespace lsq
+
+extern "C" int lsq_transpose(lsq_geom g, int b, int precision, int range_x, const void *X,
+                             int range_out, void *out, double alpha, void *stream) {
+    clear_error();
+    LSQ_TRY(geom_check(g, range_x));
+    LSQ_TRY(geom_check(g, range_out));
+    if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
+    if (precision != LSQ_F64 && precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    if (g->n > 0 && (!X || !out)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
+    if (X == out) return set_error(LSQ_ERR_INVALID_ARG, "out must not alias X");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t *pm = nullptr;
+    LSQ_TRY(get_posmap(g, range_out, range_x, 1, &pm, s));
+    const int64_t nnzb = g->pats[range_out].nnzb;
+    if (nnzb == 0) return LSQ_OK;
+    note_launch();
+    if (precision == LSQ_F64)
+        k_transpose_into<double><<<tgrid(nnzb * b * b), 256, 0, s>>>(nnzb, b, pm, alpha,
+                                                                      (const double *)X, (double *)out);
+    else
+        k_transpose_into<float><<<tgrid(nnzb * b * b), 256, 0, s>>>(nnzb, b, pm, (float)alpha,
+                                                                     (const float *)X, (float *)out);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
 }

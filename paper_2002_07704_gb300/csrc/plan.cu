@@ -10,13 +10,15 @@
 //   A_ik = A[a_ptr[i] + ao] and B_kj = (X_jk)^T, X_jk = X[x_ptr[j] + xe],
 //   where X = B^T lives on B's (symmetric) pattern.
 //
-// Blocks of C are grouped 32 to a warp within a row of C, sorted by list
-// length so that the lanes of a warp run lists of similar length; the
-// items of a group are interleaved (item t of lane l at off + 32 t + l) so
-// that each step of the warp reads 128 contiguous bytes of plan.  The
-// numeric kernel then does no index search at all: each lane streams its
-// list, gathers A_ik from row i (shared by the warp, cache resident) and
-// X_jk from row j, and accumulates C_ij in registers.
+// The lists are stored back to back in the order of C's blocks (CSR over
+// blocks of C).  The numeric kernel gives each block of C to a team of 16
+// lanes, lane (r, c) owning C_ij[r][c]: per item it reads row r of A_ik
+// and row c of X_jk (16 bytes each, the four lanes that share a row read
+// the same 64-byte block), so every load instruction of a team touches
+// one block of A and one of X.  All teams of a thread block work on the
+// same row i of C, so row i of A is reused from L1; they take the row's
+// blocks in an order sorted by list length, so the two teams of a warp
+// run lists of similar length.  No index search is left in the kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(512) k_plan_count(int n, const int64_t *__rest
                                                     const int32_t *__restrict__ x_col,
                                                     const int64_t *__restrict__ c_ptr,
                                                     const int32_t *__restrict__ c_col,
-                                                    int32_t *__restrict__ cnt) {
+                                                    int upper, int32_t *__restrict__ cnt) {
     extern __shared__ int amap[];  // [n]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
@@ -49,7 +51,8 @@ __global__ void __launch_bounds__(512) k_plan_count(int n, const int64_t *__rest
         for (int64_t s = c_ptr[i] + warp; s < c_ptr[i + 1]; s += nwarps) {
             const int j = c_col[s];
             int c = 0;
-            for (int64_t q = x_ptr[j] + lane; q < x_ptr[j + 1]; q += 32) c += amap[x_col[q]] >= 0;
+            if (!upper || j >= i)
+                for (int64_t q = x_ptr[j] + lane; q < x_ptr[j + 1]; q += 32) c += amap[x_col[q]] >= 0;
             for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
             if (lane == 0) cnt[s] = c;
         }
@@ -95,31 +98,8 @@ __global__ void __launch_bounds__(512) k_plan_sort(int n, const int64_t *__restr
     }
 }
 
-// ---- groups of 32 blocks: row, first index, lanes in use, longest list ------------
-__global__ void k_plan_groups(int n, const int64_t *__restrict__ c_ptr,
-                              const int64_t *__restrict__ gbase, const int64_t *__restrict__ perm,
-                              const int32_t *__restrict__ cnt, int32_t *__restrict__ g_row,
-                              int64_t *__restrict__ g_first, int32_t *__restrict__ g_nvalid,
-                              int64_t *__restrict__ g_size) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t c0 = c_ptr[i], len = c_ptr[i + 1] - c0;
-    int64_t g = gbase[i];
-    for (int64_t f = 0; f < len; f += 32, ++g) {
-        g_row[g] = i;
-        g_first[g] = c0 + f;
-        g_nvalid[g] = (int)min((int64_t)32, len - f);
-        g_size[g] = 32 * (int64_t)cnt[perm[c0 + f]];  // sorted: the first block has the longest list
-    }
-}
-
-__global__ void k_rows_to_groups(int n, const int64_t *__restrict__ c_ptr, int64_t *__restrict__ ng) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) ng[i] = (c_ptr[i + 1] - c_ptr[i] + 31) / 32;
-}
-
-// Exclusive scan of int64 (one block).
-__global__ void k_scan64(int64_t m, const int64_t *__restrict__ in, int64_t *__restrict__ out) {
+// Exclusive scan of int32 counts into int64 offsets (one block).
+__global__ void k_scan_cnt(int64_t m, const int32_t *__restrict__ in, int64_t *__restrict__ out) {
     __shared__ int64_t part[1024];
     int t = threadIdx.x, nt = blockDim.x;
     int64_t seg = (m + nt - 1) / nt;
@@ -146,17 +126,14 @@ __global__ void k_scan64(int64_t m, const int64_t *__restrict__ in, int64_t *__r
     if (m == 0 && t == 0) out[0] = 0;
 }
 
-// ---- fill the interleaved items ------------------------------------------------
+// ---- fill the item lists (one warp per block of C, ordered compaction) ---------
 __global__ void __launch_bounds__(512) k_plan_fill(int n, const int64_t *__restrict__ a_ptr,
                                                    const int32_t *__restrict__ a_col,
                                                    const int64_t *__restrict__ x_ptr,
                                                    const int32_t *__restrict__ x_col,
+                                                   const int64_t *__restrict__ c_ptr,
                                                    const int32_t *__restrict__ c_col,
-                                                   const int64_t *__restrict__ gbase,
-                                                   const int64_t *__restrict__ g_first,
-                                                   const int32_t *__restrict__ g_nvalid,
-                                                   const int64_t *__restrict__ g_off,
-                                                   const int64_t *__restrict__ perm,
+                                                   const int64_t *__restrict__ item_ptr, int upper,
                                                    uint32_t *__restrict__ items) {
     extern __shared__ int amap[];
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -167,19 +144,18 @@ __global__ void __launch_bounds__(512) k_plan_fill(int n, const int64_t *__restr
         const int64_t a0 = a_ptr[i], a1 = a_ptr[i + 1];
         for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = (int)(p - a0);
         __syncthreads();
-        for (int64_t g = gbase[i] + warp; g < gbase[i + 1]; g += nwarps) {
-            if (lane < g_nvalid[g]) {
-                const int64_t s = perm[g_first[g] + lane];
-                const int j = c_col[s];
-                const int64_t x0 = x_ptr[j];
-                int64_t w = g_off[g] + lane;
-                for (int64_t q = x0; q < x_ptr[j + 1]; ++q) {
-                    const int ao = amap[x_col[q]];
-                    if (ao >= 0) {
-                        items[w] = (uint32_t)ao | ((uint32_t)(q - x0) << 16);
-                        w += 32;
-                    }
-                }
+        for (int64_t s = c_ptr[i] + warp; s < c_ptr[i + 1]; s += nwarps) {
+            const int j = c_col[s];
+            if (upper && j < i) continue;
+            const int64_t x0 = x_ptr[j], x1 = x_ptr[j + 1];
+            int64_t w = item_ptr[s];
+            for (int64_t qb = x0; qb < x1; qb += 32) {
+                const int64_t q = qb + lane;
+                const int ao = q < x1 ? amap[x_col[q]] : -1;
+                const unsigned m = __ballot_sync(0xffffffffu, ao >= 0);
+                if (ao >= 0)
+                    items[w + __popc(m & ((1u << lane) - 1u))] = (uint32_t)ao | ((uint32_t)(q - x0) << 16);
+                w += __popc(m);
             }
         }
         __syncthreads();
@@ -189,38 +165,32 @@ __global__ void __launch_bounds__(512) k_plan_fill(int n, const int64_t *__restr
 }
 
 // ---- numeric product from a plan -------------------------------------------------
-__device__ __forceinline__ void ldb(const double *__restrict__ p, double (&x)[16]) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        double2 v = __ldg(q + k);
-        x[2 * k] = v.x;
-        x[2 * k + 1] = v.y;
+template <typename T> struct Row4;
+template <> struct Row4<float> {
+    static __device__ __forceinline__ void load(const float *__restrict__ p, float (&v)[4]) {
+        float4 x = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
     }
-}
-__device__ __forceinline__ void ldb(const float *__restrict__ p, float (&x)[16]) {
-    const float4 *q = reinterpret_cast<const float4 *>(p);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float4 v = __ldg(q + k);
-        x[4 * k] = v.x;
-        x[4 * k + 1] = v.y;
-        x[4 * k + 2] = v.z;
-        x[4 * k + 3] = v.w;
+};
+template <> struct Row4<double> {
+    static __device__ __forceinline__ void load(const double *__restrict__ p, double (&v)[4]) {
+        double2 x = __ldg(reinterpret_cast<const double2 *>(p));
+        double2 y = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
     }
-}
+};
 
 struct PlanArgs {
-    int64_t ngroups;
-    const int32_t *g_row;
-    const int64_t *g_first;
-    const int32_t *g_nvalid;
-    const int64_t *g_off;
-    const int64_t *perm;
-    const int32_t *cnt;
+    int n;                      // atoms (rows)
+    int upper;                  // compute only blocks with j >= i
+    const int64_t *c_ptr;       // row pointers of C
+    int64_t nblocks;            // blocks of C
+    const int64_t *perm;        // blocks of C in processing order
+    const int64_t *item_ptr;    // [nblocks + 1]
     const uint32_t *items;
     const int64_t *a_ptr;
     const int64_t *x_ptr;
+    const int64_t *c_row;       // row of each block of C
     const int32_t *c_col;
     const void *A;  // op(A), rows contiguous
     const void *X;  // op(B)^T, rows contiguous
@@ -228,62 +198,118 @@ struct PlanArgs {
     double alpha, beta;
 };
 
-// One warp per group of 32 blocks of one row of C; lane l owns block perm[first + l].
+// Accumulates the items [q0, q1) of one block of C into acc (lane (r, c) of a 16-lane team).
+// UNROLL items are fetched before any of their blocks is used, so each lane keeps
+// 2 * UNROLL independent 16-byte loads in flight.
+template <typename T, int UNROLL>
+__device__ __forceinline__ T plan_items(const uint32_t *__restrict__ it, int nit,
+                                        const T *__restrict__ arow, const T *__restrict__ xrow) {
+    T acc[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) acc[u] = T(0);
+    int q = 0;
+    for (; q + UNROLL <= nit; q += UNROLL) {
+        uint32_t w[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) w[u] = __ldg(it + q + u);
+        T a[UNROLL][4], x[UNROLL][4];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            Row4<T>::load(arow + 16 * (w[u] & 0xffffu), a[u]);
+            Row4<T>::load(xrow + 16 * (w[u] >> 16), x[u]);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) acc[u] = fma(a[u][t], x[u][t], acc[u]);
+    }
+    for (; q < nit; ++q) {
+        const uint32_t w0 = __ldg(it + q);
+        T a0[4], x0[4];
+        Row4<T>::load(arow + 16 * (w0 & 0xffffu), a0);
+        Row4<T>::load(xrow + 16 * (w0 >> 16), x0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc[0] = fma(a0[t], x0[t], acc[0]);
+    }
+    T v = acc[0];
+#pragma unroll
+    for (int u = 1; u < UNROLL; ++u) v += acc[u];
+    return v;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_mm_plan_b4(PlanArgs g) {
+__device__ __forceinline__ void plan_store(const PlanArgs &g, T *__restrict__ C, int64_t s, int sub, T v) {
+    T *dst = C + 16 * s + sub;
+    v = (T)g.alpha * v;
+    *dst = g.beta != 0.0 ? fma((T)g.beta, *dst, v) : v;
+}
+
+// Two schedules of the same work (the plan's autotuner picks one per product):
+//  ROWS = false: teams take blocks of C in the plan's order across the whole grid;
+//  ROWS = true:  a thread block works on one row i of C at a time, so the row i of A it
+//                reads stays in L1, and its teams share out that row's blocks.
+// In both, a team of 16 lanes owns one block (i, j) of C, lane (r, c) accumulating
+// C_ij[r][c] = sum over items of sum_t A_ik[r][t] X_jk[c][t]   (B_kj = X_jk^T).
+template <typename T, bool ROWS, int UNROLL>
+__global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4(PlanArgs g) {
     const T *__restrict__ A = static_cast<const T *>(g.A);
     const T *__restrict__ X = static_cast<const T *>(g.X);
     T *__restrict__ C = static_cast<T *>(g.C);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t gi = warp0; gi < g.ngroups; gi += nw) {
-        const bool valid = lane < g.g_nvalid[gi];
-        if (!valid) continue;
-        const int64_t s = g.perm[g.g_first[gi] + lane];
-        const int j = g.c_col[s];
-        const T *__restrict__ arow = A + 16 * g.a_ptr[g.g_row[gi]];
-        const T *__restrict__ xrow = X + 16 * g.x_ptr[j];
-        const uint32_t *__restrict__ it = g.items + g.g_off[gi] + lane;
-        const int nit = g.cnt[s];
-        T acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = T(0);
-        uint32_t cur = nit > 0 ? __ldg(it) : 0u;
-        for (int t = 0; t < nit; ++t) {
-            const uint32_t nxt = (t + 1 < nit) ? __ldg(it + 32 * (t + 1)) : 0u;
-            T a[16], x[16];
-            ldb(arow + 16 * (cur & 0xffffu), a);
-            ldb(xrow + 16 * (cur >> 16), x);
-            // B_kj = (X_jk)^T:  acc[r][c] += sum_t a[r][t] x[c][t]
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    T v = acc[r * 4 + c];
-                    v = fma(a[r * 4 + 0], x[c * 4 + 0], v);
-                    v = fma(a[r * 4 + 1], x[c * 4 + 1], v);
-                    v = fma(a[r * 4 + 2], x[c * 4 + 2], v);
-                    v = fma(a[r * 4 + 3], x[c * 4 + 3], v);
-                    acc[r * 4 + c] = v;
-                }
-            cur = nxt;
+    const int sub = threadIdx.x & 15;
+    const int r = sub >> 2, c = sub & 3;
+    if (ROWS) {
+        const int team = threadIdx.x >> 4, nteams = blockDim.x >> 4;
+        for (int i = blockIdx.x; i < g.n; i += gridDim.x) {
+            const T *__restrict__ arow = A + 16 * g.a_ptr[i] + 4 * r;
+            for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
+                const int64_t s = g.perm[e];
+                if (g.upper && g.c_col[s] < i) continue;  // lower block: mirrored afterwards
+                const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
+                const int64_t i0 = g.item_ptr[s];
+                const T v = plan_items<T, UNROLL>(g.items + i0, (int)(g.item_ptr[s + 1] - i0), arow, xrow);
+                plan_store(g, C, s, sub, v);
+            }
         }
-        T *dst = C + 16 * s;
-        if (g.beta != 0.0) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) dst[e] = fma((T)g.beta, dst[e], (T)g.alpha * acc[e]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) dst[e] = (T)g.alpha * acc[e];
+    } else {
+        const int64_t team0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+        const int64_t nteams = ((int64_t)gridDim.x * blockDim.x) >> 4;
+        for (int64_t t = team0; t < g.nblocks; t += nteams) {
+            const int64_t s = g.perm[t];
+            const int i = (int)g.c_row[s];
+            if (g.upper && g.c_col[s] < i) continue;
+            const T *__restrict__ arow = A + 16 * g.a_ptr[i] + 4 * r;
+            const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
+            const int64_t i0 = g.item_ptr[s];
+            const T v = plan_items<T, UNROLL>(g.items + i0, (int)(g.item_ptr[s + 1] - i0), arow, xrow);
+            plan_store(g, C, s, sub, v);
         }
     }
 }
 
-static int grid64(int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 65535)); }
+// Lower blocks of a symmetric result: C_ij = (C_ji)^T for j < i (tm: transpose map of C's pattern).
+template <typename T>
+__global__ void k_mirror_lower(int n, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
+                               const int64_t *__restrict__ tm, T *__restrict__ C) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int i = warp;
+    for (int64_t e = c_ptr[i] * 16 + lane; e < c_ptr[i + 1] * 16; e += 32) {
+        const int64_t p = e >> 4;
+        const int rc = (int)(e & 15);
+        if (c_col[p] >= i) continue;
+        C[e] = C[tm[p] * 16 + (rc & 3) * 4 + (rc >> 2)];
+    }
+}
 
-int plan_build(lsq_geom g, int ra, int rb, int rc, ProductPlan **out, cudaStream_t s) {
-    auto key = std::make_tuple(ra, rb, rc);
+__global__ void k_rows_of(int n, const int64_t *__restrict__ c_ptr, int64_t *__restrict__ c_row) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t s = c_ptr[i]; s < c_ptr[i + 1]; ++s) c_row[s] = i;
+}
+
+int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out, cudaStream_t s) {
+    auto key = std::make_tuple(ra, rb, rc + (upper ? 1000 : 0));
     auto it = g->pplans.find(key);
     if (it != g->pplans.end()) {
         *out = &it->second;
@@ -297,22 +323,21 @@ int plan_build(lsq_geom g, int ra, int rb, int rc, ProductPlan **out, cudaStream
         return set_error(LSQ_ERR_UNSUPPORTED, "too many atoms for the shared-memory atom map");
     ProductPlan p;
     const int64_t nc = PC.nnzb;
-    DevBuf<int64_t> ng, gbase, gsize;
     LSQ_TRY(p.cnt.alloc(nc));
     LSQ_TRY(p.perm.alloc(nc));
-    LSQ_TRY(ng.alloc((size_t)n + 1));
-    LSQ_TRY(gbase.alloc((size_t)n + 1));
+    LSQ_TRY(p.item_ptr.alloc((size_t)nc + 1));
+    LSQ_TRY(p.c_row.alloc(nc));
     int per_sm = 1;
     size_t smem_map = (size_t)n * sizeof(int);
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_plan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_map));
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_plan_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_map));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_count, 512, smem_map);
     const int grid_rows = std::max(1, std::min(n, g->num_sms * std::max(per_sm, 1)));
-    if (n > 0) {
+    int64_t nitems = 0;
+    if (n > 0 && nc > 0) {
         note_launch();
         k_plan_count<<<grid_rows, 512, smem_map, s>>>(n, PA.row_ptr.p, PA.col.p, PB.row_ptr.p, PB.col.p,
-                                                      PC.row_ptr.p, PC.col.p, p.cnt.p);
-        LSQ_CHECK_LAUNCH();
+                                                      PC.row_ptr.p, PC.col.p, upper, p.cnt.p);
         int m = 1;
         while (m < PC.max_row) m <<= 1;
         size_t smem_sort = sizeof(unsigned long long) * (size_t)std::max(m, 1);
@@ -320,87 +345,130 @@ int plan_build(lsq_geom g, int ra, int rb, int rc, ProductPlan **out, cudaStream
         note_launch();
         k_plan_sort<<<std::min(n, g->num_sms * 2), 512, smem_sort, s>>>(n, PC.row_ptr.p, p.cnt.p, p.perm.p);
         note_launch();
-        k_rows_to_groups<<<(n + 255) / 256, 256, 0, s>>>(n, PC.row_ptr.p, ng.p);
+        k_scan_cnt<<<1, 1024, 0, s>>>(nc, p.cnt.p, p.item_ptr.p);
         note_launch();
-        k_scan64<<<1, 1024, 0, s>>>(n, ng.p, gbase.p);
+        k_rows_of<<<(n + 255) / 256, 256, 0, s>>>(n, PC.row_ptr.p, p.c_row.p);
         LSQ_CHECK_LAUNCH();
-    }
-    int64_t ngroups = 0;
-    if (n > 0) {
-        LSQ_CUDA_TRY(cudaMemcpyAsync(&ngroups, gbase.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(&nitems, p.item_ptr.p + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    p.ngroups = ngroups;
-    LSQ_TRY(p.g_row.alloc(ngroups));
-    LSQ_TRY(p.g_first.alloc(ngroups));
-    LSQ_TRY(p.g_nvalid.alloc(ngroups));
-    LSQ_TRY(p.g_off.alloc((size_t)ngroups + 1));
-    LSQ_TRY(gsize.alloc(ngroups));
-    int64_t nitems = 0;
-    if (ngroups > 0) {
-        note_launch();
-        k_plan_groups<<<(n + 255) / 256, 256, 0, s>>>(n, PC.row_ptr.p, gbase.p, p.perm.p, p.cnt.p, p.g_row.p,
-                                                      p.g_first.p, p.g_nvalid.p, gsize.p);
-        note_launch();
-        k_scan64<<<1, 1024, 0, s>>>(ngroups, gsize.p, p.g_off.p);
-        LSQ_CHECK_LAUNCH();
-        LSQ_CUDA_TRY(cudaMemcpyAsync(&nitems, p.g_off.p + ngroups, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    } else if (nc >= 0) {
+        LSQ_CUDA_TRY(cudaMemsetAsync(p.item_ptr.p, 0, sizeof(int64_t) * (nc + 1), s));
     }
     LSQ_TRY(p.items.alloc((size_t)std::max<int64_t>(nitems, 1)));
-    if (ngroups > 0) {
+    if (nitems > 0) {
         note_launch();
         k_plan_fill<<<grid_rows, 512, smem_map, s>>>(n, PA.row_ptr.p, PA.col.p, PB.row_ptr.p, PB.col.p,
-                                                     PC.col.p, gbase.p, p.g_first.p, p.g_nvalid.p,
-                                                     p.g_off.p, p.perm.p, p.items.p);
+                                                     PC.row_ptr.p, PC.col.p, p.item_ptr.p, upper, p.items.p);
         LSQ_CHECK_LAUNCH();
     }
-    // exact triple count = sum of list lengths
-    {
-        std::vector<int32_t> h((size_t)std::max<int64_t>(nc, 1));
-        if (nc > 0) {
-            LSQ_CUDA_TRY(cudaMemcpyAsync(h.data(), p.cnt.p, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, s));
-            LSQ_CUDA_TRY(cudaStreamSynchronize(s));
-        }
-        int64_t t = 0;
-        for (int64_t e = 0; e < nc; ++e) t += h[e];
-        p.triples = t;
-        p.nitems = nitems;
-    }
+    p.triples = nitems;
+    p.nitems = nitems;
+    p.upper = upper;
+    p.nblocks = nc;
     *out = &g->pplans.emplace(key, std::move(p)).first->second;
     return LSQ_OK;
 }
 
-int plan_launch(lsq_geom g, int dtype, const ProductPlan &p, int ra, int rb, int rc, const void *Aop,
+namespace {
+using PlanKernel = void (*)(PlanArgs);
+struct Variant {
+    PlanKernel k;
+    bool rows;
+    int threads;
+};
+template <typename T>
+const Variant *variants(int *count) {
+    static const Variant v[] = {
+        {k_mm_plan_b4<T, false, 2>, false, 256}, {k_mm_plan_b4<T, false, 4>, false, 256},
+        {k_mm_plan_b4<T, true, 2>, true, 1024},  {k_mm_plan_b4<T, true, 4>, true, 1024},
+    };
+    *count = 4;
+    return v;
+}
+
+int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks, cudaStream_t s) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)v.k, v.threads, 0);
+    per_sm = std::max(per_sm, 1);
+    int grid;
+    if (v.rows)
+        grid = std::max(1, std::min(g->n, g->num_sms * per_sm));
+    else
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>((nblocks * 16 + v.threads - 1) / v.threads,
+                                                           (int64_t)g->num_sms * per_sm));
+    note_launch();
+    v.k<<<grid, v.threads, 0, s>>>(a);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+}  // namespace
+
+int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, int rc, const void *Aop,
                 const void *X, void *C, double alpha, double beta, cudaStream_t s) {
-    if (p.ngroups == 0) return LSQ_OK;
+    ProductPlan &p = const_cast<ProductPlan &>(pc);
+    if (p.nblocks == 0) return LSQ_OK;
     PlanArgs a;
-    a.ngroups = p.ngroups;
-    a.g_row = p.g_row.p;
-    a.g_first = p.g_first.p;
-    a.g_nvalid = p.g_nvalid.p;
-    a.g_off = p.g_off.p;
+    a.n = g->n;
+    a.upper = p.upper;
+    a.c_ptr = g->pats[rc].row_ptr.p;
+    a.nblocks = p.nblocks;
     a.perm = p.perm.p;
-    a.cnt = p.cnt.p;
+    a.item_ptr = p.item_ptr.p;
     a.items = p.items.p;
     a.a_ptr = g->pats[ra].row_ptr.p;
     a.x_ptr = g->pats[rb].row_ptr.p;
+    a.c_row = p.c_row.p;
     a.c_col = g->pats[rc].col.p;
     a.A = Aop;
     a.X = X;
     a.C = C;
     a.alpha = alpha;
     a.beta = beta;
-    const int threads = 256;
-    const int64_t warps = p.ngroups;
-    int grid = (int)std::min<int64_t>((warps * 32 + threads - 1) / threads, (int64_t)g->num_sms * 64);
-    grid = std::max(grid, 1);
-    note_launch();
-    if (dtype == LSQ_F64)
-        k_mm_plan_b4<double><<<grid, threads, 0, s>>>(a);
-    else
-        k_mm_plan_b4<float><<<grid, threads, 0, s>>>(a);
-    LSQ_CHECK_LAUNCH();
+    int nv = 0;
+    const Variant *v = dtype == LSQ_F64 ? variants<double>(&nv) : variants<float>(&nv);
+    int &choice = p.variant[dtype == LSQ_F64 ? 0 : 1];
+    if (choice < 0) {
+        // autotune: time every variant once on this product (each writes the same C), keep
+        // the fastest for later calls.  Runs when beta == 0 so repeated runs are harmless.
+        if (beta != 0.0) {
+            choice = 0;
+        } else {
+            cudaEvent_t e0, e1;
+            LSQ_CUDA_TRY(cudaEventCreate(&e0));
+            LSQ_CUDA_TRY(cudaEventCreate(&e1));
+            float best = 1e30f;
+            int bi = 0;
+            for (int k = 0; k < nv; ++k) {
+                LSQ_CUDA_TRY(cudaEventRecord(e0, s));
+                LSQ_TRY(run_variant(g, v[k], a, p.nblocks, s));
+                LSQ_CUDA_TRY(cudaEventRecord(e1, s));
+                LSQ_CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                LSQ_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    bi = k;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            choice = bi;
+            p.tuned_ms[dtype == LSQ_F64 ? 0 : 1] = best;
+        }
+    }
+    LSQ_TRY(run_variant(g, v[choice], a, p.nblocks, s));
+    if (p.upper) {
+        LSQ_TRY(ensure_tmap(g, rc, s));
+        const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);
+        note_launch();
+        if (dtype == LSQ_F64)
+            k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->n, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
+                                                           g->pats[rc].tmap.p, (double *)C);
+        else
+            k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->n, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
+                                                          g->pats[rc].tmap.p, (float *)C);
+        LSQ_CHECK_LAUNCH();
+    }
     return LSQ_OK;
 }
 
