@@ -143,6 +143,30 @@ int lsq_transpose(lsq_geom g, int b, int precision, int range_x, const void *X_d
 int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
               int range_y, const void *Y_dev, double *out_host, void *stream);
 
+/*
+ * The same trace, Tr[X Y], computed without allocating any device memory.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc: code whose device memory is all owned by its own
+ * pool or caching allocator, and code that must not stall the device
+ * (cudaMalloc and cudaFree can synchronise it).  lsq_trace may allocate on
+ * its first call (a position map and reduction buffers); this one never
+ * does, and never calls an allocating library routine.
+ *
+ * Scratch: one float64 partial sum per atom row in a fixed file-scope
+ * device array of 262144 entries (2 MiB), which every GPU that loads the
+ * library holds until the process exits.  Geometries with more than
+ * 262144 atoms are rejected with LSQ_ERR_UNSUPPORTED.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU
+ * (different streams without ordering) race and give wrong results.
+ *
+ * X_dev, Y_dev: blocks on patterns range_x and range_y (dtype = precision).
+ * out_dev: device pointer to one float64 that receives the trace.  The
+ * work is enqueued on stream; the call does not synchronise.
+ */
+int lsq_trace_static(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
+                     int range_y, const void *Y_dev, double *out_dev, void *stream);
 
 /* ---- LNV grand-potential minimisation (Sec. 2.3.2, Eq. 8) ----------- */
 

@@ -72,6 +72,7 @@ def load():
         "lsq_block_matmul": (I, [P, I, I, I, I, P, I, I, P, I, P, D, D, P, P]),
         "lsq_trace": (I, [P, I, I, I, P, I, P, P, P]),
         "lsq_transpose": (I, [P, I, I, I, P, I, P, D, P]),
+        "lsq_trace_static": (I, [P, I, I, I, P, I, P, P, P]),
         "lsq_lnv_default_opts": (I, [P]),
         "lsq_lnv_required_ranges": (I, [D, D, D, P]),
         "lsq_lnv_create": (I, [P, I, D, D, D, P]),
@@ -93,6 +94,7 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lsq_last_error", "lsq_version", "lsq_launch_count", "lsq_build_neighbour_lists", "lsq_geom_destroy",
             "lsq_geom_info", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_trace", "lsq_transpose",
+            "lsq_trace_static",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise"]
 
@@ -208,6 +210,20 @@ def transpose(geom, b, X, range_x, out, range_out, alpha=1.0, precision=F64, str
     dt = torch.float64 if precision == F64 else torch.float32
     _check(load().lsq_transpose(geom.handle, b, precision, range_x, _dev(X, dt), range_out,
                                 _dev(out, dt), float(alpha), _stream(stream)))
+
+
+def trace_static(geom, b, X, range_x, Y, range_y, out, precision=F64, stream=None):
+    """Tr[X Y] into the one-element float64 CUDA tensor `out`, allocating no device memory.
+
+    For callers that cannot let the library call cudaMalloc (all device
+    memory owned by their own pool, or no device stalls allowed).  At most
+    262144 atoms; concurrent calls on unordered streams race (they share
+    one fixed scratch array).  Enqueued on the stream; does not synchronise.
+    """
+    import torch
+    dt = torch.float64 if precision == F64 else torch.float32
+    _check(load().lsq_trace_static(geom.handle, b, precision, range_x, _dev(X, dt), range_y,
+                                   _dev(Y, dt), _dev(out, torch.float64), _stream(stream)))
 
 
 def lnv_required_ranges(R_S, R_H, R_L):
