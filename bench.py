@@ -279,8 +279,8 @@ def run_ours(args):
         try:
             tj = json.load(open(tpath))
             import hashlib
-            src = open(os.path.join(ROOT, "paper_2002_07704_gb300", "csrc", "mm.cu"), "rb").read()
-            if tj.get("mm_cu_sha256") == hashlib.sha256(src).hexdigest():
+            src = open(os.path.join(ROOT, "paper_2002_07704_gb300", "csrc", "plan.cu"), "rb").read()
+            if tj.get("plan_cu_sha256") == hashlib.sha256(src).hexdigest():
                 traffic = tj.get("bytes_per_launch")
         except Exception:
             traffic = None

@@ -94,6 +94,22 @@ int lsq_geom_destroy(lsq_geom g);
 int lsq_geom_info(lsq_geom g, int *n_atoms, int *n_ranges);
 
 /*
+ * Holds n_sys independent systems in one geometry, block-diagonally: the
+ * atoms of geoms[k] follow those of geoms[k-1] and every pattern is the
+ * concatenation of the systems' patterns (no pair couples two systems).
+ * All geometries must have the same list of ranges; each keeps its own
+ * cell.  Products, traces and LNV steps on the result run over all systems
+ * in single launches (the batched workload; the paper's systems are one at
+ * a time).  The inputs stay valid and owned by the caller.  Synchronises.
+ */
+int lsq_geom_concat(int n_sys, const lsq_geom *geoms, lsq_geom *out, void *stream);
+
+/* Number of systems of a geometry (1 unless made by lsq_geom_concat) and,
+ * if atom_off_host is not NULL, the first atom of each system
+ * (atom_off_host[n_sys + 1], the last entry is n_atoms). */
+int lsq_geom_systems(lsq_geom g, int *n_sys, int64_t *atom_off_host);
+
+/*
  * Device views of pattern range_id: row_ptr_dev [n_atoms+1] int64,
  * col_dev [nnzb] int32 (sorted ascending within a row).  Owned by the
  * geometry; valid until lsq_geom_destroy.  nnzb is returned on the host.
@@ -180,6 +196,8 @@ typedef struct {
     int final_eval;            /* 1 (default): evaluate Omega and N_e of the returned L in
                                   float64 for the report; 0: report the last step's prediction */
     int verbose;               /* 1: print one line per CG step to stderr (default 0) */
+    int graph;                 /* batched minimisation: 1 (default) captures one CG step in a
+                                  CUDA graph after the first and replays it */
 } lsq_lnv_opts;
 
 typedef struct {
@@ -238,6 +256,27 @@ int lsq_lnv_energy_gradient(lsq_lnv ctx, const double *L_dev, const double *S_de
  */
 int lsq_lnv_minimise(lsq_lnv ctx, double *L_dev, const double *S_dev, const double *H_dev,
                      double mu, const lsq_lnv_opts *opts, lsq_lnv_report *rep, void *stream);
+
+/*
+ * The same minimisation for every system of a geometry made by
+ * lsq_geom_concat, all systems at once: each CG step is one sequence of
+ * launches over all systems, with each system's Omega, beta, line
+ * coefficients and step length reduced and computed on the device, so no
+ * step waits for the host; with opts->graph the step is captured in a CUDA
+ * graph after the first one (which builds plans and tunes kernels) and
+ * replayed.  Systems are independent: each has its own mu (mu_host[n_sys]),
+ * its own line search and its own convergence (a converged system is
+ * frozen, alpha = 0, while the others continue).  Differences from
+ * lsq_lnv_minimise: a direction that is not descent is restarted on the
+ * next step (the step is skipped) instead of immediately.  The mixed path
+ * refines every system with refine_iter float64 steps.  reps[n_sys]
+ * receives one report per system.  Synchronises the stream every 5 steps
+ * (convergence check) and at the end.  The first call allocates the
+ * per-system state; capture needs no allocation after that.
+ */
+int lsq_lnv_minimise_batch(lsq_lnv ctx, double *L_dev, const double *S_dev, const double *H_dev,
+                           const double *mu_host, const lsq_lnv_opts *opts, lsq_lnv_report *reps,
+                           void *stream);
 
 #ifdef __cplusplus
 }

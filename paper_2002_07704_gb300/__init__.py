@@ -34,7 +34,7 @@ class LnvOpts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_ha_per_atom", ctypes.c_double),
                 ("cg_reset", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_iter", ctypes.c_int), ("spin", ctypes.c_double),
-                ("final_eval", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("final_eval", ctypes.c_int), ("verbose", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class LnvReport(ctypes.Structure):
@@ -67,6 +67,8 @@ def load():
         "lsq_build_neighbour_lists": (I, [P, I, P, P, I, P, P]),
         "lsq_geom_destroy": (I, [P]),
         "lsq_geom_info": (I, [P, P, P]),
+        "lsq_geom_concat": (I, [I, P, P, P]),
+        "lsq_geom_systems": (I, [P, P, P]),
         "lsq_pattern": (I, [P, I, P, P, P]),
         "lsq_pattern_copy": (I, [P, I, P, P, P]),
         "lsq_block_matmul": (I, [P, I, I, I, I, P, I, I, P, I, P, D, D, P, P]),
@@ -80,6 +82,7 @@ def load():
         "lsq_lnv_init_L": (I, [P, P, P, P]),
         "lsq_lnv_energy_gradient": (I, [P, P, P, P, D, D, I, P, P, P, P]),
         "lsq_lnv_minimise": (I, [P, P, P, P, D, P, P, P]),
+        "lsq_lnv_minimise_batch": (I, [P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -93,10 +96,11 @@ def load():
 def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lsq_last_error", "lsq_version", "lsq_launch_count", "lsq_build_neighbour_lists", "lsq_geom_destroy",
-            "lsq_geom_info", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_trace", "lsq_transpose",
+            "lsq_geom_info", "lsq_geom_concat", "lsq_geom_systems", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_trace", "lsq_transpose",
             "lsq_trace_static",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
-            "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise"]
+            "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
+            "lsq_lnv_minimise_batch"]
 
 
 def launch_count():
@@ -150,6 +154,23 @@ class Geometry:
         self.handle = h
         self.n_atoms = int(pos.shape[0])
 
+    @classmethod
+    def _from_handle(cls, handle, n_atoms, ranges):
+        self = cls.__new__(cls)
+        self.handle = handle
+        self.n_atoms = int(n_atoms)
+        self.ranges = list(ranges)
+        self.cell = None
+        return self
+
+    def systems(self):
+        """Atom offsets of the systems held by this geometry ([n_sys + 1])."""
+        n = ctypes.c_int()
+        _check(_lib.lsq_geom_systems(self.handle, ctypes.byref(n), None))
+        off = (ctypes.c_int64 * (n.value + 1))()
+        _check(_lib.lsq_geom_systems(self.handle, ctypes.byref(n), off))
+        return list(off)
+
     def range_id(self, R):
         return self.ranges.index(float(R))
 
@@ -181,6 +202,16 @@ class Geometry:
 
 def build_neighbour_lists(pos, cell, ranges, stream=None):
     return Geometry(pos, cell, ranges, stream)
+
+
+def concat_geometries(geoms, stream=None):
+    """One block-diagonal geometry holding independent systems (lsq_geom_concat)."""
+    arr = (ctypes.c_void_p * len(geoms))(*[g.handle.value for g in geoms])
+    h = ctypes.c_void_p()
+    _check(load().lsq_geom_concat(len(geoms), arr, ctypes.byref(h), _stream(stream)))
+    g = Geometry._from_handle(h, sum(x.n_atoms for x in geoms), geoms[0].ranges)
+    g.parts = list(geoms)
+    return g
 
 
 def block_matmul(geom, b, A, range_a, B, range_b, C, range_c, precision=F64, trans_a=False,
@@ -262,7 +293,7 @@ class Lnv:
                  stream=None, raise_on_status=False):
         import torch
         o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
-                    int(bool(final_eval)), int(bool(verbose)))
+                    int(bool(final_eval)), int(bool(verbose)), 1)
         rep = LnvReport()
         f = torch.float64
         rc = _lib.lsq_lnv_minimise(self.handle, _dev(L, f), _dev(S, f), _dev(H, f), float(mu),
@@ -270,6 +301,22 @@ class Lnv:
         if rc != 0 and (raise_on_status or rc not in (5, 6)):
             _check(rc)
         return rep.as_dict()
+
+    def minimise_batch(self, L, S, H, mu, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
+                       precision=F64, refine_iter=2, spin=2.0, graph=True, stream=None,
+                       raise_on_status=False):
+        """Minimises every system of a concatenated geometry; mu: one value per system."""
+        import torch
+        mu = [float(m) for m in mu]
+        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin, 1, 0,
+                    int(bool(graph)))
+        reps = (LnvReport * len(mu))()
+        f = torch.float64
+        rc = _lib.lsq_lnv_minimise_batch(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),
+                                         _darr(mu), ctypes.byref(o), reps, _stream(stream))
+        if rc != 0 and (raise_on_status or rc not in (5, 6)):
+            _check(rc)
+        return [r.as_dict() for r in reps]
 
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

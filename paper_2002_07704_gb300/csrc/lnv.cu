@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "lsq_internal.h"
 
@@ -145,6 +146,173 @@ __global__ void k_onsite_inverse(int n, int b, const int64_t *__restrict__ sp,
         for (int c = 0; c < b; ++c) L[pl * b * b + r * b + c] = 0.25 * (a[r][b + c] + a[c][b + r]);
 }
 
+// ============================================================================
+// Batched minimisation: many independent systems held block-diagonally in one
+// geometry (lsq_geom_concat).  Every product, trace and update of a CG step is
+// one launch over all systems; the per-system scalars (Omega, the CG beta, the
+// line coefficients and alpha) are reduced and computed on the device, so a
+// whole step is captured once in a CUDA graph and replayed.
+// ============================================================================
+constexpr int kSlots = 16;
+
+// warp per row: rowsum[i] = sum over the row's blocks of <X_p, Y_p>
+template <typename T>
+__global__ void k_rowdot(int n, int bb, const int64_t *__restrict__ rp, const T *__restrict__ X,
+                         const T *__restrict__ Y, double *__restrict__ rowsum) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double s = 0.0;
+    for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) s += (double)X[e] * (double)Y[e];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) rowsum[warp] = s;
+}
+
+// warp per row i of X: rowsum[i] = sum over (i, j) in X of <X_ij, (Y_ji)^T> (pm: posmap X -> Y^T)
+template <typename T>
+__global__ void k_rowtrace(int n, int b, const int64_t *__restrict__ xp, const int64_t *__restrict__ pm,
+                           const T *__restrict__ X, const T *__restrict__ Y, double *__restrict__ rowsum) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int bb = b * b;
+    double s = 0.0;
+    for (int64_t e = xp[warp] * bb + lane; e < xp[warp + 1] * bb; e += 32) {
+        const int64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        const int64_t q = pm[p];
+        if (q < 0) continue;
+        const int r = rc / b, c = rc - r * b;
+        s += (double)X[e] * (double)Y[q * bb + c * b + r];
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) rowsum[warp] = s;
+}
+
+// block per system: slots[sys * kSlots + slot] = sum of its rows' partial sums (fixed order)
+__global__ void k_sys_sum(const int64_t *__restrict__ off, const double *__restrict__ rowsum,
+                          double *__restrict__ slots, int slot) {
+    __shared__ double sh[256];
+    const int sys = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = off[sys] + threadIdx.x; i < off[sys + 1]; i += blockDim.x) s += rowsum[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) slots[(int64_t)sys * kSlots + slot] = sh[0];
+}
+
+// H' = H - mu_sys S_H per row (mu of the row's system)
+__global__ void k_hprime_rows(int n, int bb, const int64_t *__restrict__ hp, const int *__restrict__ atom_sys,
+                              const double *__restrict__ mu, const double *__restrict__ H,
+                              const double *__restrict__ S, const int64_t *__restrict__ pos_s,
+                              double *__restrict__ Hp, double *__restrict__ Sh) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double m = mu[atom_sys ? atom_sys[warp] : 0];
+    for (int64_t e = hp[warp] * bb + lane; e < hp[warp + 1] * bb; e += 32) {
+        const int64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        const int64_t q = pos_s[p];
+        const double sv = q >= 0 ? S[q * bb + rc] : 0.0;
+        Sh[e] = sv;
+        Hp[e] = H[e] - m * sv;
+    }
+}
+
+struct BatchDev {
+    double *slots, *gg_prev, *beta, *alpha, *omega, *dom;
+    int *status, *frozen, *reset, *iters, *natoms, *step;
+};
+
+// After the gradient: Omega and the Polak-Ribiere beta of every system.
+__global__ void k_batch_beta(int nsys, double spin, int cg_reset, BatchDev d) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    const double *sl = d.slots + (int64_t)s * kSlots;
+    d.omega[s] = spin * (3.0 * sl[0] - 2.0 * sl[1]);
+    const double gg = sl[10], ggp = sl[11];
+    double b = 0.0;
+    const int it = d.step[0];
+    if (!d.reset[s] && it % cg_reset != 0 && d.gg_prev[s] > 0.0) b = fmax(0.0, (gg - ggp) / d.gg_prev[s]);
+    d.reset[s] = 0;
+    d.beta[s] = b;
+    d.gg_prev[s] = gg;
+}
+
+// After the line products: alpha of every system (0 for frozen systems).
+__global__ void k_batch_alpha(int nsys, double spin, double tol, BatchDev d) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) d.step[0] += 1;
+    if (s >= nsys) return;
+    const double *sl = d.slots + (int64_t)s * kSlots;
+    d.alpha[s] = 0.0;
+    if (d.frozen[s]) return;
+    const double c1 = sl[4];
+    const double c2 = spin * (3.0 * sl[5] - 2.0 * (2.0 * sl[6] + sl[7]));
+    const double c3 = -2.0 * spin * sl[8];
+    if (!(c1 < 0.0)) {  // not a descent direction: restart from -G next step
+        d.reset[s] = 1;
+        if (sl[10] == 0.0) d.frozen[s] = 1;  // exact stationary point
+        return;
+    }
+    double a = 0.0;
+    const double disc = c2 * c2 - 3.0 * c1 * c3;
+    bool ok = false;
+    if (disc >= 0.0) {
+        const double den = c2 + sqrt(disc);
+        if (den > 0.0) {
+            a = -c1 / den;
+            ok = true;
+        }
+    }
+    if (!ok && c2 > 0.0) {
+        a = -c1 / (2.0 * c2);
+        ok = true;
+    }
+    if (!ok || !isfinite(a)) {
+        d.status[s] = LSQ_ERR_UNSTABLE;
+        d.frozen[s] = 1;
+        return;
+    }
+    d.alpha[s] = a;
+    const double dom = fabs(c1 * a + c2 * a * a + c3 * a * a * a) / kHartreeEv / max(d.natoms[s], 1);
+    d.dom[s] = dom;
+    d.iters[s] += 1;
+    if (tol > 0.0 && dom < tol) {
+        d.frozen[s] = 1;
+        d.status[s] = LSQ_OK;
+    }
+}
+
+// warp per row: D = -G + beta_sys D ; L += alpha_sys D ; Gp = G
+__global__ void k_batch_dir(int n, int bb, const int64_t *__restrict__ rp, const int *__restrict__ atom_sys,
+                            const double *__restrict__ beta, const double *__restrict__ G, double *__restrict__ D) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double b = beta[atom_sys ? atom_sys[warp] : 0];
+    for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) D[e] = b == 0.0 ? -G[e] : -G[e] + b * D[e];
+}
+
+__global__ void k_batch_update(int n, int bb, const int64_t *__restrict__ rp, const int *__restrict__ atom_sys,
+                               const double *__restrict__ alpha, const double *__restrict__ D,
+                               double *__restrict__ L, const double *__restrict__ G, double *__restrict__ Gp) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double a = alpha[atom_sys ? atom_sys[warp] : 0];
+    for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) {
+        L[e] = L[e] + a * D[e];
+        Gp[e] = G[e];
+    }
+}
+
+
 static int grid_for(int64_t m) {
     int64_t g = (m + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8192));
@@ -165,6 +333,11 @@ struct lsq_lnv_s {
     // product buffers, sized for float64 and reused for float32
     DevBuf<char> LS, SL, LSL, Q, QT, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
     const int64_t *pos_s_in_h = nullptr;
+    // batched minimisation state (allocated by the first batch call)
+    int b_nsys = 0;
+    DevBuf<double> b_slots, b_rowsum, b_mu, b_gg_prev, b_beta, b_alpha, b_omega, b_dom;
+    DevBuf<int> b_status, b_frozen, b_reset, b_iters, b_natoms, b_step;
+    DevBuf<int64_t> b_off;
 };
 
 static int64_t nvals(lsq_lnv c, int r) { return c->g->pats[r].nnzb * c->b * c->b; }
@@ -180,6 +353,7 @@ extern "C" int lsq_lnv_default_opts(lsq_lnv_opts *o) {
     o->spin = 2.0;
     o->final_eval = 1;
     o->verbose = 0;
+    o->graph = 1;
     return LSQ_OK;
 }
 
@@ -318,9 +492,47 @@ Ops operands(lsq_lnv c, const double *L, const double *S, int prec, cudaStream_t
     return o;
 }
 
+// Per-system sums (batched geometries): slot k of every system.
+int seg_dot(lsq_lnv c, int prec, int r, const void *X, const void *Y, int slot, cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int n = g->n, bb = c->b * c->b;
+    const int blocks = (int)(((int64_t)n * 32 + 255) / 256);
+    note_launch();
+    if (prec == LSQ_F64)
+        k_rowdot<double><<<blocks, 256, 0, s>>>(n, bb, g->pats[r].row_ptr.p, (const double *)X,
+                                                (const double *)Y, c->b_rowsum.p);
+    else
+        k_rowdot<float><<<blocks, 256, 0, s>>>(n, bb, g->pats[r].row_ptr.p, (const float *)X,
+                                               (const float *)Y, c->b_rowsum.p);
+    note_launch();
+    k_sys_sum<<<c->b_nsys, 256, 0, s>>>(c->b_off.p, c->b_rowsum.p, c->b_slots.p, slot);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
+int seg_trace(lsq_lnv c, int prec, int rx, const void *X, int ry, const void *Y, int slot, cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int64_t *pm = nullptr;
+    LSQ_TRY(get_posmap(g, rx, ry, 1, &pm, s));
+    const int n = g->n;
+    const int blocks = (int)(((int64_t)n * 32 + 255) / 256);
+    note_launch();
+    if (prec == LSQ_F64)
+        k_rowtrace<double><<<blocks, 256, 0, s>>>(n, c->b, g->pats[rx].row_ptr.p, pm, (const double *)X,
+                                                  (const double *)Y, c->b_rowsum.p);
+    else
+        k_rowtrace<float><<<blocks, 256, 0, s>>>(n, c->b, g->pats[rx].row_ptr.p, pm, (const float *)X,
+                                                 (const float *)Y, c->b_rowsum.p);
+    note_launch();
+    k_sys_sum<<<c->b_nsys, 256, 0, s>>>(c->b_off.p, c->b_rowsum.p, c->b_slots.p, slot);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
 // Omega, N_e (scalars slots 0..3 hold the four traces) and, if G != null, the gradient.
+// seg: per-system sums into the batch slots, nothing fetched (omega, ne ignored).
 int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *G,
-                    double *omega, double *ne, cudaStream_t s) {
+                    double *omega, double *ne, cudaStream_t s, bool seg = false, bool want_ne = false) {
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
@@ -329,13 +541,19 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
     LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
     LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, c->SL.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, c->LSL.p, 0, s));
-    LSQ_TRY(dot_into(g, b, prec, c->r3, c->LSL.p, c->Q.p, 1, s));
-    if (ne) {
+    auto tr = [&](int rx, const void *X, int ry, const void *Y, int slot) {
+        return seg ? seg_trace(c, prec, rx, X, ry, Y, slot, s) : trace_into(g, b, prec, rx, X, ry, Y, slot, s);
+    };
+    auto dt = [&](int r, const void *X, const void *Y, int slot) {
+        return seg ? seg_dot(c, prec, r, X, Y, slot, s) : dot_into(g, b, prec, r, X, Y, slot, s);
+    };
+    LSQ_TRY(tr(c->rH, o.Hp, c->r3, c->LSL.p, 0));
+    LSQ_TRY(dt(c->r3, c->LSL.p, c->Q.p, 1));
+    if (ne || want_ne) {
         void *SLS = c->QD.p;
         LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, 1, c->SL.p, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
-        LSQ_TRY(trace_into(g, b, prec, c->rH, o.Sh, c->r3, c->LSL.p, 2, s));
-        LSQ_TRY(dot_into(g, b, prec, c->r3, c->LSL.p, SLS, 3, s));
+        LSQ_TRY(tr(c->rH, o.Sh, c->r3, c->LSL.p, 2));
+        LSQ_TRY(dt(c->r3, c->LSL.p, SLS, 3));
     }
     if (G) {
         // G1 = Q.LS = Q.(SL)^T and G2 = Q^T.LS, with SL and Q^T materialised so both
@@ -360,7 +578,7 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         }
         LSQ_CHECK_LAUNCH();
     }
-    if (omega || ne) {
+    if (!seg && (omega || ne)) {
         double t[4];
         LSQ_TRY(fetch_scalars(g, ne ? 4 : 2, t, s));
         if (omega) *omega = spin * (3.0 * t[0] - 2.0 * t[1]);
@@ -371,7 +589,7 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
 
 // c1 = <G, D> (float64), c2, c3 from the products listed at the top of the file.
 int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *c123,
-                cudaStream_t s) {
+                cudaStream_t s, bool seg = false) {
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
@@ -389,6 +607,14 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
     LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
     LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+    if (seg) {
+        LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
+        LSQ_TRY(seg_trace(c, prec, c->rH, o.Hp, c->r3, F, 5, s));
+        LSQ_TRY(seg_dot(c, prec, c->r3, F, c->Q.p, 6, s));
+        LSQ_TRY(seg_dot(c, prec, c->rL, o.L, Z, 7, s));
+        LSQ_TRY(seg_dot(c, prec, c->r3, F, c->QD.p, 8, s));
+        return LSQ_OK;
+    }
     LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
     LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, F, 5, s));
     LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->Q.p, 6, s));
@@ -545,5 +771,249 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
     }
     if (status == LSQ_ERR_UNSTABLE) return set_error(status, "no local minimum along the CG direction");
     if (status == LSQ_ERR_NOT_CONVERGED) return set_error(status, "iteration limit reached");
+    return LSQ_OK;
+}
+
+
+namespace {
+
+int batch_alloc(lsq_lnv c) {
+    lsq_geom g = c->g;
+    const int ns = g->n_sys;
+    if (c->b_nsys == ns && c->b_slots.p) return LSQ_OK;
+    c->b_nsys = ns;
+    LSQ_TRY(c->b_slots.alloc((size_t)ns * kSlots));
+    LSQ_TRY(c->b_rowsum.alloc((size_t)std::max(g->n, 1)));
+    LSQ_TRY(c->b_mu.alloc(ns));
+    LSQ_TRY(c->b_gg_prev.alloc(ns));
+    LSQ_TRY(c->b_beta.alloc(ns));
+    LSQ_TRY(c->b_alpha.alloc(ns));
+    LSQ_TRY(c->b_omega.alloc(ns));
+    LSQ_TRY(c->b_dom.alloc(ns));
+    LSQ_TRY(c->b_status.alloc(ns));
+    LSQ_TRY(c->b_frozen.alloc(ns));
+    LSQ_TRY(c->b_reset.alloc(ns));
+    LSQ_TRY(c->b_iters.alloc(ns));
+    LSQ_TRY(c->b_natoms.alloc(ns));
+    LSQ_TRY(c->b_step.alloc(1));
+    LSQ_TRY(c->b_off.alloc((size_t)ns + 1));
+    std::vector<int> na(ns);
+    for (int k = 0; k < ns; ++k) na[k] = (int)(g->sys_atom_off[k + 1] - g->sys_atom_off[k]);
+    LSQ_CUDA_TRY(cudaMemcpy(c->b_natoms.p, na.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+    LSQ_CUDA_TRY(cudaMemcpy(c->b_off.p, g->sys_atom_off.data(), sizeof(int64_t) * (ns + 1),
+                            cudaMemcpyHostToDevice));
+    return LSQ_OK;
+}
+
+BatchDev batch_dev(lsq_lnv c) {
+    BatchDev d;
+    d.slots = c->b_slots.p;
+    d.gg_prev = c->b_gg_prev.p;
+    d.beta = c->b_beta.p;
+    d.alpha = c->b_alpha.p;
+    d.omega = c->b_omega.p;
+    d.dom = c->b_dom.p;
+    d.status = c->b_status.p;
+    d.frozen = c->b_frozen.p;
+    d.reset = c->b_reset.p;
+    d.iters = c->b_iters.p;
+    d.natoms = c->b_natoms.p;
+    d.step = c->b_step.p;
+    return d;
+}
+
+// One CG step of every system, enqueued on s with no host synchronisation.
+int batch_step(lsq_lnv c, double *L, const double *S, double spin, int prec, double tol, int cg_reset,
+               cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int ns = g->n_sys, bb = c->b * c->b;
+    const int rows = (int)(((int64_t)g->n * 32 + 255) / 256);
+    const int *asys = g->n_sys > 1 ? g->atom_sys.p : nullptr;
+    BatchDev d = batch_dev(c);
+    LSQ_TRY(energy_gradient(c, L, S, spin, prec, c->G.p, nullptr, nullptr, s, true));
+    LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
+    LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
+    note_launch();
+    k_batch_beta<<<(ns + 127) / 128, 128, 0, s>>>(ns, spin, cg_reset, d);
+    note_launch();
+    k_batch_dir<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rL].row_ptr.p, asys, c->b_beta.p, c->G.p, c->D.p);
+    LSQ_CHECK_LAUNCH();
+    double unused[3];
+    LSQ_TRY(line_coeffs(c, L, S, spin, prec, unused, s, true));
+    note_launch();
+    k_batch_alpha<<<(ns + 127) / 128, 128, 0, s>>>(ns, spin, tol, d);
+    note_launch();
+    k_batch_update<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rL].row_ptr.p, asys, c->b_alpha.p, c->D.p, L,
+                                        c->G.p, c->Gp.p);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
+int batch_prepare_hs(lsq_lnv c, const double *S, const double *H, int prec, cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int bb = c->b * c->b;
+    const int rows = (int)(((int64_t)g->n * 32 + 255) / 256);
+    note_launch();
+    k_hprime_rows<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rH].row_ptr.p, g->n_sys > 1 ? g->atom_sys.p : nullptr,
+                                       c->b_mu.p, H, S, c->pos_s_in_h, c->Hp.p, c->Sh.p);
+    LSQ_CHECK_LAUNCH();
+    if (prec == LSQ_F32) {
+        int64_t nh = nvals(c, c->rH), ns = nvals(c, c->rS);
+        note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Hp.p, (float *)c->Hpc.p);
+        note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Sh.p, (float *)c->Shc.p);
+        note_launch();
+        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p);
+        LSQ_CHECK_LAUNCH();
+    }
+    return LSQ_OK;
+}
+
+}  // namespace
+
+extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, const double *H,
+                                      const double *mu_host, const lsq_lnv_opts *opts,
+                                      lsq_lnv_report *reps, void *stream) {
+    clear_error();
+    if (!c || !L || !S || !H || !mu_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    lsq_lnv_opts o;
+    lsq_lnv_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != LSQ_F64 && o.precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    if (o.max_iter < 0 || o.cg_reset < 1 || o.refine_iter < 0)
+        return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
+    cudaStream_t us = (cudaStream_t)stream;
+    lsq_geom g = c->g;
+    const int ns = g->n_sys;
+    auto t0 = std::chrono::steady_clock::now();
+    LSQ_TRY(batch_alloc(c));
+    // Work runs on a private stream ordered after the caller's (a graph cannot be captured
+    // from the legacy default stream); the caller's stream waits for it at the end.
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    LSQ_CUDA_TRY(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    LSQ_CUDA_TRY(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    struct Cleanup {
+        cudaStream_t us, s;
+        cudaEvent_t a, b;
+        ~Cleanup() {
+            if (b && s) {
+                cudaEventRecord(b, s);
+                cudaStreamWaitEvent(us, b, 0);
+            }
+            if (s) cudaStreamSynchronize(s);
+            if (s) cudaStreamDestroy(s);
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } cleanup{us, s, ev_in, ev_out};
+    LSQ_CUDA_TRY(cudaEventRecord(ev_in, us));
+    LSQ_CUDA_TRY(cudaStreamWaitEvent(s, ev_in, 0));
+    const int64_t nl = nvals(c, c->rL);
+    LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_mu.p, mu_host, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+    LSQ_TRY(batch_prepare_hs(c, S, H, LSQ_F64, s));
+    if (o.precision == LSQ_F32) LSQ_TRY(batch_prepare_hs(c, S, H, LSQ_F32, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->Gp.p, 0, sizeof(double) * nl, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_frozen.p, 0, sizeof(int) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_iters.p, 0, sizeof(int) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_gg_prev.p, 0, sizeof(double) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_dom.p, 0, sizeof(double) * ns, s));
+    {
+        std::vector<int> one(ns, 1), st(ns, o.tol_ha_per_atom > 0.0 ? LSQ_ERR_NOT_CONVERGED : LSQ_OK);
+        LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_status.p, st.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    std::vector<int> iters64(ns, 0), frozen(ns, 0), status(ns, 0), it_before(ns, 0);
+    const int nphase = o.precision == LSQ_F32 ? 2 : 1;
+    const int check_every = 5;
+    for (int phase = 0; phase < nphase; ++phase) {
+        const int prec = phase == 0 ? o.precision : LSQ_F64;
+        const int budget = phase == 0 ? o.max_iter : o.refine_iter;
+        if (phase == 1) {
+            // refinement: float64 steps from a fresh direction for every system that did not fail
+            LSQ_CUDA_TRY(cudaMemcpy(status.data(), c->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+            LSQ_CUDA_TRY(cudaMemcpy(it_before.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+            for (int k = 0; k < ns; ++k) frozen[k] = status[k] == LSQ_ERR_UNSTABLE ? 1 : 0;
+            std::vector<int> one(ns, 1);
+            LSQ_CUDA_TRY(cudaMemcpy(c->b_frozen.p, frozen.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+            LSQ_CUDA_TRY(cudaMemcpy(c->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+        }
+        LSQ_CUDA_TRY(cudaMemsetAsync(c->b_step.p, 0, sizeof(int), s));
+        // tol = 0 freezes nothing; the refinement uses tol = 0 (fixed number of steps)
+        const double tol = phase == 0 ? o.tol_ha_per_atom : 0.0;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        for (int it = 0; it < budget; ++it) {
+            if (it == 1 && o.graph) {
+                // plans, maps and autotuning exist after the first step: capture one step
+                LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                int rc = batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s);
+                cudaError_t ec = cudaStreamEndCapture(s, &graph);
+                if (rc != LSQ_OK) return rc;
+                if (ec != cudaSuccess) return set_error(LSQ_ERR_CUDA, cudaGetErrorString(ec));
+                LSQ_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+            }
+            if (exec) {
+                LSQ_CUDA_TRY(cudaGraphLaunch(exec, s));
+            } else {
+                LSQ_TRY(batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s));
+            }
+            if (tol > 0.0 && (it + 1) % check_every == 0) {
+                LSQ_CUDA_TRY(cudaMemcpyAsync(frozen.data(), c->b_frozen.p, sizeof(int) * ns,
+                                             cudaMemcpyDeviceToHost, s));
+                LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+                bool all = true;
+                for (int k = 0; k < ns; ++k) all = all && frozen[k];
+                if (all) break;
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+        if (phase == 1) {
+            std::vector<int> it_after(ns);
+            LSQ_CUDA_TRY(cudaMemcpy(it_after.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+            for (int k = 0; k < ns; ++k) iters64[k] = it_after[k] - it_before[k];
+        } else if (prec == LSQ_F64) {
+            LSQ_CUDA_TRY(cudaMemcpy(iters64.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+        }
+    }
+    // final float64 Omega and N_e of every system
+    LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, nullptr, nullptr, s, true, true));
+    std::vector<double> slots((size_t)ns * kSlots), dom(ns);
+    std::vector<int> iters(ns);
+    LSQ_CUDA_TRY(cudaMemcpyAsync(slots.data(), c->b_slots.p, sizeof(double) * ns * kSlots, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(dom.data(), c->b_dom.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(iters.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(status.data(), c->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int worst = LSQ_OK;
+    for (int k = 0; k < ns; ++k) {
+        const double *sl = slots.data() + (size_t)k * kSlots;
+        const int na = (int)(g->sys_atom_off[k + 1] - g->sys_atom_off[k]);
+        int st = status[k];
+        if (nphase == 2 && st != LSQ_ERR_UNSTABLE && o.tol_ha_per_atom > 0.0 && iters64[k] > 0 &&
+            dom[k] < o.tol_ha_per_atom)
+            st = LSQ_OK;
+        if (reps) {
+            reps[k].iterations = iters[k];
+            reps[k].iterations_fp64 = iters64[k];
+            reps[k].status = st;
+            reps[k].omega_ev = o.spin * (3.0 * sl[0] - 2.0 * sl[1]);
+            reps[k].ne = o.spin * (3.0 * sl[2] - 2.0 * sl[3]);
+            reps[k].omega_ha_per_atom = reps[k].omega_ev / kHartreeEv / std::max(na, 1);
+            reps[k].last_domega_ha_per_atom = dom[k];
+            reps[k].seconds = sec;
+        }
+        if (st == LSQ_ERR_UNSTABLE) worst = LSQ_ERR_UNSTABLE;
+        else if (st == LSQ_ERR_NOT_CONVERGED && worst == LSQ_OK) worst = LSQ_ERR_NOT_CONVERGED;
+    }
+    if (worst == LSQ_ERR_UNSTABLE) return set_error(worst, "a system has no local minimum along its CG direction");
+    if (worst == LSQ_ERR_NOT_CONVERGED) return set_error(worst, "iteration limit reached for a system");
     return LSQ_OK;
 }

@@ -286,6 +286,68 @@ __global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4(PlanArgs g) {
     }
 }
 
+// Third schedule: one row i of C per thread block with row i of A copied once into shared
+// memory, so that only the blocks of B^T come from L2 (needs 16 |row of A| values of smem).
+template <typename T, int UNROLL>
+__global__ void __launch_bounds__(1024) k_mm_plan_b4_smem(PlanArgs g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    const T *__restrict__ A = static_cast<const T *>(g.A);
+    const T *__restrict__ X = static_cast<const T *>(g.X);
+    T *__restrict__ C = static_cast<T *>(g.C);
+    const int sub = threadIdx.x & 15;
+    const int r = sub >> 2, c = sub & 3;
+    const int team = threadIdx.x >> 4, nteams = blockDim.x >> 4;
+    for (int i = blockIdx.x; i < g.n; i += gridDim.x) {
+        const int64_t a0 = g.a_ptr[i], na = g.a_ptr[i + 1] - a0;
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < na * 16; e += blockDim.x) As[e] = A[16 * a0 + e];
+        __syncthreads();
+        const T *arow = As + 4 * r;
+        for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
+            const int64_t s = g.perm[e];
+            if (g.upper && g.c_col[s] < i) continue;
+            const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
+            const int64_t i0 = g.item_ptr[s];
+            const uint32_t *__restrict__ it = g.items + i0;
+            const int nit = (int)(g.item_ptr[s + 1] - i0);
+            T acc[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) acc[u] = T(0);
+            int q = 0;
+            for (; q + UNROLL <= nit; q += UNROLL) {
+                uint32_t w[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) w[u] = __ldg(it + q + u);
+                T a[UNROLL][4], x[UNROLL][4];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const T *ap = arow + 16 * (w[u] & 0xffffu);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) a[u][t] = ap[t];
+                    Row4<T>::load(xrow + 16 * (w[u] >> 16), x[u]);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) acc[u] = fma(a[u][t], x[u][t], acc[u]);
+            }
+            for (; q < nit; ++q) {
+                const uint32_t w0 = __ldg(it + q);
+                const T *ap = arow + 16 * (w0 & 0xffffu);
+                T x0[4];
+                Row4<T>::load(xrow + 16 * (w0 >> 16), x0);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) acc[0] = fma(ap[t], x0[t], acc[0]);
+            }
+            T v = acc[0];
+#pragma unroll
+            for (int u = 1; u < UNROLL; ++u) v += acc[u];
+            plan_store(g, C, s, sub, v);
+        }
+    }
+}
+
 // Lower blocks of a symmetric result: C_ij = (C_ji)^T for j < i (tm: transpose map of C's pattern).
 template <typename T>
 __global__ void k_mirror_lower(int n, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
@@ -375,20 +437,33 @@ struct Variant {
     PlanKernel k;
     bool rows;
     int threads;
+    bool smem_a;  // stages the row of A in shared memory (16 values per block of the longest row)
 };
 template <typename T>
 const Variant *variants(int *count) {
     static const Variant v[] = {
-        {k_mm_plan_b4<T, false, 2>, false, 256}, {k_mm_plan_b4<T, false, 4>, false, 256},
-        {k_mm_plan_b4<T, true, 2>, true, 1024},  {k_mm_plan_b4<T, true, 4>, true, 1024},
+        {k_mm_plan_b4<T, false, 2>, false, 256, false}, {k_mm_plan_b4<T, false, 4>, false, 256, false},
+        {k_mm_plan_b4<T, true, 2>, true, 1024, false},  {k_mm_plan_b4<T, true, 4>, true, 1024, false},
+        {k_mm_plan_b4_smem<T, 2>, true, 1024, true},    {k_mm_plan_b4_smem<T, 4>, true, 1024, true},
     };
-    *count = 4;
+    *count = 6;
     return v;
 }
 
-int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks, cudaStream_t s) {
+// Shared memory a variant needs for pattern ra (0 if none; -1 if it does not fit).
+int64_t variant_smem(lsq_geom g, const Variant &v, int ra, size_t es) {
+    if (!v.smem_a) return 0;
+    const int64_t need = (int64_t)g->pats[ra].max_row * 16 * (int64_t)es;
+    return need + 1024 <= (int64_t)g->smem_optin ? need : -1;
+}
+
+int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks, cudaStream_t s,
+                int64_t smem = 0) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)v.k, v.threads, 0);
+    if (smem > 0)
+        LSQ_CUDA_TRY(cudaFuncSetAttribute((const void *)v.k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)v.k, v.threads, (size_t)smem);
     per_sm = std::max(per_sm, 1);
     int grid;
     if (v.rows)
@@ -397,7 +472,7 @@ int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks
         grid = (int)std::max<int64_t>(1, std::min<int64_t>((nblocks * 16 + v.threads - 1) / v.threads,
                                                            (int64_t)g->num_sms * per_sm));
     note_launch();
-    v.k<<<grid, v.threads, 0, s>>>(a);
+    v.k<<<grid, v.threads, (size_t)smem, s>>>(a);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -439,8 +514,10 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
             float best = 1e30f;
             int bi = 0;
             for (int k = 0; k < nv; ++k) {
+                const int64_t sm = variant_smem(g, v[k], ra, dtype_size(dtype));
+                if (sm < 0) continue;
                 LSQ_CUDA_TRY(cudaEventRecord(e0, s));
-                LSQ_TRY(run_variant(g, v[k], a, p.nblocks, s));
+                LSQ_TRY(run_variant(g, v[k], a, p.nblocks, s, sm));
                 LSQ_CUDA_TRY(cudaEventRecord(e1, s));
                 LSQ_CUDA_TRY(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -456,7 +533,7 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
             p.tuned_ms[dtype == LSQ_F64 ? 0 : 1] = best;
         }
     }
-    LSQ_TRY(run_variant(g, v[choice], a, p.nblocks, s));
+    LSQ_TRY(run_variant(g, v[choice], a, p.nblocks, s, variant_smem(g, v[choice], ra, dtype_size(dtype))));
     if (p.upper) {
         LSQ_TRY(ensure_tmap(g, rc, s));
         const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);

@@ -1,0 +1,101 @@
+"""Batched minimisation of independent systems (one block-diagonal geometry).
+
+Each system of the batch must follow the same trajectory as its own
+single-system minimisation (float64: 1e-9 relative in Omega after the
+same number of steps), which is itself parity-checked against the oracle;
+the smallest systems are also checked against the oracle directly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import lnv as OL
+import paper_2002_07704_gb300 as lsq
+from gpu_common import cuda, gpu_geometry, gpu_pattern, si
+from synth import batch_system_seed, sk_blocks
+
+pytestmark = pytest.mark.gpu
+
+R_S = R_H = 6.6
+R_L = 8.0
+
+
+def _system(n, sigma, seed, b, perturb=None):
+    pos, cell = si(n, sigma, seed)
+    ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
+    g = gpu_geometry(pos, cell, ranges)
+    pH = gpu_pattern(g, 1)
+    H, S = sk_blocks(pos, cell, pH.rows(), pH.col, b=b, perturb_seed=perturb)
+    return pos, cell, g, pH, H, S
+
+
+def _batch(specs, b):
+    systems = [_system(n, sg, sd, b, pt) for (n, sg, sd, pt) in specs]
+    bg = lsq.concat_geometries([s[2] for s in systems])
+    H = np.concatenate([s[4] for s in systems])
+    S = np.concatenate([s[5] for s in systems])
+    return systems, bg, H, S
+
+
+def _init_L(ctx, g, S, b):
+    L = torch.zeros((g.nnzb(2), b, b), dtype=torch.float64, device="cuda")
+    ctx.init_L(cuda(S), L)
+    return L
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_matches_single_systems_float64(graph):
+    lsq.build()
+    specs = [(2, 0.05, batch_system_seed(0), None), (1, 0.1, batch_system_seed(1), None),
+             (3, 0.15, batch_system_seed(2), None)]
+    mus = [-2.0, -1.5, -2.2]
+    systems, bg, H, S = _batch(specs, 4)
+    ctx = lsq.Lnv(bg, 4, R_S, R_H, R_L)
+    L = _init_L(ctx, bg, S, 4)
+    reps = ctx.minimise_batch(L, cuda(S), cuda(H), mus, max_iter=12, graph=graph)
+    for k, (pos, cell, g, pH, Hk, Sk) in enumerate(systems):
+        c1 = lsq.Lnv(g, 4, R_S, R_H, R_L)
+        Lk = _init_L(c1, g, Sk, 4)
+        rep = c1.minimise(Lk, cuda(Sk), cuda(Hk), mus[k], max_iter=12)
+        assert reps[k]["iterations"] == rep["iterations"] == 12
+        assert abs(reps[k]["omega_ev"] - rep["omega_ev"]) <= 1e-9 * abs(rep["omega_ev"])
+        assert abs(reps[k]["ne"] - rep["ne"]) <= 1e-9 * abs(rep["ne"])
+
+
+def test_batch_block13_against_oracle():
+    """13-orbital systems (three s,p copies plus a d-like orbital, perturbed H) in one batch."""
+    lsq.build()
+    specs = [(1, 0.1, batch_system_seed(24), batch_system_seed(24) + 7),
+             (2, 0.05, batch_system_seed(25), batch_system_seed(25) + 7)]
+    systems, bg, H, S = _batch(specs, 13)
+    ctx = lsq.Lnv(bg, 13, R_S, R_H, R_L)
+    L = _init_L(ctx, bg, S, 13)
+    mus = [-2.0, -2.0]
+    reps = ctx.minimise_batch(L, cuda(S), cuda(H), mus, max_iter=6)
+    for k, (pos, cell, g, pH, Hk, Sk) in enumerate(systems):
+        m = OL.System(pos, cell)
+        pHo = m.pattern(R_H)
+        assert pHo == pH
+        ref = OL.Lnv(m, oracle.Bsr(pHo, 13, Sk), oracle.Bsr(pHo, 13, Hk), R_L, mus[k])
+        L0 = OL.onsite_inverse_half(oracle.Bsr(pHo, 13, Sk), ref.pat_L)
+        Lr, hist = OL.minimise(ref, L0, 6)
+        om_ref, ne_ref = ref.energy(Lr)
+        assert abs(reps[k]["omega_ev"] - om_ref) <= 1e-8 * abs(om_ref)
+        assert abs(reps[k]["ne"] - ne_ref) <= 1e-8 * abs(ne_ref)
+
+
+def test_batch_mixed_precision_converges_to_float64():
+    lsq.build()
+    specs = [(2, 0.05, batch_system_seed(3), None), (2, 0.1, batch_system_seed(4), None)]
+    systems, bg, H, S = _batch(specs, 4)
+    ctx = lsq.Lnv(bg, 4, R_S, R_H, R_L)
+    L64 = _init_L(ctx, bg, S, 4)
+    L32 = L64.clone()
+    mus = [-2.0, -2.0]
+    r64 = ctx.minimise_batch(L64, cuda(S), cuda(H), mus, max_iter=200, tol_ha_per_atom=1e-11)
+    r32 = ctx.minimise_batch(L32, cuda(S), cuda(H), mus, max_iter=200, tol_ha_per_atom=1e-9,
+                             precision=lsq.F32, refine_iter=3)
+    for a, b in zip(r64, r32):
+        assert a["status"] == 0
+        assert abs(a["omega_ha_per_atom"] - b["omega_ha_per_atom"]) < 1e-6

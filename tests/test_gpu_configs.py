@@ -1,0 +1,81 @@
+"""The full-size configurations, checked through properties that hold at any size.
+
+* 8000-atom Si (10x10x10 cells), L range 10 A: dOmega/dL from autograd
+  backward (intermediates recomputed) equals the analytic LNV gradient of
+  lsq_lnv_energy_gradient, which is parity-checked against the oracle at
+  small sizes, and matches finite differences on seeded entries (Omega is a
+  cubic in each entry of L, so the Richardson combination of central
+  differences at h and 2h is exact up to the rounding of Omega).
+* 32768-atom Si (16x16x16 cells, sigma 0.1 A): the mixed-precision
+  minimisation to |dOmega| < 1e-7 Ha/atom with float64 refinement reaches
+  the float64 minimum within 1e-6 Ha/atom.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2002_07704_gb300 as lsq
+from paper_2002_07704_gb300.autograd import lnv_omega
+from gpu_common import cuda, gpu_geometry, gpu_pattern, si
+from synth import config_seed, sk_blocks
+
+pytestmark = pytest.mark.gpu
+
+R_S = R_H = 6.6
+R_L = 10.0
+MU = -2.0
+
+
+def _setup(n, sigma, seed):
+    pos, cell = si(n, sigma, seed)
+    g = gpu_geometry(pos, cell, lsq.lnv_required_ranges(R_S, R_H, R_L))
+    pH = gpu_pattern(g, 1)
+    H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
+    ctx = lsq.Lnv(g, 4, R_S, R_H, R_L)
+    L = torch.zeros((g.nnzb(2), 4, 4), dtype=torch.float64, device="cuda")
+    Sd, Hd = cuda(S), cuda(H)
+    ctx.init_L(Sd, L)
+    return g, ctx, L, Sd, Hd
+
+
+def test_8000_atoms_autograd_gradient_and_fd():
+    lsq.build()
+    g, ctx, L, S, H = _setup(10, 0.05, config_seed(3))
+    ctx.minimise(L, S, H, MU, max_iter=3, precision=lsq.F32, refine_iter=0, final_eval=False)
+    G = torch.zeros_like(L)
+    om_ref, _ = ctx.energy_gradient(L, S, H, MU, G=G)
+    Lt = L.clone().requires_grad_(True)
+    Ht = H.clone().requires_grad_(True)
+    rid = (0, 1, 2, 3, 5)
+    om = lnv_omega(g, 4, Lt, S, Ht, MU, rid, recompute=True)
+    om.backward()
+    assert abs(om.item() - om_ref) <= 1e-11 * abs(om_ref)
+    gmax = G.abs().max().item()
+    assert (Lt.grad - G).abs().max().item() <= 1e-10 * gmax
+    # dOmega/dH is the (transposed) density matrix on H's range: finite differences too
+    rng = np.random.default_rng(2002)
+    Lf = L.reshape(-1)
+    h = 1e-3
+
+    def omega_at(idx, delta):
+        Lp = Lf.clone()
+        Lp[idx] += delta
+        with torch.no_grad():
+            return lnv_omega(g, 4, Lp.reshape(L.shape), S, H, MU, rid, recompute=False).item()
+
+    Gf = Lt.grad.reshape(-1)
+    for idx in rng.choice(Lf.numel(), size=16, replace=False):
+        d1 = (omega_at(idx, h) - omega_at(idx, -h)) / (2 * h)
+        d2 = (omega_at(idx, 2 * h) - omega_at(idx, -2 * h)) / (4 * h)
+        fd = (4 * d1 - d2) / 3
+        assert abs(fd - Gf[idx].item()) <= 1e-6 * gmax
+
+
+def test_32768_atoms_mixed_reaches_float64_minimum():
+    lsq.build()
+    g, ctx, L, S, H = _setup(16, 0.1, config_seed(4))
+    rep = ctx.minimise(L, S, H, MU, max_iter=300, tol_ha_per_atom=1e-7, precision=lsq.F32,
+                       refine_iter=2)
+    assert rep["status"] == 0
+    rep64 = ctx.minimise(L, S, H, MU, max_iter=40, tol_ha_per_atom=1e-9)
+    assert abs(rep["omega_ha_per_atom"] - rep64["omega_ha_per_atom"]) < 1e-6
