@@ -400,11 +400,12 @@ extern "C" int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double 
     };
     int rc;
     size_t d = sizeof(double);
+    const bool mat = b == 4;  // transposed operands materialised (see energy_gradient)
     if ((rc = c->Hp.alloc(nvals(c, c->rH))) || (rc = c->Sh.alloc(nvals(c, c->rH))) ||
         (rc = c->G.alloc(nvals(c, c->rL))) || (rc = c->Gp.alloc(nvals(c, c->rL))) ||
         (rc = c->D.alloc(nvals(c, c->rL))) || (rc = c->LS.alloc(d * nvals(c, c->r1))) ||
-        (rc = c->LSL.alloc(d * nvals(c, c->r3))) || (rc = c->SL.alloc(d * nvals(c, c->r1))) ||
-        (rc = c->QT.alloc(d * nvals(c, c->r3))) ||
+        (rc = c->LSL.alloc(d * nvals(c, c->r3))) ||
+        (mat && (rc = c->SL.alloc(d * nvals(c, c->r1)))) || (mat && (rc = c->QT.alloc(d * nvals(c, c->r3)))) ||
         (rc = c->Q.alloc(d * nvals(c, c->r3))) || (rc = c->QD.alloc(d * nvals(c, c->r3))) ||
         (rc = c->G1.alloc(d * nvals(c, c->rL))) || (rc = c->G2.alloc(d * nvals(c, c->rL))) ||
         (rc = c->Lc.alloc(4 * nvals(c, c->rL))) || (rc = c->Dc.alloc(4 * nvals(c, c->rL))) ||
@@ -539,8 +540,13 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     // scalar slots: 0 = Tr[H' LSL], 1 = <LSL, Q>, 2 = Tr[S LSL], 3 = <LSL, SLS>
     LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 1, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
-    LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, c->SL.p, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
+    // 4 x 4 blocks: transposed operands are materialised so the plan kernel reads rows; other
+    // block sizes use the plan-free kernels, which read transposes through the transpose map
+    const bool mat = c->b == 4;
+    const void *LSop = mat ? c->SL.p : c->LS.p;  // operand giving LS as op(B)
+    const int tLS = mat ? 1 : 0;
+    if (mat) LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, tLS, LSop, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
     auto tr = [&](int rx, const void *X, int ry, const void *Y, int slot) {
         return seg ? seg_trace(c, prec, rx, X, ry, Y, slot, s) : trace_into(g, b, prec, rx, X, ry, Y, slot, s);
     };
@@ -551,16 +557,20 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     LSQ_TRY(dt(c->r3, c->LSL.p, c->Q.p, 1));
     if (ne || want_ne) {
         void *SLS = c->QD.p;
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, 1, c->SL.p, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, tLS, LSop, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
         LSQ_TRY(tr(c->rH, o.Sh, c->r3, c->LSL.p, 2));
         LSQ_TRY(dt(c->r3, c->LSL.p, SLS, 3));
     }
     if (G) {
         // G1 = Q.LS = Q.(SL)^T and G2 = Q^T.LS, with SL and Q^T materialised so both
         // operands are read row by row
-        LSQ_TRY(transpose_on(g, c->r3, b, prec, c->Q.p, c->QT.p, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, 1, c->SL.p, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->QT.p, c->r1, 1, c->SL.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, tLS, LSop, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
+        if (mat) {
+            LSQ_TRY(transpose_on(g, c->r3, b, prec, c->Q.p, c->QT.p, s));
+            LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->QT.p, c->r1, 1, LSop, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 1));
+        } else {
+            LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->Q.p, c->r1, 0, LSop, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 1));
+        }
         const int64_t *pq = nullptr, *pqt = nullptr;
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
@@ -601,12 +611,21 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
         D = c->Dc.p;
     }
     void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
+    const bool mat = c->b == 4;  // see energy_gradient
     LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(transpose_on(g, c->r1, b, prec, P, PT, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, PT, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+    if (mat) {
+        LSQ_TRY(transpose_on(g, c->r1, b, prec, P, PT, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, PT, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+    } else {
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+    }
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
-    LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+    if (mat) {
+        LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+    } else {
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->QD.p, c->r1, 0, P, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+    }
     if (seg) {
         LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
         LSQ_TRY(seg_trace(c, prec, c->rH, o.Hp, c->r3, F, 5, s));
