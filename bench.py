@@ -113,6 +113,21 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest of one float across all ranks (the timing rule: max over ranks)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps_per_rank, world, ms_per_step_max):
+    """Whole-job steps/s: every rank runs its own replica, timed by the slowest rank."""
+    return world * steps_per_rank / (steps_per_rank * ms_per_step_max / 1000.0)
+
+
 # ---- clocks during the timed region -----------------------------------------
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -229,12 +244,8 @@ def run_ours(args):
         print("warning: the timed minimisation stopped after %d of %d steps (status %d)"
               % (done, args.steps, rep["status"]), file=sys.stderr)
     ms = e0.elapsed_time(e1) / max(done, 1)
-    ms_all = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * 1000.0 / ms_all
+    ms_all = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(done, world, ms_all)
 
     # --- float64 path, same steps from the same start ---
     L64 = L0.clone()

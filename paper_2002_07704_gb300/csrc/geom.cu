@@ -287,10 +287,10 @@ int get_posmap(lsq_geom g, int p, int q, int transposed, const int64_t **out, cu
         if (g->n > 0 && g->pats[p].nnzb > 0) {
             int threads = 256;
             int blocks = (int)(((int64_t)g->n * 32 + threads - 1) / threads);
-            { note_launch();
+            note_launch();
             k_posmap<<<blocks, threads, 0, s>>>(g->n, g->pats[p].row_ptr.p, g->pats[p].col.p,
                                                 g->pats[q].row_ptr.p, g->pats[q].col.p, transposed,
-                                                buf.p); }
+                                                buf.p);
             LSQ_CHECK_LAUNCH();
         }
         it = g->posmaps.emplace(key, std::move(buf)).first;
@@ -306,9 +306,9 @@ int ensure_tmap(lsq_geom g, int r, cudaStream_t s) {
     if (g->n > 0 && P.nnzb > 0) {
         int threads = 256;
         int blocks = (int)(((int64_t)g->n * 32 + threads - 1) / threads);
-        { note_launch();
+        note_launch();
         k_posmap<<<blocks, threads, 0, s>>>(g->n, P.row_ptr.p, P.col.p, P.row_ptr.p, P.col.p, 1,
-                                            P.tmap.p); }
+                                            P.tmap.p);
         LSQ_CHECK_LAUNCH();
     }
     return LSQ_OK;
@@ -421,22 +421,22 @@ extern "C" int lsq_build_neighbour_lists(const double *pos_dev, int n, const dou
     cudaMemsetAsync(ccount.p, 0, sizeof(int) * ncell, s);
     cudaMemsetAsync(maxc.p, 0, sizeof(int), s);
     if (n > 0) {
-        { note_launch();
-        k_cell_ids<<<(n + 255) / 256, 256, 0, s>>>(n, g->pos.p, cg, cid.p, ccount.p); }
-        { note_launch();
-        k_scan_single<int, int><<<1, 1024, 0, s>>>(ncell, ccount.p, cstart.p); }
+        note_launch();
+        k_cell_ids<<<(n + 255) / 256, 256, 0, s>>>(n, g->pos.p, cg, cid.p, ccount.p);
+        note_launch();
+        k_scan_single<int, int><<<1, 1024, 0, s>>>(ncell, ccount.p, cstart.p);
         cudaMemcpyAsync(ccount.p, cstart.p, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, s);
-        { note_launch();
-        k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(n, cid.p, ccount.p, catoms.p); }
+        note_launch();
+        k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(n, cid.p, ccount.p, catoms.p);
         int threads = 256;
         int blocks = (int)(((int64_t)n * 32 + threads - 1) / threads);
-        { note_launch();
+        note_launch();
         k_pair_count<<<blocks, threads, 0, s>>>(n, g->pos.p, cg, cstart.p, catoms.p, rs, nr, r2max,
-                                                counts.p, maxc.p); }
+                                                counts.p, maxc.p);
         for (int r = 0; r < nr; ++r) {
-            { note_launch();
+            note_launch();
             k_scan_single<int64_t, int64_t>
-                <<<1, 1024, 0, s>>>(n, counts.p + (int64_t)r * n, g->pats[r].row_ptr.p); }
+                <<<1, 1024, 0, s>>>(n, counts.p + (int64_t)r * n, g->pats[r].row_ptr.p);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(set_error(LSQ_ERR_CUDA, cudaGetErrorString(e)));
@@ -477,9 +477,9 @@ extern "C" int lsq_build_neighbour_lists(const double *pos_dev, int n, const dou
         size_t smem = sizeof(int) * (size_t)std::max(m, 1);
         cudaFuncSetAttribute(k_pair_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(int) * kMaxRowCandidates));
-        { note_launch();
+        note_launch();
         k_pair_fill<<<n, threads, smem, s>>>(n, g->pos.p, cg, cstart.p, catoms.p, rs, nr, r2max,
-                                              dp.p, dc.p); }
+                                              dp.p, dc.p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(set_error(LSQ_ERR_CUDA, cudaGetErrorString(e)));
         // row lengths: max per pattern (host needs them for kernel limits)

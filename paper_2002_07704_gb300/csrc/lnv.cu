@@ -436,11 +436,12 @@ extern "C" int lsq_lnv_init_L(lsq_lnv c, const double *S, double *L, void *strea
     DevBuf<int> bad;
     LSQ_TRY(bad.alloc(1));
     LSQ_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int), s));
-    if (g->n > 0)
-        { note_launch();
+    if (g->n > 0) {
+        note_launch();
         k_onsite_inverse<<<(g->n + 127) / 128, 128, 0, s>>>(
             g->n, c->b, g->pats[c->rS].row_ptr.p, g->pats[c->rS].col.p, S,
-            g->pats[c->rL].row_ptr.p, g->pats[c->rL].col.p, L, bad.p); }
+            g->pats[c->rL].row_ptr.p, g->pats[c->rL].col.p, L, bad.p);
+    }
     LSQ_CHECK_LAUNCH();
     int hbad = 0;
     LSQ_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -454,17 +455,17 @@ namespace {
 // Prepares H', S_H (float64) and the reduced-precision copies for 'prec'.
 int prepare_hs(lsq_lnv c, const double *S, const double *H, double mu, int prec, cudaStream_t s) {
     int64_t nh = nvals(c, c->rH);
-    { note_launch();
+    note_launch();
     k_hprime<<<grid_for(nh), 256, 0, s>>>(c->g->pats[c->rH].nnzb, c->b * c->b, H, S, c->pos_s_in_h,
-                                          mu, c->Hp.p, c->Sh.p); }
+                                          mu, c->Hp.p, c->Sh.p);
     if (prec == LSQ_F32) {
-        { note_launch();
-        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Hp.p, (float *)c->Hpc.p); }
-        { note_launch();
-        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Sh.p, (float *)c->Shc.p); }
+        note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Hp.p, (float *)c->Hpc.p);
+        note_launch();
+        k_to_f32<<<grid_for(nh), 256, 0, s>>>(nh, c->Sh.p, (float *)c->Shc.p);
         int64_t ns = nvals(c, c->rS);
-        { note_launch();
-        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p); }
+        note_launch();
+        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p);
     }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
@@ -478,8 +479,8 @@ Ops operands(lsq_lnv c, const double *L, const double *S, int prec, cudaStream_t
     Ops o;
     if (prec == LSQ_F32) {
         int64_t nl = nvals(c, c->rL);
-        { note_launch();
-        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p); }
+        note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p);
         o.L = c->Lc.p;
         o.S = c->Sc.p;
         o.Hp = c->Hpc.p;
@@ -606,8 +607,8 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     const void *D = c->D.p;
     if (prec == LSQ_F32) {
         int64_t nl = nvals(c, c->rL);
-        { note_launch();
-        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, c->D.p, (float *)c->Dc.p); }
+        note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, c->D.p, (float *)c->Dc.p);
         D = c->Dc.p;
     }
     void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
@@ -728,14 +729,14 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
             }
             double beta = 0.0;
             if (it % o.cg_reset != 0 && gg_prev > 0.0) beta = std::max(0.0, (gg - ggp) / gg_prev);
-            { note_launch();
-            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, c->G.p, c->D.p); }
+            note_launch();
+            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, c->G.p, c->D.p);
             LSQ_CHECK_LAUNCH();
             double cc[3];
             LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
             if (cc[0] >= 0.0 && beta != 0.0) {  // not a descent direction: restart
-                { note_launch();
-                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, c->G.p, c->D.p); }
+                note_launch();
+                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, c->G.p, c->D.p);
                 LSQ_CHECK_LAUNCH();
                 LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
             }
@@ -747,8 +748,8 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
                 status = LSQ_ERR_UNSTABLE;
                 break;
             }
-            { note_launch();
-            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L); }
+            note_launch();
+            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L);
             LSQ_CHECK_LAUNCH();
             std::swap(c->G.p, c->Gp.p);
             gg_prev = gg;

@@ -430,24 +430,24 @@ static int launch_typed(lsq_geom g, int b, int mode, int chunk, const MMArgs &a,
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int threads = 512;
         int grid = occupancy_grid(g, kern, threads, smem);
-        { note_launch();
-        kern<<<grid, threads, smem, s>>>(a, chunk); }
+        note_launch();
+        kern<<<grid, threads, smem, s>>>(a, chunk);
     } else if (b == 4) {
         auto kern = k_mm_inner_b4<T, TA, TB, COUNT>;
         size_t smem = (size_t)g->n * sizeof(int);
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int threads = 512;
         int grid = occupancy_grid(g, kern, threads, smem);
-        { note_launch();
-        kern<<<grid, threads, smem, s>>>(a); }
+        note_launch();
+        kern<<<grid, threads, smem, s>>>(a);
     } else {
         auto kern = k_mm_inner_gen<T, TA, TB, COUNT>;
         size_t smem = (size_t)g->n * sizeof(int);
         LSQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int threads = 256;
         int grid = occupancy_grid(g, kern, threads, smem);
-        { note_launch();
-        kern<<<grid, threads, smem, s>>>(a, b); }
+        note_launch();
+        kern<<<grid, threads, smem, s>>>(a, b);
     }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
@@ -480,9 +480,9 @@ static int get_plan(lsq_geom g, int b, int dtype, int ra, int ta, int rb, int tb
     if (g->n > 0) {
         int threads = 256;
         int blocks = (int)(((int64_t)g->n * 32 + threads - 1) / threads);
-        { note_launch();
+        note_launch();
         k_mm_cost<<<blocks, threads, 0, s>>>(g->n, PA.row_ptr.p, PA.col.p, PB.row_ptr.p,
-                                             PC.row_ptr.p, PC.col.p, std::max(p.chunk, 1), cnt.p); }
+                                             PC.row_ptr.p, PC.col.p, std::max(p.chunk, 1), cnt.p);
         LSQ_CHECK_LAUNCH();
         LSQ_CUDA_TRY(cudaMemcpyAsync(h, cnt.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -647,16 +647,17 @@ int trace_into(lsq_geom g, int b, int dtype, int rx, const void *X, int ry, cons
     const int64_t *pm = nullptr;
     LSQ_TRY(get_posmap(g, rx, ry, 1, &pm, s));
     int64_t nnzb = g->pats[rx].nnzb;
-    if (dtype == LSQ_F64)
-        { note_launch();
+    if (dtype == LSQ_F64) {
+        note_launch();
         k_trace<double><<<kRedBlocks, kRedThreads, 0, s>>>(nnzb, b, (const double *)X,
-                                                           (const double *)Y, pm, g->red.partial.p); }
-    else
-        { note_launch();
+                                                           (const double *)Y, pm, g->red.partial.p);
+    } else {
+        note_launch();
         k_trace<float><<<kRedBlocks, kRedThreads, 0, s>>>(nnzb, b, (const float *)X,
-                                                          (const float *)Y, pm, g->red.partial.p); }
-    { note_launch();
-    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot); }
+                                                          (const float *)Y, pm, g->red.partial.p);
+    }
+    note_launch();
+    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -665,16 +666,17 @@ int dot_into(lsq_geom g, int b, int dtype, int r, const void *X, const void *Y, 
              cudaStream_t s) {
     LSQ_TRY(reducer_ensure(g, slot + 1));
     int64_t total = g->pats[r].nnzb * b * b;
-    if (dtype == LSQ_F64)
-        { note_launch();
+    if (dtype == LSQ_F64) {
+        note_launch();
         k_dot<double><<<kRedBlocks, kRedThreads, 0, s>>>(total, (const double *)X, (const double *)Y,
-                                                         g->red.partial.p); }
-    else
-        { note_launch();
+                                                         g->red.partial.p);
+    } else {
+        note_launch();
         k_dot<float><<<kRedBlocks, kRedThreads, 0, s>>>(total, (const float *)X, (const float *)Y,
-                                                        g->red.partial.p); }
-    { note_launch();
-    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot); }
+                                                        g->red.partial.p);
+    }
+    note_launch();
+    k_finish<<<1, 1024, 0, s>>>(g->red.partial.p, kRedBlocks, g->red.scalars.p + slot);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -180,6 +182,46 @@ template <> struct Row4<double> {
     }
 };
 
+// Blocks of A staged in shared memory are stored with a padded stride (20 floats, 18 doubles:
+// a multiple of 16 bytes) so that the lanes of a warp reading different blocks spread over
+// the banks instead of colliding on the 16-value period.
+template <typename T> struct SmemStride;
+template <> struct SmemStride<float> { static constexpr int v = 20; };
+template <> struct SmemStride<double> { static constexpr int v = 18; };
+
+// N consecutive values from shared memory (16-byte vector loads through a generic pointer;
+// the read-only global path must not be used on shared memory).
+template <typename T, int N>
+__device__ __forceinline__ void load_rows_shared(const T *p, T (&v)[N]) {
+    constexpr int per = 16 / sizeof(T);
+#pragma unroll
+    for (int k = 0; k < N; k += per) {
+        if (sizeof(T) == 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(p + k);
+            reinterpret_cast<float *>(v)[k] = x.x;
+            reinterpret_cast<float *>(v)[k + 1] = x.y;
+            reinterpret_cast<float *>(v)[k + 2] = x.z;
+            reinterpret_cast<float *>(v)[k + 3] = x.w;
+        } else {
+            const double2 x = *reinterpret_cast<const double2 *>(p + k);
+            reinterpret_cast<double *>(v)[k] = x.x;
+            reinterpret_cast<double *>(v)[k + 1] = x.y;
+        }
+    }
+}
+
+// Copies row i of A (na blocks of 16 values) into shared memory with the padded stride.
+template <typename T>
+__device__ __forceinline__ void stage_row(T *As, const T *__restrict__ A, int64_t a0, int64_t na) {
+    constexpr int per = 16 / sizeof(T);   // values per 16-byte vector
+    constexpr int vpb = 16 / per;         // vectors per block
+    constexpr int svb = SmemStride<T>::v / per;
+    for (int64_t e = threadIdx.x; e < na * vpb; e += blockDim.x) {
+        const int64_t blk = e / vpb, q = e - blk * vpb;
+        reinterpret_cast<float4 *>(As)[blk * svb + q] = reinterpret_cast<const float4 *>(A + 16 * a0)[e];
+    }
+}
+
 struct PlanArgs {
     int n;                      // atoms (rows)
     int upper;                  // compute only blocks with j >= i
@@ -299,10 +341,10 @@ __global__ void __launch_bounds__(1024) k_mm_plan_b4_smem(PlanArgs g) {
     const int r = sub >> 2, c = sub & 3;
     const int team = threadIdx.x >> 4, nteams = blockDim.x >> 4;
     for (int i = blockIdx.x; i < g.n; i += gridDim.x) {
-        const int64_t a0 = g.a_ptr[i], na = g.a_ptr[i + 1] - a0;
         __syncthreads();
-        for (int64_t e = threadIdx.x; e < na * 16; e += blockDim.x) As[e] = A[16 * a0 + e];
+        stage_row(As, A, g.a_ptr[i], g.a_ptr[i + 1] - g.a_ptr[i]);
         __syncthreads();
+        constexpr int AS = SmemStride<T>::v;
         const T *arow = As + 4 * r;
         for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
             const int64_t s = g.perm[e];
@@ -322,7 +364,7 @@ __global__ void __launch_bounds__(1024) k_mm_plan_b4_smem(PlanArgs g) {
                 T a[UNROLL][4], x[UNROLL][4];
 #pragma unroll
                 for (int u = 0; u < UNROLL; ++u) {
-                    const T *ap = arow + 16 * (w[u] & 0xffffu);
+                    const T *ap = arow + AS * (w[u] & 0xffffu);
 #pragma unroll
                     for (int t = 0; t < 4; ++t) a[u][t] = ap[t];
                     Row4<T>::load(xrow + 16 * (w[u] >> 16), x[u]);
@@ -334,7 +376,7 @@ __global__ void __launch_bounds__(1024) k_mm_plan_b4_smem(PlanArgs g) {
             }
             for (; q < nit; ++q) {
                 const uint32_t w0 = __ldg(it + q);
-                const T *ap = arow + 16 * (w0 & 0xffffu);
+                const T *ap = arow + AS * (w0 & 0xffffu);
                 T x0[4];
                 Row4<T>::load(xrow + 16 * (w0 >> 16), x0);
 #pragma unroll
@@ -344,6 +386,144 @@ __global__ void __launch_bounds__(1024) k_mm_plan_b4_smem(PlanArgs g) {
 #pragma unroll
             for (int u = 1; u < UNROLL; ++u) v += acc[u];
             plan_store(g, C, s, sub, v);
+        }
+    }
+}
+
+// Register-blocked schedule: a team of TEAM lanes per block (i, j) of C (TEAM = 4: each lane
+// a 2 x 2 sub-block; TEAM = 2: a 2 x 4 sub-block), so each lane receives fewer bytes per FMA
+// than with one element per lane (the 16-lane teams are bound by L1 register writeback).
+template <typename T, int TEAM>
+struct SubBlock {
+    static constexpr int CT = TEAM == 4 ? 2 : 4;  // columns per lane
+    static constexpr int RT = TEAM == 1 ? 4 : 2;  // rows per lane
+};
+
+// N consecutive values from global memory (read-only path).
+template <typename T, int N>
+__device__ __forceinline__ void load_rows(const T *__restrict__ p, T (&v)[N]) {
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+        T t[4];
+        Row4<T>::load(p + k, t);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[k + u] = t[u];
+    }
+}
+
+template <bool SMEM, typename T, int N>
+__device__ __forceinline__ void load_a(const T *p, T (&v)[N]) {
+    if (SMEM)
+        load_rows_shared(p, v);
+    else
+        load_rows(p, v);
+}
+
+// SPLIT > 1 (row schedule only): SPLIT consecutive teams share one block of C, each taking a
+// contiguous part of its list, and combine with warp shuffles (for rows of C shorter than the
+// number of teams of a thread block, e.g. products truncated to L's range).
+template <typename T, bool ROWS, int TEAM, bool SMEM = false, int SPLIT = 1>
+__global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4_rb(PlanArgs g) {
+    static_assert(TEAM * SPLIT <= 32, "a group of teams must fit in a warp");
+    constexpr int RT = SubBlock<T, TEAM>::RT, CT = SubBlock<T, TEAM>::CT;
+    constexpr int NCB = 4 / CT;  // column blocks per row block
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);  // row i of A (SMEM variant only)
+    const T *__restrict__ A = static_cast<const T *>(g.A);
+    const T *__restrict__ X = static_cast<const T *>(g.X);
+    T *__restrict__ C = static_cast<T *>(g.C);
+    const int sub = threadIdx.x % TEAM;
+    const int r0 = (sub / NCB) * RT, c0 = (sub % NCB) * CT;
+    auto work = [&](int64_t s, int i, int part) {
+        constexpr int AS = SMEM ? SmemStride<T>::v : 16;  // stride between blocks of A
+        const T *arow = (SMEM ? As : A + 16 * g.a_ptr[i]) + 4 * r0;
+        const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c0;
+        const int64_t i0 = g.item_ptr[s];
+        const int ntot = (int)(g.item_ptr[s + 1] - i0);
+        const int q0 = SPLIT == 1 ? 0 : (int)((int64_t)ntot * part / SPLIT);
+        const int q1 = SPLIT == 1 ? ntot : (int)((int64_t)ntot * (part + 1) / SPLIT);
+        const uint32_t *__restrict__ it = g.items + i0 + q0;
+        const int nit = q1 - q0;
+        T acc[RT][CT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) acc[r][c] = T(0);
+        int q = 0;
+        for (; q + 2 <= nit; q += 2) {
+            const uint32_t w0 = __ldg(it + q), w1 = __ldg(it + q + 1);
+            T a0[4 * RT], x0[4 * CT], a1[4 * RT], x1[4 * CT];
+            load_a<SMEM>(arow + AS * (w0 & 0xffffu), a0);
+            load_rows(xrow + 16 * (w0 >> 16), x0);
+            load_a<SMEM>(arow + AS * (w1 & 0xffffu), a1);
+            load_rows(xrow + 16 * (w1 >> 16), x1);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int c = 0; c < CT; ++c)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
+                        acc[r][c] = fma(a1[4 * r + t], x1[4 * c + t], acc[r][c]);
+                    }
+        }
+        if (q < nit) {
+            const uint32_t w0 = __ldg(it + q);
+            T a0[4 * RT], x0[4 * CT];
+            load_a<SMEM>(arow + AS * (w0 & 0xffffu), a0);
+            load_rows(xrow + 16 * (w0 >> 16), x0);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int c = 0; c < CT; ++c)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
+        }
+        if (SPLIT > 1) {
+            const int lane = threadIdx.x & 31;
+            const int gsz = TEAM * SPLIT;
+            const unsigned gmask = gsz == 32 ? 0xffffffffu : (((1u << gsz) - 1u) << (lane / gsz * gsz));
+#pragma unroll
+            for (int off = TEAM; off < gsz; off <<= 1)
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int c = 0; c < CT; ++c) acc[r][c] += __shfl_xor_sync(gmask, acc[r][c], off);
+            if (part != 0) return;
+        }
+        T *dst = C + 16 * s;
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+                const int e = (r0 + r) * 4 + c0 + c;
+                const T v = (T)g.alpha * acc[r][c];
+                dst[e] = g.beta != 0.0 ? fma((T)g.beta, dst[e], v) : v;
+            }
+    };
+    if (ROWS) {
+        const int team = threadIdx.x / TEAM / SPLIT, nteams = blockDim.x / TEAM / SPLIT;
+        const int part = (threadIdx.x / TEAM) % SPLIT;
+        for (int i = blockIdx.x; i < g.n; i += gridDim.x) {
+            if (SMEM) {
+                __syncthreads();
+                stage_row(As, A, g.a_ptr[i], g.a_ptr[i + 1] - g.a_ptr[i]);
+                __syncthreads();
+            }
+            for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
+                const int64_t s = g.perm[e];
+                if (g.upper && g.c_col[s] < i) continue;
+                work(s, i, part);
+            }
+        }
+    } else {
+        const int64_t team0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TEAM;
+        const int64_t nteams = ((int64_t)gridDim.x * blockDim.x) / TEAM;
+        for (int64_t t = team0; t < g.nblocks; t += nteams) {
+            const int64_t s = g.perm[t];
+            const int i = (int)g.c_row[s];
+            if (g.upper && g.c_col[s] < i) continue;
+            work(s, i, 0);
         }
     }
 }
@@ -445,15 +625,23 @@ const Variant *variants(int *count) {
         {k_mm_plan_b4<T, false, 2>, false, 256, false}, {k_mm_plan_b4<T, false, 4>, false, 256, false},
         {k_mm_plan_b4<T, true, 2>, true, 1024, false},  {k_mm_plan_b4<T, true, 4>, true, 1024, false},
         {k_mm_plan_b4_smem<T, 2>, true, 1024, true},    {k_mm_plan_b4_smem<T, 4>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, false, 4>, false, 256, false}, {k_mm_plan_b4_rb<T, true, 4>, true, 1024, false},
+        {k_mm_plan_b4_rb<T, false, 2>, false, 256, false}, {k_mm_plan_b4_rb<T, true, 2>, true, 1024, false},
+        {k_mm_plan_b4_rb<T, true, 1>, true, 1024, false},
+        {k_mm_plan_b4_rb<T, true, 4, true>, true, 1024, true}, {k_mm_plan_b4_rb<T, true, 2, true>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, true, 1, true>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, true, 4, true, 2>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, true, 4, true, 4>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, true, 4, false, 4>, true, 1024, false},
     };
-    *count = 6;
+    *count = 17;
     return v;
 }
 
 // Shared memory a variant needs for pattern ra (0 if none; -1 if it does not fit).
 int64_t variant_smem(lsq_geom g, const Variant &v, int ra, size_t es) {
     if (!v.smem_a) return 0;
-    const int64_t need = (int64_t)g->pats[ra].max_row * 16 * (int64_t)es;
+    const int64_t need = (int64_t)g->pats[ra].max_row * (es == 8 ? 18 : 20) * (int64_t)es;
     return need + 1024 <= (int64_t)g->smem_optin ? need : -1;
 }
 
@@ -471,6 +659,7 @@ int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks
     else
         grid = (int)std::max<int64_t>(1, std::min<int64_t>((nblocks * 16 + v.threads - 1) / v.threads,
                                                            (int64_t)g->num_sms * per_sm));
+    // (a grid-wide schedule never needs more threads than 16 per block of C)
     note_launch();
     v.k<<<grid, v.threads, (size_t)smem, s>>>(a);
     LSQ_CHECK_LAUNCH();
@@ -502,6 +691,11 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
     int nv = 0;
     const Variant *v = dtype == LSQ_F64 ? variants<double>(&nv) : variants<float>(&nv);
     int &choice = p.variant[dtype == LSQ_F64 ? 0 : 1];
+    if (const char *force = std::getenv("LSQ_PLAN_VARIANT")) {
+        // a fixed schedule (tests exercise every variant this way)
+        const int k = std::atoi(force);
+        if (k >= 0 && k < nv && variant_smem(g, v[k], ra, dtype_size(dtype)) >= 0) choice = k;
+    }
     if (choice < 0) {
         // autotune: time every variant once on this product (each writes the same C), keep
         // the fastest for later calls.  Runs when beta == 0 so repeated runs are harmless.
@@ -531,6 +725,10 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
             cudaEventDestroy(e1);
             choice = bi;
             p.tuned_ms[dtype == LSQ_F64 ? 0 : 1] = best;
+            if (std::getenv("LSQ_TUNE_LOG"))
+                std::fprintf(stderr, "lsq autotune: ranges (%g, %g, %g)%s %s: variant %d, %.3f ms\n",
+                             g->pats[ra].R, g->pats[rb].R, g->pats[rc].R, p.upper ? " upper" : "",
+                             dtype == LSQ_F64 ? "f64" : "f32", bi, best);
         }
     }
     LSQ_TRY(run_variant(g, v[choice], a, p.nblocks, s, variant_smem(g, v[choice], ra, dtype_size(dtype))));
