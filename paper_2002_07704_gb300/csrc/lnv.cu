@@ -541,8 +541,8 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     // scalar slots: 0 = Tr[H' LSL], 1 = <LSL, Q>, 2 = Tr[S LSL], 3 = <LSL, SLS>
     LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 1, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
-    // 4 x 4 blocks: transposed operands are materialised so the plan kernel reads rows; other
-    // block sizes use the plan-free kernels, which read transposes through the transpose map
+    // 4 x 4 blocks: transposed operands are materialised so the plan kernel reads rows; the
+    // kernel for other block sizes reads transposes through the transpose map
     const bool mat = c->b == 4;
     const void *LSop = mat ? c->SL.p : c->LS.p;  // operand giving LS as op(B)
     const int tLS = mat ? 1 : 0;

@@ -153,6 +153,9 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
 int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out, cudaStream_t s);
 int plan_launch(lsq_geom g, int dtype, const ProductPlan &p, int ra, int rb, int rc, const void *Aop,
                 const void *X, void *C, double alpha, double beta, cudaStream_t s);
+// Plan-driven product for any block size; transposed operands read through transpose maps.
+int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, int ta, int rb, int tb, int rc,
+                    const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s);
 // out = X^T on the (symmetric) pattern r: out_ij = (X_ji)^T.
 int transpose_on(lsq_geom g, int r, int b, int dtype, const void *X, void *out, cudaStream_t s);
 

@@ -564,6 +564,18 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
         if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
         (void)cudaGetLastError();  // a failed allocation is not sticky; drop it
         clear_error();             // and fall back to the plan-free forms below
+    } else {
+        // any other block size: plan-driven warp-per-block kernel (no scratch)
+        ProductPlan *pp = nullptr;
+        int prc = plan_build(g, ra, rb, rc, (sym && beta == 0.0) ? 1 : 0, &pp, s);
+        if (prc == LSQ_OK) {
+            if (triples) *triples = pp->triples;
+            if (g->n == 0 || g->pats[rc].nnzb == 0) return LSQ_OK;
+            return plan_launch_gen(g, b, dtype, *pp, ra, ta, rb, tb, rc, A, B, C, alpha, beta, s);
+        }
+        if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
+        (void)cudaGetLastError();
+        clear_error();
     }
     Plan *p = nullptr;
     LSQ_TRY(get_plan(g, b, dtype, ra, ta, rb, tb, rc, a, &p, s));

@@ -421,9 +421,13 @@ __device__ __forceinline__ void load_a(const T *p, T (&v)[N]) {
 
 // SPLIT > 1 (row schedule only): SPLIT consecutive teams share one block of C, each taking a
 // contiguous part of its list, and combine with warp shuffles (for rows of C shorter than the
-// number of teams of a thread block, e.g. products truncated to L's range).
-template <typename T, bool ROWS, int TEAM, bool SMEM = false, int SPLIT = 1>
-__global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4_rb(PlanArgs g) {
+// number of teams of a thread block, e.g. products truncated to L's range).  With IL the teams
+// take the list interleaved instead (team p items p, p + SPLIT, ...): a list is sorted by k, so
+// the teams of a group then read neighbouring blocks of A (distinct shared-memory banks) and of
+// B^T (shared cache lines).  THREADS fixes the block size, and with it the register budget.
+template <typename T, bool ROWS, int TEAM, bool SMEM = false, int SPLIT = 1, bool IL = false,
+          int THREADS = (ROWS ? 1024 : 256)>
+__global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
     static_assert(TEAM * SPLIT <= 32, "a group of teams must fit in a warp");
     constexpr int RT = SubBlock<T, TEAM>::RT, CT = SubBlock<T, TEAM>::CT;
     constexpr int NCB = 4 / CT;  // column blocks per row block
@@ -440,18 +444,18 @@ __global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4_rb(PlanArgs g)
         const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c0;
         const int64_t i0 = g.item_ptr[s];
         const int ntot = (int)(g.item_ptr[s + 1] - i0);
-        const int q0 = SPLIT == 1 ? 0 : (int)((int64_t)ntot * part / SPLIT);
-        const int q1 = SPLIT == 1 ? ntot : (int)((int64_t)ntot * (part + 1) / SPLIT);
-        const uint32_t *__restrict__ it = g.items + i0 + q0;
-        const int nit = q1 - q0;
+        constexpr int STEP = IL ? SPLIT : 1;
+        const int q0 = IL ? part : (SPLIT == 1 ? 0 : (int)((int64_t)ntot * part / SPLIT));
+        const int nit = IL ? ntot : (SPLIT == 1 ? ntot : (int)((int64_t)ntot * (part + 1) / SPLIT));
+        const uint32_t *__restrict__ it = g.items + i0;
         T acc[RT][CT];
 #pragma unroll
         for (int r = 0; r < RT; ++r)
 #pragma unroll
             for (int c = 0; c < CT; ++c) acc[r][c] = T(0);
-        int q = 0;
-        for (; q + 2 <= nit; q += 2) {
-            const uint32_t w0 = __ldg(it + q), w1 = __ldg(it + q + 1);
+        int q = q0;
+        for (; q + STEP < nit; q += 2 * STEP) {
+            const uint32_t w0 = __ldg(it + q), w1 = __ldg(it + q + STEP);
             T a0[4 * RT], x0[4 * CT], a1[4 * RT], x1[4 * CT];
             load_a<SMEM>(arow + AS * (w0 & 0xffffu), a0);
             load_rows(xrow + 16 * (w0 >> 16), x0);
@@ -528,6 +532,76 @@ __global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4_rb(PlanArgs g)
     }
 }
 
+// Any block size b <= 16: one warp per block of C.  Per item the warp stages op(A)_ik and
+// X_jk = op(B)_kj^T in shared memory (transposing on the way when an operand is read through
+// its transpose map), then lane l computes row l % b of C_ij over a slice of its columns.
+struct PlanArgsGen {
+    PlanArgs p;
+    int b;
+    const int64_t *a_tm;  // transpose map of A's pattern (TA)
+    const int64_t *b_tm;  // transpose map of B's pattern (!TB)
+};
+
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
+    const PlanArgs &g = ga.p;
+    const int b = ga.b, bb = b * b;
+    __shared__ T stage[8][2][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T *As = stage[w][0], *Xs = stage[w][1];
+    const T *__restrict__ A = static_cast<const T *>(g.A);
+    const T *__restrict__ X = static_cast<const T *>(g.X);
+    T *__restrict__ C = static_cast<T *>(g.C);
+    const int nparts = 32 / b;                // lanes per row of C
+    const int cw = (b + nparts - 1) / nparts;  // columns per lane (<= 8 for b <= 16)
+    const int r = lane % b, part = lane / b;
+    const bool active = part < nparts;
+    const int cbeg = min(b, part * cw), cend = min(b, cbeg + cw);
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = w0; t < g.nblocks; t += nw) {
+        const int64_t s = g.perm[t];
+        const int i = (int)g.c_row[s];
+        if (g.upper && g.c_col[s] < i) continue;
+        const int j = g.c_col[s];
+        const int64_t abase = g.a_ptr[i], xbase = g.x_ptr[j];
+        const int64_t i0 = g.item_ptr[s], i1 = g.item_ptr[s + 1];
+        T acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = T(0);
+        for (int64_t q = i0; q < i1; ++q) {
+            const uint32_t it = __ldg(g.items + q);
+            const int64_t pa = abase + (it & 0xffffu), px = xbase + (it >> 16);
+            const T *ab = A + (int64_t)bb * (TA ? ga.a_tm[pa] : pa);
+            const T *xb = X + (int64_t)bb * (TB ? px : ga.b_tm[px]);
+            __syncwarp();
+            for (int e = lane; e < bb; e += 32) {
+                const int u = e / b, v = e - u * b;
+                As[e] = TA ? ab[v * b + u] : ab[e];  // As[u][v] = op(A)_ik[u][v]
+                Xs[e] = TB ? xb[e] : xb[v * b + u];  // Xs[u][v] = X_jk[u][v] = op(B)_kj[v][u]
+            }
+            __syncwarp();
+            if (active) {
+                for (int tt = 0; tt < b; ++tt) {
+                    const T a = As[r * b + tt];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (cbeg + c < cend) acc[c] = fma(a, Xs[(cbeg + c) * b + tt], acc[c]);
+                }
+            }
+        }
+        if (active) {
+            T *dst = C + (int64_t)bb * s + r * b;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (cbeg + c < cend) {
+                    const T v = (T)g.alpha * acc[c];
+                    dst[cbeg + c] = g.beta != 0.0 ? fma((T)g.beta, dst[cbeg + c], v) : v;
+                }
+        }
+    }
+}
+
 // Lower blocks of a symmetric result: C_ij = (C_ji)^T for j < i (tm: transpose map of C's pattern).
 template <typename T>
 __global__ void k_mirror_lower(int n, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
@@ -542,6 +616,36 @@ __global__ void k_mirror_lower(int n, const int64_t *__restrict__ c_ptr, const i
         if (c_col[p] >= i) continue;
         C[e] = C[tm[p] * 16 + (rc & 3) * 4 + (rc >> 2)];
     }
+}
+
+template <typename T>
+__global__ void k_mirror_lower_gen(int n, int b, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
+                                   const int64_t *__restrict__ tm, T *__restrict__ C) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int i = warp, bb = b * b;
+    for (int64_t e = c_ptr[i] * bb + lane; e < c_ptr[i + 1] * bb; e += 32) {
+        const int64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        if (c_col[p] >= i) continue;
+        const int r = rc / b, c = rc - r * b;
+        C[e] = C[tm[p] * bb + c * b + r];
+    }
+}
+
+int mirror_lower_gen(lsq_geom g, int rc, int b, int dtype, void *C, cudaStream_t s) {
+    LSQ_TRY(ensure_tmap(g, rc, s));
+    const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);
+    note_launch();
+    if (dtype == LSQ_F64)
+        k_mirror_lower_gen<double><<<blocks, 256, 0, s>>>(g->n, b, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
+                                                           g->pats[rc].tmap.p, (double *)C);
+    else
+        k_mirror_lower_gen<float><<<blocks, 256, 0, s>>>(g->n, b, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
+                                                          g->pats[rc].tmap.p, (float *)C);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
 }
 
 __global__ void k_rows_of(int n, const int64_t *__restrict__ c_ptr, int64_t *__restrict__ c_row) {
@@ -633,8 +737,14 @@ const Variant *variants(int *count) {
         {k_mm_plan_b4_rb<T, true, 4, true, 2>, true, 1024, true},
         {k_mm_plan_b4_rb<T, true, 4, true, 4>, true, 1024, true},
         {k_mm_plan_b4_rb<T, true, 4, false, 4>, true, 1024, false},
+        {k_mm_plan_b4_rb<T, true, 4, true, 2, true>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, true, 4, true, 4, true>, true, 1024, true},
+        {k_mm_plan_b4_rb<T, true, 2, true, 4, true, 512>, true, 512, true},
+        {k_mm_plan_b4_rb<T, true, 1, true, 4, true, 256>, true, 256, true},
+        {k_mm_plan_b4_rb<T, true, 1, true, 8, true, 256>, true, 256, true},
+        {k_mm_plan_b4_rb<T, true, 1, false, 8, true, 256>, true, 256, false},
     };
-    *count = 17;
+    *count = 23;
     return v;
 }
 
@@ -743,6 +853,53 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
             k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->n, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
                                                           g->pats[rc].tmap.p, (float *)C);
         LSQ_CHECK_LAUNCH();
+    }
+    return LSQ_OK;
+}
+
+int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, int ta, int rb, int tb, int rc,
+                    const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s) {
+    if (p.nblocks == 0) return LSQ_OK;
+    PlanArgsGen ga;
+    PlanArgs &a = ga.p;
+    a.n = g->n;
+    a.upper = p.upper;
+    a.c_ptr = g->pats[rc].row_ptr.p;
+    a.nblocks = p.nblocks;
+    a.perm = p.perm.p;
+    a.item_ptr = p.item_ptr.p;
+    a.items = p.items.p;
+    a.a_ptr = g->pats[ra].row_ptr.p;
+    a.x_ptr = g->pats[rb].row_ptr.p;
+    a.c_row = p.c_row.p;
+    a.c_col = g->pats[rc].col.p;
+    a.A = A;
+    a.X = B;
+    a.C = C;
+    a.alpha = alpha;
+    a.beta = beta;
+    ga.b = b;
+    ga.a_tm = g->pats[ra].tmap.p;
+    ga.b_tm = g->pats[rb].tmap.p;
+    const int threads = 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((p.nblocks + 7) / 8, (int64_t)g->num_sms * 8));
+    note_launch();
+    auto go = [&](auto kern) { kern<<<grid, threads, 0, s>>>(ga); };
+    if (dtype == LSQ_F64) {
+        if (ta && tb) go(k_mm_plan_gen<double, true, true>);
+        else if (ta) go(k_mm_plan_gen<double, true, false>);
+        else if (tb) go(k_mm_plan_gen<double, false, true>);
+        else go(k_mm_plan_gen<double, false, false>);
+    } else {
+        if (ta && tb) go(k_mm_plan_gen<float, true, true>);
+        else if (ta) go(k_mm_plan_gen<float, true, false>);
+        else if (tb) go(k_mm_plan_gen<float, false, true>);
+        else go(k_mm_plan_gen<float, false, false>);
+    }
+    LSQ_CHECK_LAUNCH();
+    if (p.upper) {
+        // C_ij = (C_ji)^T for j < i, any block size
+        LSQ_TRY(mirror_lower_gen(g, rc, b, dtype, C, s));
     }
     return LSQ_OK;
 }
