@@ -135,7 +135,10 @@ int lsq_pattern_copy(lsq_geom g, int range_id, int64_t *row_ptr_dev, int32_t *co
  *
  * A_dev, B_dev, C_dev: block arrays on patterns range_a, range_b, range_c
  * of g with block size b (1..16), dtype given by precision.  C must not
- * alias A or B.  The first call for a (range_a, range_b, range_c, trans)
+ * alias A or B.  Arrays need only the alignment of their value type: with
+ * b = 4, 16-byte aligned arrays run the vectorised 4 x 4 kernels (32-byte
+ * aligned ones may also use 32-byte loads), others the general kernel.
+ * The first call for a (range_a, range_b, range_c, trans)
  * combination builds and caches a product plan (allocates device memory,
  * synchronises); later calls allocate nothing.  n_triples_host (optional)
  * receives the number of block triples (i, k, j) of the product; the

@@ -304,12 +304,12 @@ class Lnv:
 
     def minimise_batch(self, L, S, H, mu, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
                        precision=F64, refine_iter=2, spin=2.0, graph=True, stream=None,
-                       raise_on_status=False):
+                       raise_on_status=False, final_eval=True):
         """Minimises every system of a concatenated geometry; mu: one value per system."""
         import torch
         mu = [float(m) for m in mu]
-        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin, 1, 0,
-                    int(bool(graph)))
+        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
+                    int(bool(final_eval)), 0, int(bool(graph)))
         reps = (LnvReport * len(mu))()
         f = torch.float64
         rc = _lib.lsq_lnv_minimise_batch(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),

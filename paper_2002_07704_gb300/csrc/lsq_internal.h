@@ -92,6 +92,7 @@ struct ProductPlan {
     int64_t nitems = 0;
     int upper = 0;         // only blocks with j >= i are computed; the rest mirrored
     int variant[2] = {-1, -1};      // kernel schedule picked by the autotuner (f64, f32)
+    int variant16[2] = {-1, -1};    // the fastest of those needing only 16-byte alignment
     float tuned_ms[2] = {0.f, 0.f};
     DevBuf<int64_t> perm;      // blocks of C in processing order (sorted by list length per row)
     DevBuf<int32_t> cnt;       // list length per block of C

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <string>
 
 #include "lsq_internal.h"
@@ -538,7 +539,10 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     a.alpha = alpha;
     a.beta = beta;
     a.triples = nullptr;
-    if (b == 4) {
+    // the 4 x 4 kernels read blocks in 16-byte vectors; other matrices take the general kernel
+    const bool al16 = (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) |
+                       reinterpret_cast<uintptr_t>(C)) % 16 == 0;
+    if (b == 4 && al16) {
         // plan-driven form: op(A) rows and op(B)^T rows, transposing into scratch if needed
         ProductPlan *pp = nullptr;
         int prc = plan_build(g, ra, rb, rc, (sym && beta == 0.0) ? 1 : 0, &pp, s);
@@ -565,7 +569,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
         (void)cudaGetLastError();  // a failed allocation is not sticky; drop it
         clear_error();             // and fall back to the plan-free forms below
     } else {
-        // any other block size: plan-driven warp-per-block kernel (no scratch)
+        // any other block size (or unaligned 4 x 4 blocks): warp-per-block kernel, no scratch
         ProductPlan *pp = nullptr;
         int prc = plan_build(g, ra, rb, rc, (sym && beta == 0.0) ? 1 : 0, &pp, s);
         if (prc == LSQ_OK) {
@@ -577,6 +581,9 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
         (void)cudaGetLastError();
         clear_error();
     }
+    if (b == 4 && !al16)
+        return set_error(LSQ_ERR_OOM, "no device memory for a product plan, and the plan-free 4 x 4 "
+                                      "kernels need 16-byte aligned matrices");
     Plan *p = nullptr;
     LSQ_TRY(get_plan(g, b, dtype, ra, ta, rb, tb, rc, a, &p, s));
     if (triples) *triples = p->triples;

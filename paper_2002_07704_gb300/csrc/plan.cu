@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -411,12 +412,44 @@ __device__ __forceinline__ void load_rows(const T *__restrict__ p, T (&v)[N]) {
     }
 }
 
-template <bool SMEM, typename T, int N>
-__device__ __forceinline__ void load_a(const T *p, T (&v)[N]) {
-    if (SMEM)
-        load_rows_shared(p, v);
+// N consecutive values from global memory in 32-byte loads (read-only path; p must be
+// 32-byte aligned).  Half as many load instructions as load_rows for the same bytes, so the
+// lanes of a warp touch each cache line in half as many L1 wavefronts.
+template <typename T, int N>
+__device__ __forceinline__ void load_rows_256(const T *__restrict__ p, T (&v)[N]) {
+    const size_t ga = __cvta_generic_to_global(p);
+    if constexpr (sizeof(T) == 4) {
+        static_assert(N % 8 == 0, "whole 32-byte vectors");
+#pragma unroll
+        for (int k = 0; k < N; k += 8)
+            asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=f"(v[k]), "=f"(v[k + 1]), "=f"(v[k + 2]), "=f"(v[k + 3]), "=f"(v[k + 4]),
+                  "=f"(v[k + 5]), "=f"(v[k + 6]), "=f"(v[k + 7])
+                : "l"(ga + 4 * k));
+    } else {
+        static_assert(N % 4 == 0, "whole 32-byte vectors");
+#pragma unroll
+        for (int k = 0; k < N; k += 4)
+            asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];"
+                : "=d"(v[k]), "=d"(v[k + 1]), "=d"(v[k + 2]), "=d"(v[k + 3])
+                : "l"(ga + 8 * k));
+    }
+}
+
+template <bool W256, typename T, int N>
+__device__ __forceinline__ void load_x(const T *p, T (&v)[N]) {
+    if constexpr (W256)
+        load_rows_256(p, v);
     else
         load_rows(p, v);
+}
+
+template <bool SMEM, typename T, int N, bool W256 = false>
+__device__ __forceinline__ void load_a(const T *p, T (&v)[N]) {
+    if constexpr (SMEM)
+        load_rows_shared(p, v);
+    else
+        load_x<W256>(p, v);
 }
 
 // SPLIT > 1 (row schedule only): SPLIT consecutive teams share one block of C, each taking a
@@ -426,7 +459,7 @@ __device__ __forceinline__ void load_a(const T *p, T (&v)[N]) {
 // the teams of a group then read neighbouring blocks of A (distinct shared-memory banks) and of
 // B^T (shared cache lines).  THREADS fixes the block size, and with it the register budget.
 template <typename T, bool ROWS, int TEAM, bool SMEM = false, int SPLIT = 1, bool IL = false,
-          int THREADS = (ROWS ? 1024 : 256)>
+          int THREADS = (ROWS ? 1024 : 256), bool W256 = false>
 __global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
     static_assert(TEAM * SPLIT <= 32, "a group of teams must fit in a warp");
     constexpr int RT = SubBlock<T, TEAM>::RT, CT = SubBlock<T, TEAM>::CT;
@@ -454,13 +487,18 @@ __global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
 #pragma unroll
             for (int c = 0; c < CT; ++c) acc[r][c] = T(0);
         int q = q0;
+        // the next pair of item words is fetched while the current pair's blocks load, so a
+        // pair costs one trip to L2 instead of two dependent ones
+        uint32_t w0 = q < nit ? __ldg(it + q) : 0u, w1 = q + STEP < nit ? __ldg(it + q + STEP) : 0u;
         for (; q + STEP < nit; q += 2 * STEP) {
-            const uint32_t w0 = __ldg(it + q), w1 = __ldg(it + q + STEP);
+            const int qn = q + 2 * STEP;
+            const uint32_t n0 = qn < nit ? __ldg(it + qn) : 0u;
+            const uint32_t n1 = qn + STEP < nit ? __ldg(it + qn + STEP) : 0u;
             T a0[4 * RT], x0[4 * CT], a1[4 * RT], x1[4 * CT];
-            load_a<SMEM>(arow + AS * (w0 & 0xffffu), a0);
-            load_rows(xrow + 16 * (w0 >> 16), x0);
-            load_a<SMEM>(arow + AS * (w1 & 0xffffu), a1);
-            load_rows(xrow + 16 * (w1 >> 16), x1);
+            load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w0 & 0xffffu), a0);
+            load_x<W256>(xrow + 16 * (w0 >> 16), x0);
+            load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w1 & 0xffffu), a1);
+            load_x<W256>(xrow + 16 * (w1 >> 16), x1);
 #pragma unroll
             for (int r = 0; r < RT; ++r)
 #pragma unroll
@@ -470,12 +508,13 @@ __global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
                         acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
                         acc[r][c] = fma(a1[4 * r + t], x1[4 * c + t], acc[r][c]);
                     }
+            w0 = n0;
+            w1 = n1;
         }
         if (q < nit) {
-            const uint32_t w0 = __ldg(it + q);
             T a0[4 * RT], x0[4 * CT];
-            load_a<SMEM>(arow + AS * (w0 & 0xffffu), a0);
-            load_rows(xrow + 16 * (w0 >> 16), x0);
+            load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w0 & 0xffffu), a0);
+            load_x<W256>(xrow + 16 * (w0 >> 16), x0);
 #pragma unroll
             for (int r = 0; r < RT; ++r)
 #pragma unroll
@@ -618,6 +657,105 @@ __global__ void k_mirror_lower(int n, const int64_t *__restrict__ c_ptr, const i
     }
 }
 
+// Block sizes 9..16 (the 13-orbital model): one warp per block of C.  Per item, op(A)_ik and
+// B^T_jk are staged transposed in shared memory (At[t][r] = op(A)_ik[r][t], Xt[t][c] =
+// op(B)_kj[t][c]) inside a 16 x 16 frame, and lane l accumulates the 4 x 2 tile of C_ij at rows
+// 4(l / 8) and columns 2(l % 8): per t one 4-vector of At and one 2-vector of Xt feed 8 FMAs.
+// The next item's blocks are fetched into registers while the current one is multiplied.
+// Frame entries beyond b are never initialised; they only reach accumulators that are not stored.
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
+    const PlanArgs &g = ga.p;
+    const int b = ga.b, bb = b * b;
+    constexpr int ST = 20;  // frame row stride: 16-byte rows for float and double
+    constexpr int PF = 8;   // values of a block per lane (256 / 32)
+    __shared__ __align__(16) T stage[8][2][16 * ST];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T *At = stage[w][0], *Xt = stage[w][1];
+    const int r0 = 4 * (lane >> 3), c0 = 2 * (lane & 7);
+    const T *__restrict__ A = static_cast<const T *>(g.A);
+    const T *__restrict__ X = static_cast<const T *>(g.X);
+    T *__restrict__ C = static_cast<T *>(g.C);
+    // frame offsets of the source elements e = lane + 32 k, fixed for the whole kernel
+    int offA[PF], offX[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        const int e = lane + 32 * k;
+        const int u = e / b, v = e - u * b;  // element (u, v) of the source block
+        offA[k] = TA ? u * ST + v : v * ST + u;
+        offX[k] = TB ? v * ST + u : u * ST + v;
+    }
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = w0; t < g.nblocks; t += nw) {
+        const int64_t s = g.perm[t];
+        const int i = (int)g.c_row[s];
+        if (g.upper && g.c_col[s] < i) continue;
+        const int j = g.c_col[s];
+        const int64_t abase = g.a_ptr[i], xbase = g.x_ptr[j];
+        const int64_t i0 = g.item_ptr[s], i1 = g.item_ptr[s + 1];
+        T acc[4][2];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = T(0);
+        T pa[PF], px[PF];
+        auto fetch = [&](int64_t q) {
+            const uint32_t it = __ldg(g.items + q);
+            const int64_t qa = abase + (it & 0xffffu), qx = xbase + (it >> 16);
+            const T *ab = A + (int64_t)bb * (TA ? ga.a_tm[qa] : qa);
+            const T *xb = X + (int64_t)bb * (TB ? qx : ga.b_tm[qx]);
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const int e = lane + 32 * k;
+                if (e < bb) {
+                    pa[k] = __ldg(ab + e);
+                    px[k] = __ldg(xb + e);
+                }
+            }
+        };
+        if (i0 < i1) fetch(i0);
+        for (int64_t q = i0; q < i1; ++q) {
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                if (lane + 32 * k < bb) {
+                    At[offA[k]] = pa[k];
+                    Xt[offX[k]] = px[k];
+                }
+            }
+            __syncwarp();
+            if (q + 1 < i1) fetch(q + 1);
+            for (int tt = 0; tt < b; ++tt) {
+                T a[4], x[2];
+                load_rows_shared(At + tt * ST + r0, a);
+                if constexpr (sizeof(T) == 4) {
+                    const float2 v = *reinterpret_cast<const float2 *>(Xt + tt * ST + c0);
+                    x[0] = v.x;
+                    x[1] = v.y;
+                } else {
+                    const double2 v = *reinterpret_cast<const double2 *>(Xt + tt * ST + c0);
+                    x[0] = v.x;
+                    x[1] = v.y;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc[r][0] = fma(a[r], x[0], acc[r][0]);
+                    acc[r][1] = fma(a[r], x[1], acc[r][1]);
+                }
+            }
+        }
+        T *dst = C + (int64_t)bb * s;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                if (r0 + r < b && c0 + c < b) {
+                    const int e = (r0 + r) * b + c0 + c;
+                    const T v = (T)g.alpha * acc[r][c];
+                    dst[e] = g.beta != 0.0 ? fma((T)g.beta, dst[e], v) : v;
+                }
+    }
+}
+
 template <typename T>
 __global__ void k_mirror_lower_gen(int n, int b, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
                                    const int64_t *__restrict__ tm, T *__restrict__ C) {
@@ -722,6 +860,7 @@ struct Variant {
     bool rows;
     int threads;
     bool smem_a;  // stages the row of A in shared memory (16 values per block of the longest row)
+    bool w256 = false;  // 32-byte global loads: A (unless staged) and B^T must be 32-byte aligned
 };
 template <typename T>
 const Variant *variants(int *count) {
@@ -743,8 +882,14 @@ const Variant *variants(int *count) {
         {k_mm_plan_b4_rb<T, true, 1, true, 4, true, 256>, true, 256, true},
         {k_mm_plan_b4_rb<T, true, 1, true, 8, true, 256>, true, 256, true},
         {k_mm_plan_b4_rb<T, true, 1, false, 8, true, 256>, true, 256, false},
+        {k_mm_plan_b4_rb<T, true, 4, true, 2, true, 1024, true>, true, 1024, true, true},
+        {k_mm_plan_b4_rb<T, true, 4, true, 4, true, 1024, true>, true, 1024, true, true},
+        {k_mm_plan_b4_rb<T, true, 4, true, 8, true, 1024, true>, true, 1024, true, true},
+        {k_mm_plan_b4_rb<T, true, 2, true, 4, true, 512, true>, true, 512, true, true},
+        {k_mm_plan_b4_rb<T, true, 1, true, 8, true, 256, true>, true, 256, true, true},
+        {k_mm_plan_b4_rb<T, false, 4, false, 1, false, 256, true>, false, 256, false, true},
     };
-    *count = 23;
+    *count = 29;
     return v;
 }
 
@@ -800,11 +945,18 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
     a.beta = beta;
     int nv = 0;
     const Variant *v = dtype == LSQ_F64 ? variants<double>(&nv) : variants<float>(&nv);
-    int &choice = p.variant[dtype == LSQ_F64 ? 0 : 1];
+    const int di = dtype == LSQ_F64 ? 0 : 1;
+    int &choice = p.variant[di];
+    // variants with 32-byte loads need 32-byte aligned operands (the blocks then are too)
+    const bool al32 = reinterpret_cast<uintptr_t>(Aop) % 32 == 0 && reinterpret_cast<uintptr_t>(X) % 32 == 0;
+    auto smem_for = [&](int k) -> int64_t {
+        if (v[k].w256 && !al32) return -1;
+        return variant_smem(g, v[k], ra, dtype_size(dtype));
+    };
     if (const char *force = std::getenv("LSQ_PLAN_VARIANT")) {
         // a fixed schedule (tests exercise every variant this way)
         const int k = std::atoi(force);
-        if (k >= 0 && k < nv && variant_smem(g, v[k], ra, dtype_size(dtype)) >= 0) choice = k;
+        if (k >= 0 && k < nv && smem_for(k) >= 0) choice = k;
     }
     if (choice < 0) {
         // autotune: time every variant once on this product (each writes the same C), keep
@@ -815,10 +967,10 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
             cudaEvent_t e0, e1;
             LSQ_CUDA_TRY(cudaEventCreate(&e0));
             LSQ_CUDA_TRY(cudaEventCreate(&e1));
-            float best = 1e30f;
-            int bi = 0;
+            float best = 1e30f, best16 = 1e30f;
+            int bi = 0, bi16 = 0;
             for (int k = 0; k < nv; ++k) {
-                const int64_t sm = variant_smem(g, v[k], ra, dtype_size(dtype));
+                const int64_t sm = smem_for(k);
                 if (sm < 0) continue;
                 LSQ_CUDA_TRY(cudaEventRecord(e0, s));
                 LSQ_TRY(run_variant(g, v[k], a, p.nblocks, s, sm));
@@ -830,18 +982,25 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
                     best = ms;
                     bi = k;
                 }
+                if (!v[k].w256 && ms < best16) {
+                    best16 = ms;
+                    bi16 = k;
+                }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             choice = bi;
-            p.tuned_ms[dtype == LSQ_F64 ? 0 : 1] = best;
+            p.variant16[di] = bi16;
+            p.tuned_ms[di] = best;
             if (std::getenv("LSQ_TUNE_LOG"))
                 std::fprintf(stderr, "lsq autotune: ranges (%g, %g, %g)%s %s: variant %d, %.3f ms\n",
                              g->pats[ra].R, g->pats[rb].R, g->pats[rc].R, p.upper ? " upper" : "",
                              dtype == LSQ_F64 ? "f64" : "f32", bi, best);
         }
     }
-    LSQ_TRY(run_variant(g, v[choice], a, p.nblocks, s, variant_smem(g, v[choice], ra, dtype_size(dtype))));
+    // a later call may pass operands that the tuned variant cannot read
+    const int use = smem_for(choice) >= 0 ? choice : std::max(p.variant16[di], 0);
+    LSQ_TRY(run_variant(g, v[use], a, p.nblocks, s, smem_for(use)));
     if (p.upper) {
         LSQ_TRY(ensure_tmap(g, rc, s));
         const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);
@@ -885,16 +1044,17 @@ int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, 
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((p.nblocks + 7) / 8, (int64_t)g->num_sms * 8));
     note_launch();
     auto go = [&](auto kern) { kern<<<grid, threads, 0, s>>>(ga); };
+    const bool t16 = b >= 9;  // 16 x 16 frames (4 x 2 tiles per lane); smaller blocks: row per lane
     if (dtype == LSQ_F64) {
-        if (ta && tb) go(k_mm_plan_gen<double, true, true>);
-        else if (ta) go(k_mm_plan_gen<double, true, false>);
-        else if (tb) go(k_mm_plan_gen<double, false, true>);
-        else go(k_mm_plan_gen<double, false, false>);
+        if (ta && tb) go(t16 ? k_mm_plan_t16<double, true, true> : k_mm_plan_gen<double, true, true>);
+        else if (ta) go(t16 ? k_mm_plan_t16<double, true, false> : k_mm_plan_gen<double, true, false>);
+        else if (tb) go(t16 ? k_mm_plan_t16<double, false, true> : k_mm_plan_gen<double, false, true>);
+        else go(t16 ? k_mm_plan_t16<double, false, false> : k_mm_plan_gen<double, false, false>);
     } else {
-        if (ta && tb) go(k_mm_plan_gen<float, true, true>);
-        else if (ta) go(k_mm_plan_gen<float, true, false>);
-        else if (tb) go(k_mm_plan_gen<float, false, true>);
-        else go(k_mm_plan_gen<float, false, false>);
+        if (ta && tb) go(t16 ? k_mm_plan_t16<float, true, true> : k_mm_plan_gen<float, true, true>);
+        else if (ta) go(t16 ? k_mm_plan_t16<float, true, false> : k_mm_plan_gen<float, true, false>);
+        else if (tb) go(t16 ? k_mm_plan_t16<float, false, true> : k_mm_plan_gen<float, false, true>);
+        else go(t16 ? k_mm_plan_t16<float, false, false> : k_mm_plan_gen<float, false, false>);
     }
     LSQ_CHECK_LAUNCH();
     if (p.upper) {

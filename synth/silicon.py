@@ -40,6 +40,28 @@ def batch_system_seed(s):
     return SEED_BASE + 100 + s
 
 
+def batch_workload(n_sys=48, n_min=2, n_max=7):
+    """The batched workload: n_sys uneven diamond-Si systems.
+
+    System s has n_s x n_s x n_s conventional cells with n_s uniform in
+    [n_min, n_max] (64 to 2744 atoms), displacement sigma_s uniform in
+    [0.05, 0.15] Angstrom (both drawn once from configuration seed 2), and
+    positions seeded by batch_system_seed(s).  The first half of the
+    systems uses 4 x 4 blocks, the second half the 13-orbital model with its
+    symmetric H perturbation seeded by batch_system_seed(s) + 7.
+    Returns a list of dicts (n, sigma, seed, b, perturb_seed).
+    """
+    rng = np.random.default_rng(config_seed(2))
+    ns = rng.integers(n_min, n_max + 1, size=n_sys)
+    sig = rng.uniform(0.05, 0.15, size=n_sys)
+    out = []
+    for s in range(n_sys):
+        b = 4 if s < n_sys // 2 else 13
+        out.append(dict(n=int(ns[s]), sigma=float(sig[s]), seed=batch_system_seed(s), b=b,
+                        perturb_seed=(batch_system_seed(s) + 7) if b == 13 else None))
+    return out
+
+
 def diamond_si_positions(n, sigma, seed, a=A_SI):
     """n x n x n conventional cells of diamond Si with Gaussian displacements.
 

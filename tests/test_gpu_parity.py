@@ -59,6 +59,10 @@ def _rand(pat, b, rng):
     (1, 13, 3.0, 2.5, 4.0, 0, 0),     # 13 x 13 blocks (generic kernel)
     (1, 13, 3.0, 2.5, 5.5, 1, 1),
     (2, 7, 4.0, 4.0, 6.0, 0, 1),      # ragged block size
+    (1, 13, 4.0, 3.0, 5.5, 0, 1),     # 13 x 13, one operand transposed each way
+    (1, 13, 4.0, 3.0, 3.0, 1, 0),
+    (1, 9, 3.0, 3.0, 5.0, 0, 1),      # smallest and largest 16 x 16-frame sizes
+    (1, 16, 3.0, 2.5, 4.0, 1, 0),
 ])
 @pytest.mark.parametrize("prec", [lsq.F64, lsq.F32])
 def test_block_matmul_matches_oracle(n, b, ra, rb, rc, ta, tb, prec):
@@ -91,6 +95,51 @@ def test_block_matmul_matches_oracle(n, b, ra, rb, rc, ta, tb, prec):
         bound, _ = oracle.matmul(absA, absB, P[rc])
         scale = abs(alpha) * bound.val.max() + abs(beta) * np.abs(C0.val).max()
         assert np.abs(got - ref_val).max() <= 1e-5 * scale
+
+
+def _at_offset(x, off):
+    """A copy of x whose data starts `off` elements into a fresh allocation."""
+    buf = torch.empty(x.numel() + off, dtype=x.dtype, device=x.device)
+    v = buf[off:].view(x.shape)
+    v.copy_(x)
+    return v
+
+
+@pytest.mark.parametrize("prec,off", [(lsq.F64, 1), (lsq.F64, 2), (lsq.F32, 1), (lsq.F32, 2),
+                                      (lsq.F32, 4), (lsq.F32, 8)])
+def test_block_matmul_any_alignment(prec, off):
+    """4 x 4 blocks at 4-, 8-, 16- and 32-byte offsets: the same product as aligned arrays.
+
+    A first aligned call lets the autotuner pick any schedule (possibly one with
+    32-byte loads); the offset call must then take a schedule its pointers allow.
+    """
+    pos, cell = si(2, 0.1, config_seed(0) + 77)
+    ranges = [10.0, 16.6, 23.2]
+    g = gpu_geometry(pos, cell, ranges)
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in ranges}
+    rng = np.random.default_rng(300 + off)
+    A = oracle.Bsr(P[16.6], 4, _rand(P[16.6], 4, rng))
+    B = oracle.Bsr(P[10.0], 4, _rand(P[10.0], 4, rng))
+    ref, _ = oracle.matmul(A, B, P[23.2])
+    dt = torch.float64 if prec == lsq.F64 else torch.float32
+    Ag, Bg = cuda(A.val, dt), cuda(B.val, dt)
+    ra, rb, rc = g.range_id(16.6), g.range_id(10.0), g.range_id(23.2)
+    C1 = torch.zeros((P[23.2].nnzb, 4, 4), dtype=dt, device="cuda")
+    lsq.block_matmul(g, 4, Ag, ra, Bg, rb, C1, rc, precision=prec, trans_b=True)
+    ref_t, _ = oracle.matmul(A, oracle.transpose(B, P[10.0]), P[23.2])
+    C2 = _at_offset(torch.zeros((P[23.2].nnzb, 4, 4), dtype=dt, device="cuda"), off)
+    lsq.block_matmul(g, 4, _at_offset(Ag, off), ra, _at_offset(Bg, off), rb, C2, rc,
+                     precision=prec, trans_b=True)
+    C3 = _at_offset(torch.zeros((P[23.2].nnzb, 4, 4), dtype=dt, device="cuda"), off)
+    lsq.block_matmul(g, 4, _at_offset(Ag, off), ra, _at_offset(Bg, off), rb, C3, rc, precision=prec)
+    torch.cuda.synchronize()
+    absA = oracle.Bsr(P[16.6], 4, np.abs(A.val))
+    absB = oracle.Bsr(P[10.0], 4, np.abs(B.val))
+    bound = max(oracle.matmul(absA, absB, P[23.2])[0].val.max(),
+                oracle.matmul(absA, oracle.transpose(absB, P[10.0]), P[23.2])[0].val.max())
+    tol = 1e-12 * np.abs(ref.val).max() if prec == lsq.F64 else 1e-5 * bound
+    for got, want in ((C1, ref_t), (C2, ref_t), (C3, ref)):
+        assert np.abs(got.double().cpu().numpy() - want.val).max() <= tol
 
 
 def test_block_matmul_full_size_sampled_rows():

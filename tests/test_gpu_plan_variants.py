@@ -15,7 +15,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-N_VARIANTS = 23
+N_VARIANTS = 29
 
 SCRIPT = r"""
 import sys, numpy as np, torch
