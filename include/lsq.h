@@ -197,7 +197,9 @@ typedef struct {
     int refine_iter;           /* mixed path: FP64 CG steps after the FP32 ones converge (default 2) */
     double spin;               /* spin degeneracy factor of Omega and N_e (default 2) */
     int final_eval;            /* 1 (default): evaluate Omega and N_e of the returned L in
-                                  float64 for the report; 0: report the last step's prediction */
+                                  float64 for the report; 0: skip that evaluation, report the
+                                  last Omega the steps computed (working precision; the batched
+                                  call: the energy at the start of the last step) and N_e = NaN */
     int verbose;               /* 1: print one line per CG step to stderr (default 0) */
     int graph;                 /* batched minimisation: 1 (default) captures one CG step in a
                                   CUDA graph after the first and replays it */

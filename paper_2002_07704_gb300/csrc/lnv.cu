@@ -24,8 +24,8 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
-#include <cstdio>
 #include <cmath>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -1002,8 +1002,9 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
             LSQ_CUDA_TRY(cudaMemcpy(iters64.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
         }
     }
-    // final float64 Omega and N_e of every system
-    LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, nullptr, nullptr, s, true, true));
+    // final float64 Omega and N_e of every system (without it the report keeps the Omega of the
+    // last step's energy evaluation, in the working precision, and no N_e)
+    if (o.final_eval) LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, nullptr, nullptr, s, true, true));
     std::vector<double> slots((size_t)ns * kSlots), dom(ns);
     std::vector<int> iters(ns);
     LSQ_CUDA_TRY(cudaMemcpyAsync(slots.data(), c->b_slots.p, sizeof(double) * ns * kSlots, cudaMemcpyDeviceToHost, s));
@@ -1025,7 +1026,7 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
             reps[k].iterations_fp64 = iters64[k];
             reps[k].status = st;
             reps[k].omega_ev = o.spin * (3.0 * sl[0] - 2.0 * sl[1]);
-            reps[k].ne = o.spin * (3.0 * sl[2] - 2.0 * sl[3]);
+            reps[k].ne = o.final_eval ? o.spin * (3.0 * sl[2] - 2.0 * sl[3]) : std::nan("");
             reps[k].omega_ha_per_atom = reps[k].omega_ev / kHartreeEv / std::max(na, 1);
             reps[k].last_domega_ha_per_atom = dom[k];
             reps[k].seconds = sec;
