@@ -10,8 +10,9 @@
 //           Q = H'LS, G1 = Q.LS, G2 = Q^T.LS (= SLH'LS)
 //
 // Products per energy + gradient (ranges in brackets, R3 = R_H+R_L+R_S):
-//   LS = L.S [R_L+R_S], LSL = (LS.L)|R3, Q = H'.LS [R3],
-//   G1 = (Q.LS)|R_L, G2 = (Q^T.LS)|R_L;
+//   LS = L.S [R_L+R_S], LSL = (LS.L)|R3, Q = H'.LS [R3], and for the gradient the upper
+//   triangles (j >= i) on R_L of T1 = (Q + Q^T).LS and T2 = SL.Q^T, whose sum is the
+//   symmetric G1 + G1^T + G2;
 //   Omega = 2 (3 Tr[H' LSL] - 2 <LSL, Q>), since Tr[LSLSLH'] = Tr[LSL (SLH')] and
 //   SLH' = Q^T; N_e = 2 (3 Tr[S LSL] - 2 <LSL, SLS>) with SLS = S.LS [R3].
 // Exact line search along D: Omega(L + a D) = Omega + c1 a + c2 a^2 + c3 a^3,
@@ -58,14 +59,18 @@ __global__ void k_hprime(int64_t nnzb, int bb, const double *__restrict__ H,
     }
 }
 
-// G_ij[r][c] = spin (3 (Q_ij[r][c] + Q_ji[c][r]) - 2 (G1_ij[r][c] + G1_ji[c][r]
-//              + (G2_ij[r][c] + G2_ji[c][r]) / 2)); each pair summed commutatively, so G is
-// symmetric to the last bit.
+// The gradient from M = G1 + G1^T + G2 = (Q + Q^T).LS + SL.Q^T, held as the upper triangles
+// (blocks with j >= i) of its two terms T1 = (Q + Q^T).LS and T2 = SL.Q^T:
+//   G_ij[r][c] = spin (3 (Q_ij[r][c] + Q_ji[c][r]) - 2 M_ij[r][c]),
+// M_ij = T1_ij + T2_ij for j > i, (T1_ji + T2_ji)^T for j < i, and the symmetric part for j = i.
+// A block (i, j) of the symmetric pattern precedes (j, i) exactly when i < j, so p < tmL[p]
+// selects the upper blocks.  Every element of G and its mirror sum the same values in the
+// same order: G is symmetric to the last bit.
 template <typename T>
-__global__ void k_grad_combine(int64_t nnzb, int b, double spin, const int64_t *__restrict__ pq,
-                               const int64_t *__restrict__ pqt, const int64_t *__restrict__ tmL,
-                               const T *__restrict__ Q, const T *__restrict__ G1,
-                               const T *__restrict__ G2, double *__restrict__ G) {
+__global__ void k_grad_combine_m(int64_t nnzb, int b, double spin, const int64_t *__restrict__ pq,
+                                 const int64_t *__restrict__ pqt, const int64_t *__restrict__ tmL,
+                                 const T *__restrict__ Q, const T *__restrict__ T1,
+                                 const T *__restrict__ T2, double *__restrict__ G) {
     const int bb = b * b;
     int64_t m = nnzb * bb;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
@@ -76,9 +81,16 @@ __global__ void k_grad_combine(int64_t nnzb, int b, double spin, const int64_t *
         int64_t tr = c * b + r;
         int64_t a = pq[p], at = pqt[p], t = tmL[p];
         double q = (a >= 0 ? (double)Q[a * bb + rc] : 0.0) + (at >= 0 ? (double)Q[at * bb + tr] : 0.0);
-        double g1 = (double)G1[p * bb + rc] + (double)G1[t * bb + tr];
-        double g2 = (double)G2[p * bb + rc] + (double)G2[t * bb + tr];
-        G[e] = spin * (3.0 * q - 2.0 * (g1 + 0.5 * g2));
+        double mv;
+        if (p < t) {
+            mv = (double)T1[p * bb + rc] + (double)T2[p * bb + rc];
+        } else if (p > t) {
+            mv = (double)T1[t * bb + tr] + (double)T2[t * bb + tr];
+        } else {
+            mv = 0.5 * (((double)T1[p * bb + rc] + (double)T2[p * bb + rc]) +
+                        ((double)T1[p * bb + tr] + (double)T2[p * bb + tr]));
+        }
+        G[e] = spin * (3.0 * q - 2.0 * mv);
     }
 }
 
@@ -563,27 +575,31 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         LSQ_TRY(dt(c->r3, c->LSL.p, SLS, 3));
     }
     if (G) {
-        // G1 = Q.LS = Q.(SL)^T and G2 = Q^T.LS, with SL and Q^T materialised so both
-        // operands are read row by row
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->Q.p, c->r1, tLS, LSop, c->rL, c->G1.p, 1.0, 0.0, nullptr, s));
-        if (mat) {
-            LSQ_TRY(transpose_on(g, c->r3, b, prec, c->Q.p, c->QT.p, s));
-            LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, c->QT.p, c->r1, 1, LSop, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 1));
-        } else {
-            LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->Q.p, c->r1, 0, LSop, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 1));
-        }
+        // M = G1 + G1^T + G2 (G1 = Q.LS, G2 = Q^T.LS) is symmetric and equals T1 + T2 with
+        // T1 = (Q + Q^T).LS and T2 = SL.Q^T, so the upper triangles of T1 and T2 on L's range
+        // give all of it: one full product's work instead of G1 in full plus G2's upper half.
+        // Q + Q^T goes to QD's storage, free until the line search.
+        void *Qs = c->QD.p;
+        LSQ_TRY(sym_sum_on(g, c->r3, b, prec, c->Q.p, Qs, s));
+        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, Qs, c->r1, tLS, LSop, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 2));
+        // T2 = SL.Q^T: op(B) = Q^T, read as rows of Q; op(A) = SL (materialised for 4 x 4 blocks)
+        if (mat)
+            LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->SL.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
+        else
+            LSQ_TRY(block_matmul(g, b, prec, c->r1, 1, c->LS.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
         const int64_t *pq = nullptr, *pqt = nullptr;
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
+        LSQ_TRY(ensure_tmap(g, c->rL, s));
         int64_t nl = nvals(c, c->rL);
         if (prec == LSQ_F64) {
             note_launch();
-            k_grad_combine<double><<<grid_for(nl), 256, 0, s>>>(
+            k_grad_combine_m<double><<<grid_for(nl), 256, 0, s>>>(
                 g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const double *)c->Q.p,
                 (const double *)c->G1.p, (const double *)c->G2.p, G);
         } else {
             note_launch();
-            k_grad_combine<float><<<grid_for(nl), 256, 0, s>>>(
+            k_grad_combine_m<float><<<grid_for(nl), 256, 0, s>>>(
                 g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const float *)c->Q.p,
                 (const float *)c->G1.p, (const float *)c->G2.p, G);
         }

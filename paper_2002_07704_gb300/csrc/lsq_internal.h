@@ -144,21 +144,27 @@ int ensure_tmap(lsq_geom g, int r, cudaStream_t s);
 int get_posmap(lsq_geom g, int p, int q, int transposed, const int64_t **out, cudaStream_t s);
 int find_range(lsq_geom g, double R);
 
-// Truncated product C = alpha op(A) op(B) + beta C (see lsq_block_matmul).  sym != 0
+// Truncated product C = alpha op(A) op(B) + beta C (see lsq_block_matmul).  sym = 1
 // declares the result symmetric (C = C^T in exact arithmetic): only blocks with j >= i
-// are computed and the others are their transposes.
+// are computed and the others are their transposes.  sym = 2 computes the blocks with
+// j >= i only and leaves the others of C as they were (for a caller that needs only the
+// upper triangle of a product that is not itself symmetric).
 int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
                  const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
                  cudaStream_t s, int sym = 0);
 
 int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out, cudaStream_t s);
+// mirror: for an upper-triangle plan, fill the lower blocks with the transposes afterwards.
 int plan_launch(lsq_geom g, int dtype, const ProductPlan &p, int ra, int rb, int rc, const void *Aop,
-                const void *X, void *C, double alpha, double beta, cudaStream_t s);
+                const void *X, void *C, double alpha, double beta, cudaStream_t s, bool mirror = true);
 // Plan-driven product for any block size; transposed operands read through transpose maps.
 int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, int ta, int rb, int tb, int rc,
-                    const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s);
+                    const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s,
+                    bool mirror = true);
 // out = X^T on the (symmetric) pattern r: out_ij = (X_ji)^T.
 int transpose_on(lsq_geom g, int r, int b, int dtype, const void *X, void *out, cudaStream_t s);
+// out = X + X^T on the (symmetric) pattern r: out_ij = X_ij + (X_ji)^T.
+int sym_sum_on(lsq_geom g, int r, int b, int dtype, const void *X, void *out, cudaStream_t s);
 
 // Reductions into g->red.scalars[slot] (float64), enqueued on s.
 int trace_into(lsq_geom g, int b, int dtype, int rx, const void *X, int ry, const void *Y, int slot,

@@ -376,6 +376,36 @@ int transpose_on(lsq_geom g, int r, int b, int prec, const void *X, void *out,
     return LSQ_OK;
 }
 
+// out_ij = X_ij + (X_ji)^T on one symmetric pattern; element (r, c) and its mirror (c, r) of the
+// mirrored block add the same two values (addition commutes), so out is symmetric to the last bit.
+template <typename T>
+__global__ void k_sym_sum(int64_t nnzb, int b, const int64_t *__restrict__ tm, const T *__restrict__ X,
+                          T *__restrict__ out) {
+    const int bb = b * b;
+    int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / bb;
+        int rc = (int)(e - p * bb);
+        int r = rc / b, c = rc - r * b;
+        out[e] = X[e] + X[tm[p] * bb + c * b + r];
+    }
+}
+
+int sym_sum_on(lsq_geom g, int r, int b, int prec, const void *X, void *out, cudaStream_t s) {
+    LSQ_TRY(ensure_tmap(g, r, s));
+    int64_t m = g->pats[r].nnzb * b * b;
+    note_launch();
+    if (prec == LSQ_F64)
+        k_sym_sum<double><<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, (const double *)X,
+                                                     (double *)out);
+    else
+        k_sym_sum<float><<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, (const float *)X,
+                                                    (float *)out);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
 // ---- index-cost estimate of the two forms ---------------------------------
 __global__ void k_mm_cost(int n, const int64_t *__restrict__ a_ptr, const int32_t *__restrict__ a_col,
                           const int64_t *__restrict__ b_ptr, const int64_t *__restrict__ c_ptr,
@@ -563,7 +593,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
                 LSQ_TRY(transpose_on(g, rb, b, dtype, B, g->scratch_x.p, s));
                 X = g->scratch_x.p;
             }
-            return plan_launch(g, dtype, *pp, ra, rb, rc, Aop, X, C, alpha, beta, s);
+            return plan_launch(g, dtype, *pp, ra, rb, rc, Aop, X, C, alpha, beta, s, sym != 2);
         }
         if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
         (void)cudaGetLastError();  // a failed allocation is not sticky; drop it
@@ -575,7 +605,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
         if (prc == LSQ_OK) {
             if (triples) *triples = pp->triples;
             if (g->n == 0 || g->pats[rc].nnzb == 0) return LSQ_OK;
-            return plan_launch_gen(g, b, dtype, *pp, ra, ta, rb, tb, rc, A, B, C, alpha, beta, s);
+            return plan_launch_gen(g, b, dtype, *pp, ra, ta, rb, tb, rc, A, B, C, alpha, beta, s, sym != 2);
         }
         if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
         (void)cudaGetLastError();

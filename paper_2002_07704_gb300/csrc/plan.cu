@@ -923,7 +923,7 @@ int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks
 }  // namespace
 
 int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, int rc, const void *Aop,
-                const void *X, void *C, double alpha, double beta, cudaStream_t s) {
+                const void *X, void *C, double alpha, double beta, cudaStream_t s, bool mirror) {
     ProductPlan &p = const_cast<ProductPlan &>(pc);
     if (p.nblocks == 0) return LSQ_OK;
     PlanArgs a;
@@ -1001,7 +1001,7 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
     // a later call may pass operands that the tuned variant cannot read
     const int use = smem_for(choice) >= 0 ? choice : std::max(p.variant16[di], 0);
     LSQ_TRY(run_variant(g, v[use], a, p.nblocks, s, smem_for(use)));
-    if (p.upper) {
+    if (p.upper && mirror) {
         LSQ_TRY(ensure_tmap(g, rc, s));
         const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);
         note_launch();
@@ -1017,7 +1017,8 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
 }
 
 int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, int ta, int rb, int tb, int rc,
-                    const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s) {
+                    const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s,
+                    bool mirror) {
     if (p.nblocks == 0) return LSQ_OK;
     PlanArgsGen ga;
     PlanArgs &a = ga.p;
@@ -1057,7 +1058,7 @@ int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, 
         else go(t16 ? k_mm_plan_t16<float, false, false> : k_mm_plan_gen<float, false, false>);
     }
     LSQ_CHECK_LAUNCH();
-    if (p.upper) {
+    if (p.upper && mirror) {
         // C_ij = (C_ji)^T for j < i, any block size
         LSQ_TRY(mirror_lower_gen(g, rc, b, dtype, C, s));
     }
