@@ -66,17 +66,18 @@ __global__ void k_hprime(int64_t nnzb, int bb, const double *__restrict__ H,
 // A block (i, j) of the symmetric pattern precedes (j, i) exactly when i < j, so p < tmL[p]
 // selects the upper blocks.  Every element of G and its mirror sum the same values in the
 // same order: G is symmetric to the last bit.
-template <typename T>
-__global__ void k_grad_combine_m(int64_t nnzb, int b, double spin, const int64_t *__restrict__ pq,
+template <typename T, int B>
+__global__ void k_grad_combine_m(int64_t nnzb, int b_rt, double spin, const int64_t *__restrict__ pq,
                                  const int64_t *__restrict__ pqt, const int64_t *__restrict__ tmL,
                                  const T *__restrict__ Q, const T *__restrict__ T1,
                                  const T *__restrict__ T2, double *__restrict__ G) {
+    const int b = B > 0 ? B : b_rt;
     const int bb = b * b;
-    int64_t m = nnzb * bb;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = e / bb;
-        int rc = (int)(e - p * bb);
+    const uint64_t m = (uint64_t)nnzb * bb;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t p = (int64_t)(e / (uint64_t)bb);
+        int rc = (int)(e - (uint64_t)p * bb);
         int r = rc / b, c = rc - r * b;
         int64_t tr = c * b + r;
         int64_t a = pq[p], at = pqt[p], t = tmL[p];
@@ -178,6 +179,30 @@ __global__ void k_rowdot(int n, int bb, const int64_t *__restrict__ rp, const T 
     for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) s += (double)X[e] * (double)Y[e];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) rowsum[warp] = s;
+}
+
+// float32 operands: each lane sums groups of 8 products as float pairs (dot2_add) and adds
+// each group to its float64 sum, so the float64 pipe sees one addition per 8 terms.
+template <>
+__global__ void k_rowdot<float>(int n, int bb, const int64_t *__restrict__ rp, const float *__restrict__ X,
+                                const float *__restrict__ Y, double *__restrict__ rowsum) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double acc = 0.0;
+    float s = 0.f, c = 0.f;
+    int k = 0;
+    for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) {
+        dot2_add(X[e], Y[e], s, c);
+        if (++k == 8) {
+            acc += (double)s + (double)c;
+            s = c = 0.f;
+            k = 0;
+        }
+    }
+    acc += (double)s + (double)c;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) rowsum[warp] = acc;
 }
 
 // warp per row i of X: rowsum[i] = sum over (i, j) in X of <X_ij, (Y_ji)^T> (pm: posmap X -> Y^T)
@@ -592,16 +617,19 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
         LSQ_TRY(ensure_tmap(g, c->rL, s));
         int64_t nl = nvals(c, c->rL);
+        auto go = [&](auto kern, auto *q, auto *t1, auto *t2) {
+            note_launch();
+            kern<<<grid_for(nl), 256, 0, s>>>(g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p,
+                                              q, t1, t2, G);
+        };
         if (prec == LSQ_F64) {
-            note_launch();
-            k_grad_combine_m<double><<<grid_for(nl), 256, 0, s>>>(
-                g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const double *)c->Q.p,
-                (const double *)c->G1.p, (const double *)c->G2.p, G);
+            auto *q = (const double *)c->Q.p, *t1 = (const double *)c->G1.p, *t2 = (const double *)c->G2.p;
+            if (b == 4) go(k_grad_combine_m<double, 4>, q, t1, t2);
+            else go(k_grad_combine_m<double, 0>, q, t1, t2);
         } else {
-            note_launch();
-            k_grad_combine_m<float><<<grid_for(nl), 256, 0, s>>>(
-                g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p, (const float *)c->Q.p,
-                (const float *)c->G1.p, (const float *)c->G2.p, G);
+            auto *q = (const float *)c->Q.p, *t1 = (const float *)c->G1.p, *t2 = (const float *)c->G2.p;
+            if (b == 4) go(k_grad_combine_m<float, 4>, q, t1, t2);
+            else go(k_grad_combine_m<float, 0>, q, t1, t2);
         }
         LSQ_CHECK_LAUNCH();
     }

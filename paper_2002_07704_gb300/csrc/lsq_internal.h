@@ -176,4 +176,25 @@ int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s);
 
 inline size_t dtype_size(int dtype) { return dtype == LSQ_F64 ? 8 : 4; }
 
+#ifdef __CUDACC__
+// Error-free float32 sum (Knuth's TwoSum): s = fl(a + b) and s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// Adds x * y to the float pair (s, c) without losing the rounding errors of the product (an
+// FMA recovers it exactly) or of the sum (TwoSum); s + c then carries about twice the float32
+// precision.  Used to accumulate float32 dot products without a float64 operation per term.
+__device__ __forceinline__ void dot2_add(float x, float y, float &s, float &c) {
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);
+    float t, te;
+    two_sum(s, p, t, te);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(te, pe));
+}
+#endif
+
 }  // namespace lsq

@@ -344,17 +344,19 @@ __global__ void __launch_bounds__(256) k_mm_inner_gen(MMArgs g, int b) {
 }
 
 // out_ij = (X_ji)^T on one symmetric pattern (tm = transpose map of the pattern).
-template <typename T>
-__global__ void k_transpose_pattern(int64_t nnzb, int b, const int64_t *__restrict__ tm,
+// B > 0 fixes the block size at compile time (index arithmetic by shifts for B = 4).
+template <typename T, int B>
+__global__ void k_transpose_pattern(int64_t nnzb, int b_rt, const int64_t *__restrict__ tm,
                                     const T *__restrict__ X, T *__restrict__ out) {
-    const int bb = b * b;
-    int64_t m = nnzb * bb;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = e / bb;
-        int rc = (int)(e - p * bb);
-        int r = rc / b, c = rc - r * b;
-        out[e] = X[tm[p] * bb + c * b + r];
+    const int b = B > 0 ? B : b_rt;
+    const uint64_t bb = (uint64_t)(b * b);
+    const uint64_t m = (uint64_t)nnzb * bb;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        const int r = rc / b, c = rc - r * b;
+        out[e] = X[tm[p] * (int64_t)bb + c * b + r];
     }
 }
 
@@ -366,29 +368,32 @@ int transpose_on(lsq_geom g, int r, int b, int prec, const void *X, void *out,
     LSQ_TRY(ensure_tmap(g, r, s));
     int64_t m = g->pats[r].nnzb * b * b;
     note_launch();
-    if (prec == LSQ_F64)
-        k_transpose_pattern<double><<<tgrid(m), 256, 0, s>>>(
-            g->pats[r].nnzb, b, g->pats[r].tmap.p, (const double *)X, (double *)out);
-    else
-        k_transpose_pattern<float><<<tgrid(m), 256, 0, s>>>(
-            g->pats[r].nnzb, b, g->pats[r].tmap.p, (const float *)X, (float *)out);
+    auto go = [&](auto kern, auto *x, auto *o) { kern<<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, x, o); };
+    if (prec == LSQ_F64) {
+        if (b == 4) go(k_transpose_pattern<double, 4>, (const double *)X, (double *)out);
+        else go(k_transpose_pattern<double, 0>, (const double *)X, (double *)out);
+    } else {
+        if (b == 4) go(k_transpose_pattern<float, 4>, (const float *)X, (float *)out);
+        else go(k_transpose_pattern<float, 0>, (const float *)X, (float *)out);
+    }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
 
 // out_ij = X_ij + (X_ji)^T on one symmetric pattern; element (r, c) and its mirror (c, r) of the
 // mirrored block add the same two values (addition commutes), so out is symmetric to the last bit.
-template <typename T>
-__global__ void k_sym_sum(int64_t nnzb, int b, const int64_t *__restrict__ tm, const T *__restrict__ X,
+template <typename T, int B>
+__global__ void k_sym_sum(int64_t nnzb, int b_rt, const int64_t *__restrict__ tm, const T *__restrict__ X,
                           T *__restrict__ out) {
-    const int bb = b * b;
-    int64_t m = nnzb * bb;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = e / bb;
-        int rc = (int)(e - p * bb);
-        int r = rc / b, c = rc - r * b;
-        out[e] = X[e] + X[tm[p] * bb + c * b + r];
+    const int b = B > 0 ? B : b_rt;
+    const uint64_t bb = (uint64_t)(b * b);
+    const uint64_t m = (uint64_t)nnzb * bb;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        const int r = rc / b, c = rc - r * b;
+        out[e] = X[e] + X[tm[p] * (int64_t)bb + c * b + r];
     }
 }
 
@@ -396,12 +401,14 @@ int sym_sum_on(lsq_geom g, int r, int b, int prec, const void *X, void *out, cud
     LSQ_TRY(ensure_tmap(g, r, s));
     int64_t m = g->pats[r].nnzb * b * b;
     note_launch();
-    if (prec == LSQ_F64)
-        k_sym_sum<double><<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, (const double *)X,
-                                                     (double *)out);
-    else
-        k_sym_sum<float><<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, (const float *)X,
-                                                    (float *)out);
+    auto go = [&](auto kern, auto *x, auto *o) { kern<<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, x, o); };
+    if (prec == LSQ_F64) {
+        if (b == 4) go(k_sym_sum<double, 4>, (const double *)X, (double *)out);
+        else go(k_sym_sum<double, 0>, (const double *)X, (double *)out);
+    } else {
+        if (b == 4) go(k_sym_sum<float, 4>, (const float *)X, (float *)out);
+        else go(k_sym_sum<float, 0>, (const float *)X, (float *)out);
+    }
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -683,6 +690,38 @@ __global__ void k_dot(int64_t total, const T *__restrict__ X, const T *__restric
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+// Float32 dot product accumulated without a float64 operation per element (the float64 pipe
+// is 1/64 of the float32 one): each thread forms 8 products exactly as float pairs (TwoProduct
+// with an FMA) and sums them with error-free TwoSum steps (Knuth; the Dot2 scheme of Ogita,
+// Rump and Oishi, 2005), then adds the pair to a float64 accumulator.  Each group of 8 is
+// summed as if in twice the float32 precision, so the result matches float64 accumulation of
+// the exact products to well below float32 rounding.  X and Y must be 16-byte aligned.
+__device__ __forceinline__ double dot8_exact(const float4 a0, const float4 a1, const float4 b0,
+                                             const float4 b1) {
+    const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float y[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dot2_add(x[k], y[k], s, c);
+    return (double)s + (double)c;
+}
+
+__global__ void k_dot_f32(int64_t total, const float *__restrict__ X, const float *__restrict__ Y,
+                          double *__restrict__ partial) {
+    double s = 0.0;
+    const int64_t n8 = total / 8;
+    const float4 *__restrict__ X4 = reinterpret_cast<const float4 *>(X);
+    const float4 *__restrict__ Y4 = reinterpret_cast<const float4 *>(Y);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n8;
+         q += (int64_t)gridDim.x * blockDim.x)
+        s += dot8_exact(__ldg(X4 + 2 * q), __ldg(X4 + 2 * q + 1), __ldg(Y4 + 2 * q), __ldg(Y4 + 2 * q + 1));
+    // the last total % 8 values
+    const int64_t e = n8 * 8 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < total) s += (double)X[e] * (double)Y[e];
+    double t = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 __global__ void k_finish(const double *__restrict__ partial, int m, double *__restrict__ out) {
     double s = 0.0;
     for (int k = threadIdx.x; k < m; k += blockDim.x) s += partial[k];
@@ -719,6 +758,10 @@ int dot_into(lsq_geom g, int b, int dtype, int r, const void *X, const void *Y, 
         note_launch();
         k_dot<double><<<kRedBlocks, kRedThreads, 0, s>>>(total, (const double *)X, (const double *)Y,
                                                          g->red.partial.p);
+    } else if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) % 16 == 0) {
+        note_launch();
+        k_dot_f32<<<kRedBlocks, kRedThreads, 0, s>>>(total, (const float *)X, (const float *)Y,
+                                                     g->red.partial.p);
     } else {
         note_launch();
         k_dot<float><<<kRedBlocks, kRedThreads, 0, s>>>(total, (const float *)X, (const float *)Y,

@@ -641,19 +641,18 @@ __global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
     }
 }
 
-// Lower blocks of a symmetric result: C_ij = (C_ji)^T for j < i (tm: transpose map of C's pattern).
+// Lower blocks of a symmetric 4 x 4 result: C_ij = (C_ji)^T for j < i (tm: transpose map of C's
+// pattern).  In a sorted symmetric pattern block (i, j) precedes (j, i) exactly when i < j, so
+// the lower blocks are those with p > tm[p].
 template <typename T>
-__global__ void k_mirror_lower(int n, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
-                               const int64_t *__restrict__ tm, T *__restrict__ C) {
-    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const int i = warp;
-    for (int64_t e = c_ptr[i] * 16 + lane; e < c_ptr[i + 1] * 16; e += 32) {
-        const int64_t p = e >> 4;
+__global__ void k_mirror_lower(int64_t nnzb, const int64_t *__restrict__ tm, T *__restrict__ C) {
+    const uint64_t m = (uint64_t)nnzb * 16;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t p = (int64_t)(e >> 4), t = tm[p];
+        if (p <= t) continue;
         const int rc = (int)(e & 15);
-        if (c_col[p] >= i) continue;
-        C[e] = C[tm[p] * 16 + (rc & 3) * 4 + (rc >> 2)];
+        C[e] = C[t * 16 + (rc & 3) * 4 + (rc >> 2)];
     }
 }
 
@@ -756,32 +755,32 @@ __global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
     }
 }
 
+// Lower blocks of a symmetric result, any block size: one warp per block (lower blocks are
+// those with p > tm[p], see k_mirror_lower).
 template <typename T>
-__global__ void k_mirror_lower_gen(int n, int b, const int64_t *__restrict__ c_ptr, const int32_t *__restrict__ c_col,
-                                   const int64_t *__restrict__ tm, T *__restrict__ C) {
-    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+__global__ void k_mirror_lower_gen(int64_t nnzb, int b, const int64_t *__restrict__ tm, T *__restrict__ C) {
     const int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const int i = warp, bb = b * b;
-    for (int64_t e = c_ptr[i] * bb + lane; e < c_ptr[i + 1] * bb; e += 32) {
-        const int64_t p = e / bb;
-        const int rc = (int)(e - p * bb);
-        if (c_col[p] >= i) continue;
-        const int r = rc / b, c = rc - r * b;
-        C[e] = C[tm[p] * bb + c * b + r];
+    const int bb = b * b;
+    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < nnzb;
+         p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t t = tm[p];
+        if (p <= t) continue;
+        for (int rc = lane; rc < bb; rc += 32) {
+            const int r = rc / b, c = rc - r * b;
+            C[p * bb + rc] = C[t * bb + c * b + r];
+        }
     }
 }
 
 int mirror_lower_gen(lsq_geom g, int rc, int b, int dtype, void *C, cudaStream_t s) {
     LSQ_TRY(ensure_tmap(g, rc, s));
-    const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);
+    const int64_t nnzb = g->pats[rc].nnzb;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb * 32 + 255) / 256, (int64_t)g->num_sms * 16));
     note_launch();
     if (dtype == LSQ_F64)
-        k_mirror_lower_gen<double><<<blocks, 256, 0, s>>>(g->n, b, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
-                                                           g->pats[rc].tmap.p, (double *)C);
+        k_mirror_lower_gen<double><<<blocks, 256, 0, s>>>(nnzb, b, g->pats[rc].tmap.p, (double *)C);
     else
-        k_mirror_lower_gen<float><<<blocks, 256, 0, s>>>(g->n, b, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
-                                                          g->pats[rc].tmap.p, (float *)C);
+        k_mirror_lower_gen<float><<<blocks, 256, 0, s>>>(nnzb, b, g->pats[rc].tmap.p, (float *)C);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -1003,14 +1002,13 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
     LSQ_TRY(run_variant(g, v[use], a, p.nblocks, s, smem_for(use)));
     if (p.upper && mirror) {
         LSQ_TRY(ensure_tmap(g, rc, s));
-        const int blocks = (int)(((int64_t)g->n * 32 + 255) / 256);
+        const int64_t m = g->pats[rc].nnzb * 16;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16));
         note_launch();
         if (dtype == LSQ_F64)
-            k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->n, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
-                                                           g->pats[rc].tmap.p, (double *)C);
+            k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (double *)C);
         else
-            k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->n, g->pats[rc].row_ptr.p, g->pats[rc].col.p,
-                                                          g->pats[rc].tmap.p, (float *)C);
+            k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (float *)C);
         LSQ_CHECK_LAUNCH();
     }
     return LSQ_OK;
