@@ -15,11 +15,15 @@
 //   symmetric G1 + G1^T + G2;
 //   Omega = 2 (3 Tr[H' LSL] - 2 <LSL, Q>), since Tr[LSLSLH'] = Tr[LSL (SLH')] and
 //   SLH' = Q^T; N_e = 2 (3 Tr[S LSL] - 2 <LSL, SLS>) with SLS = S.LS [R3].
+// When the gradient is formed, LSL is not needed: by the cyclic property,
+//   Tr[LSLH'] = <L, Q> and Tr[LSLSLH'] = <L, G1> = <L, G1^T> = <L, G2> = <L, M> / 3
+// over L's range, so Omega = 2 (3 <L, Q> - (2/3) <L, M>) comes out of the gradient's own
+// data in the same pass as the combine.
 // Exact line search along D: Omega(L + a D) = Omega + c1 a + c2 a^2 + c3 a^3,
 //   c1 = <G, D>,  c2 = 2 (3 t2 - 2 (2 t3a + t3b)),  c3 = -4 t4, with
 //   P = D.S, QD = H'.P, F = (P.D)|[R_H+R_L+R_S] (= DSD), Z = (QD^T.P)|R_L,
 //   t2 = Tr[F H'] = Tr[DSDH'], t3a = <F, Q> = Tr[DSDSLH'] (= Tr[LSDSDH']),
-//   t3b = <L, Z> = Tr[DSLSDH'], t4 = <F, QD> = Tr[DSDSDH'],
+//   t3b = <L, Z> = Tr[DSLSDH'], t4 = <D, Z> = Tr[DSDSDH'] (= <F, QD>),
 // using the symmetry of S, H', L and D and the cyclic property of the trace.
 // All matrices are symmetric; the CG keeps L exactly symmetric.
 #include <cuda_runtime.h>
@@ -66,22 +70,30 @@ __global__ void k_hprime(int64_t nnzb, int bb, const double *__restrict__ H,
 // A block (i, j) of the symmetric pattern precedes (j, i) exactly when i < j, so p < tmL[p]
 // selects the upper blocks.  Every element of G and its mirror sum the same values in the
 // same order: G is symmetric to the last bit.
+// One warp per row i of L's pattern; the same pass forms the two energy terms of the row:
+// row0[i] = sum_j <L_ij, Q_ij> and row1[i] = sum_j <L_ij, M_ij> / 3 (see the header), with L
+// as the products read it (its float32 copy on the mixed path).
 template <typename T, int B>
-__global__ void k_grad_combine_m(int64_t nnzb, int b_rt, double spin, const int64_t *__restrict__ pq,
-                                 const int64_t *__restrict__ pqt, const int64_t *__restrict__ tmL,
-                                 const T *__restrict__ Q, const T *__restrict__ T1,
-                                 const T *__restrict__ T2, double *__restrict__ G) {
+__global__ void k_grad_omega_rows(int n, int b_rt, double spin, const int64_t *__restrict__ rp,
+                                  const int64_t *__restrict__ pq, const int64_t *__restrict__ pqt,
+                                  const int64_t *__restrict__ tmL, const T *__restrict__ L,
+                                  const T *__restrict__ Q, const T *__restrict__ T1, const T *__restrict__ T2,
+                                  double *__restrict__ G, double *__restrict__ row0, double *__restrict__ row1) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
     const int b = B > 0 ? B : b_rt;
     const int bb = b * b;
-    const uint64_t m = (uint64_t)nnzb * bb;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (uint64_t)gridDim.x * blockDim.x) {
-        int64_t p = (int64_t)(e / (uint64_t)bb);
-        int rc = (int)(e - (uint64_t)p * bb);
-        int r = rc / b, c = rc - r * b;
-        int64_t tr = c * b + r;
-        int64_t a = pq[p], at = pqt[p], t = tmL[p];
-        double q = (a >= 0 ? (double)Q[a * bb + rc] : 0.0) + (at >= 0 ? (double)Q[at * bb + tr] : 0.0);
+    double s0 = 0.0, s1 = 0.0;
+    const uint64_t e1 = (uint64_t)rp[warp + 1] * bb;
+    for (uint64_t e = (uint64_t)rp[warp] * bb + lane; e < e1; e += 32) {
+        const int64_t p = (int64_t)(e / (uint64_t)bb);
+        const int rc = (int)(e - (uint64_t)p * bb);
+        const int r = rc / b, c = rc - r * b;
+        const int64_t tr = c * b + r;
+        const int64_t a = pq[p], at = pqt[p], t = tmL[p];
+        const double qd = a >= 0 ? (double)Q[a * bb + rc] : 0.0;
+        const double q = qd + (at >= 0 ? (double)Q[at * bb + tr] : 0.0);
         double mv;
         if (p < t) {
             mv = (double)T1[p * bb + rc] + (double)T2[p * bb + rc];
@@ -92,6 +104,17 @@ __global__ void k_grad_combine_m(int64_t nnzb, int b_rt, double spin, const int6
                         ((double)T1[p * bb + tr] + (double)T2[p * bb + tr]));
         }
         G[e] = spin * (3.0 * q - 2.0 * mv);
+        const double l = (double)L[e];
+        s0 = fma(l, qd, s0);
+        s1 = fma(l, mv, s1);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    }
+    if (lane == 0) {
+        row0[warp] = s0;
+        row1[warp] = s1 / 3.0;
     }
 }
 
@@ -369,6 +392,7 @@ struct lsq_lnv_s {
     DevBuf<double> Hp, Sh, G, Gp, D;
     // product buffers, sized for float64 and reused for float32
     DevBuf<char> LS, SL, LSL, Q, QT, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
+    DevBuf<double> om_rows;  // per-row energy terms formed with the gradient (2 x n)
     const int64_t *pos_s_in_h = nullptr;
     // batched minimisation state (allocated by the first batch call)
     int b_nsys = 0;
@@ -575,9 +599,13 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
-    // scalar slots: 0 = Tr[H' LSL], 1 = <LSL, Q>, 2 = Tr[S LSL], 3 = <LSL, SLS>
+    // scalar slots: 0 = Tr[H' LSL], 1 = Tr[LSLSL H'] (= <LSL, Q>), 2 = Tr[S LSL], 3 = <LSL, SLS>.
+    // With the gradient, slots 0 and 1 come from <L, Q> and <L, M> / 3 (see the header) and LSL
+    // is formed only for N_e.
+    const bool need_lsl = !G || ne || want_ne;
     LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 1, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
+    if (need_lsl)
+        LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
     // 4 x 4 blocks: transposed operands are materialised so the plan kernel reads rows; the
     // kernel for other block sizes reads transposes through the transpose map
     const bool mat = c->b == 4;
@@ -591,8 +619,10 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     auto dt = [&](int r, const void *X, const void *Y, int slot) {
         return seg ? seg_dot(c, prec, r, X, Y, slot, s) : dot_into(g, b, prec, r, X, Y, slot, s);
     };
-    LSQ_TRY(tr(c->rH, o.Hp, c->r3, c->LSL.p, 0));
-    LSQ_TRY(dt(c->r3, c->LSL.p, c->Q.p, 1));
+    if (!G) {
+        LSQ_TRY(tr(c->rH, o.Hp, c->r3, c->LSL.p, 0));
+        LSQ_TRY(dt(c->r3, c->LSL.p, c->Q.p, 1));
+    }
     if (ne || want_ne) {
         void *SLS = c->QD.p;
         LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, tLS, LSop, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
@@ -616,22 +646,38 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
         LSQ_TRY(ensure_tmap(g, c->rL, s));
-        int64_t nl = nvals(c, c->rL);
-        auto go = [&](auto kern, auto *q, auto *t1, auto *t2) {
+        const int n = g->n;
+        if (c->om_rows.n < (size_t)2 * std::max(n, 1)) LSQ_TRY(c->om_rows.alloc((size_t)2 * std::max(n, 1)));
+        double *row0 = c->om_rows.p, *row1 = c->om_rows.p + std::max(n, 1);
+        const int blocks = (int)(((int64_t)n * 32 + 255) / 256);
+        auto go = [&](auto kern, auto *l, auto *q, auto *t1, auto *t2) {
+            if (n == 0) return;
             note_launch();
-            kern<<<grid_for(nl), 256, 0, s>>>(g->pats[c->rL].nnzb, b, spin, pq, pqt, g->pats[c->rL].tmap.p,
-                                              q, t1, t2, G);
+            kern<<<blocks, 256, 0, s>>>(n, b, spin, g->pats[c->rL].row_ptr.p, pq, pqt, g->pats[c->rL].tmap.p,
+                                        l, q, t1, t2, G, row0, row1);
         };
         if (prec == LSQ_F64) {
-            auto *q = (const double *)c->Q.p, *t1 = (const double *)c->G1.p, *t2 = (const double *)c->G2.p;
-            if (b == 4) go(k_grad_combine_m<double, 4>, q, t1, t2);
-            else go(k_grad_combine_m<double, 0>, q, t1, t2);
+            auto *l = (const double *)o.L, *q = (const double *)c->Q.p;
+            auto *t1 = (const double *)c->G1.p, *t2 = (const double *)c->G2.p;
+            if (b == 4) go(k_grad_omega_rows<double, 4>, l, q, t1, t2);
+            else go(k_grad_omega_rows<double, 0>, l, q, t1, t2);
         } else {
-            auto *q = (const float *)c->Q.p, *t1 = (const float *)c->G1.p, *t2 = (const float *)c->G2.p;
-            if (b == 4) go(k_grad_combine_m<float, 4>, q, t1, t2);
-            else go(k_grad_combine_m<float, 0>, q, t1, t2);
+            auto *l = (const float *)o.L, *q = (const float *)c->Q.p;
+            auto *t1 = (const float *)c->G1.p, *t2 = (const float *)c->G2.p;
+            if (b == 4) go(k_grad_omega_rows<float, 4>, l, q, t1, t2);
+            else go(k_grad_omega_rows<float, 0>, l, q, t1, t2);
         }
         LSQ_CHECK_LAUNCH();
+        if (seg) {
+            note_launch();
+            k_sys_sum<<<c->b_nsys, 256, 0, s>>>(c->b_off.p, row0, c->b_slots.p, 0);
+            note_launch();
+            k_sys_sum<<<c->b_nsys, 256, 0, s>>>(c->b_off.p, row1, c->b_slots.p, 1);
+            LSQ_CHECK_LAUNCH();
+        } else {
+            LSQ_TRY(sum_into(g, row0, n, 0, s));
+            LSQ_TRY(sum_into(g, row1, n, 1, s));
+        }
     }
     if (!seg && (omega || ne)) {
         double t[4];
@@ -676,14 +722,14 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
         LSQ_TRY(seg_trace(c, prec, c->rH, o.Hp, c->r3, F, 5, s));
         LSQ_TRY(seg_dot(c, prec, c->r3, F, c->Q.p, 6, s));
         LSQ_TRY(seg_dot(c, prec, c->rL, o.L, Z, 7, s));
-        LSQ_TRY(seg_dot(c, prec, c->r3, F, c->QD.p, 8, s));
+        LSQ_TRY(seg_dot(c, prec, c->rL, D, Z, 8, s));
         return LSQ_OK;
     }
     LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
     LSQ_TRY(trace_into(g, b, prec, c->rH, o.Hp, c->r3, F, 5, s));
     LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->Q.p, 6, s));
     LSQ_TRY(dot_into(g, b, prec, c->rL, o.L, Z, 7, s));
-    LSQ_TRY(dot_into(g, b, prec, c->r3, F, c->QD.p, 8, s));
+    LSQ_TRY(dot_into(g, b, prec, c->rL, D, Z, 8, s));
     double t[9];
     LSQ_TRY(fetch_scalars(g, 9, t, s));
     c123[0] = t[4];

@@ -172,6 +172,8 @@ int trace_into(lsq_geom g, int b, int dtype, int rx, const void *X, int ry, cons
 int dot_into(lsq_geom g, int b, int dtype, int r, const void *X, const void *Y, int slot,
              cudaStream_t s);
 int reducer_ensure(lsq_geom g, int nslots);
+// g->red.scalars[slot] = sum of x[0..m) (float64, fixed order; m < 2^31).
+int sum_into(lsq_geom g, const double *x, int64_t m, int slot, cudaStream_t s);
 int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s);
 
 inline size_t dtype_size(int dtype) { return dtype == LSQ_F64 ? 8 : 4; }

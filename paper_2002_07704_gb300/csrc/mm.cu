@@ -773,6 +773,14 @@ int dot_into(lsq_geom g, int b, int dtype, int r, const void *X, const void *Y, 
     return LSQ_OK;
 }
 
+int sum_into(lsq_geom g, const double *x, int64_t m, int slot, cudaStream_t s) {
+    LSQ_TRY(reducer_ensure(g, slot + 1));
+    note_launch();
+    k_finish<<<1, 1024, 0, s>>>(x, (int)m, g->red.scalars.p + slot);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
 int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s) {
     LSQ_CUDA_TRY(cudaMemcpyAsync(g->red.host, g->red.scalars.p, sizeof(double) * nslots,
                                  cudaMemcpyDeviceToHost, s));
