@@ -10,9 +10,9 @@
 //           Q = H'LS, G1 = Q.LS, G2 = Q^T.LS (= SLH'LS)
 //
 // Products per energy + gradient (ranges in brackets, R3 = R_H+R_L+R_S):
-//   LS = L.S [R_L+R_S], LSL = (LS.L)|R3, Q = H'.LS [R3], and for the gradient the upper
-//   triangles (j >= i) on R_L of T1 = (Q + Q^T).LS and T2 = SL.Q^T, whose sum is the
-//   symmetric G1 + G1^T + G2;
+//   LS = L.S [R_L+R_S], LSL = (LS.L)|R3, Q = H'.LS [R3], and for the gradient one triangle
+//   each on R_L of T1 = (Q + Q^T).LS (formed as its transpose SL.(Q + Q^T)) and T2 = SL.Q^T,
+//   whose sum is the symmetric G1 + G1^T + G2;
 //   Omega = 2 (3 Tr[H' LSL] - 2 <LSL, Q>), since Tr[LSLSLH'] = Tr[LSL (SLH')] and
 //   SLH' = Q^T; N_e = 2 (3 Tr[S LSL] - 2 <LSL, SLS>) with SLS = S.LS [R3].
 // When the gradient is formed, LSL is not needed: by the cyclic property,
@@ -63,13 +63,14 @@ __global__ void k_hprime(int64_t nnzb, int bb, const double *__restrict__ H,
     }
 }
 
-// The gradient from M = G1 + G1^T + G2 = (Q + Q^T).LS + SL.Q^T, held as the upper triangles
-// (blocks with j >= i) of its two terms T1 = (Q + Q^T).LS and T2 = SL.Q^T:
+// The gradient from M = G1 + G1^T + G2 = (Q + Q^T).LS + SL.Q^T = T1 + T2, held as the lower
+// triangle (j <= i) of T1^T = SL.(Q + Q^T) (array T1t) and the upper triangle (j >= i) of
+// T2 = SL.Q^T:
 //   G_ij[r][c] = spin (3 (Q_ij[r][c] + Q_ji[c][r]) - 2 M_ij[r][c]),
-// M_ij = T1_ij + T2_ij for j > i, (T1_ji + T2_ji)^T for j < i, and the symmetric part for j = i.
-// A block (i, j) of the symmetric pattern precedes (j, i) exactly when i < j, so p < tmL[p]
-// selects the upper blocks.  Every element of G and its mirror sum the same values in the
-// same order: G is symmetric to the last bit.
+// M_ij = (T1t_ji)^T + T2_ij for j > i, its transpose for j < i, and the symmetric part for
+// j = i.  A block (i, j) of the symmetric pattern precedes (j, i) exactly when i < j, so
+// p < tmL[p] selects the upper blocks.  Every element of G and its mirror sum the same
+// values in the same order: G is symmetric to the last bit.
 // One warp per row i of L's pattern; the same pass forms the two energy terms of the row:
 // row0[i] = sum_j <L_ij, Q_ij> and row1[i] = sum_j <L_ij, M_ij> / 3 (see the header), with L
 // as the products read it (its float32 copy on the mixed path).
@@ -77,7 +78,7 @@ template <typename T, int B>
 __global__ void k_grad_omega_rows(int n, int b_rt, double spin, const int64_t *__restrict__ rp,
                                   const int64_t *__restrict__ pq, const int64_t *__restrict__ pqt,
                                   const int64_t *__restrict__ tmL, const T *__restrict__ L,
-                                  const T *__restrict__ Q, const T *__restrict__ T1, const T *__restrict__ T2,
+                                  const T *__restrict__ Q, const T *__restrict__ T1t, const T *__restrict__ T2,
                                   double *__restrict__ G, double *__restrict__ row0, double *__restrict__ row1) {
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -96,12 +97,12 @@ __global__ void k_grad_omega_rows(int n, int b_rt, double spin, const int64_t *_
         const double q = qd + (at >= 0 ? (double)Q[at * bb + tr] : 0.0);
         double mv;
         if (p < t) {
-            mv = (double)T1[p * bb + rc] + (double)T2[p * bb + rc];
+            mv = (double)T1t[t * bb + tr] + (double)T2[p * bb + rc];
         } else if (p > t) {
-            mv = (double)T1[t * bb + tr] + (double)T2[t * bb + tr];
+            mv = (double)T1t[p * bb + rc] + (double)T2[t * bb + tr];
         } else {
-            mv = 0.5 * (((double)T1[p * bb + rc] + (double)T2[p * bb + rc]) +
-                        ((double)T1[p * bb + tr] + (double)T2[p * bb + tr]));
+            mv = 0.5 * (((double)T1t[p * bb + tr] + (double)T2[p * bb + rc]) +
+                        ((double)T1t[p * bb + rc] + (double)T2[p * bb + tr]));
         }
         G[e] = spin * (3.0 * q - 2.0 * mv);
         const double l = (double)L[e];
@@ -633,10 +634,16 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         // M = G1 + G1^T + G2 (G1 = Q.LS, G2 = Q^T.LS) is symmetric and equals T1 + T2 with
         // T1 = (Q + Q^T).LS and T2 = SL.Q^T, so the upper triangles of T1 and T2 on L's range
         // give all of it: one full product's work instead of G1 in full plus G2's upper half.
-        // Q + Q^T goes to QD's storage, free until the line search.
+        // Q + Q^T goes to QD's storage, free until the line search.  T1 is formed through its
+        // transpose SL.(Q + Q^T), lower triangle (j <= i), so that the operand whose rows the
+        // kernel walks is SL on L+S's range rather than Q + Q^T on R3: G1 holds T1's upper
+        // blocks transposed.
         void *Qs = c->QD.p;
         LSQ_TRY(sym_sum_on(g, c->r3, b, prec, c->Q.p, Qs, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, Qs, c->r1, tLS, LSop, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 2));
+        if (mat)
+            LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->SL.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
+        else
+            LSQ_TRY(block_matmul(g, b, prec, c->r1, 1, c->LS.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
         // T2 = SL.Q^T: op(B) = Q^T, read as rows of Q; op(A) = SL (materialised for 4 x 4 blocks)
         if (mat)
             LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->SL.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
@@ -711,11 +718,13 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
         LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
     }
     LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
+    // Z = QD^T.P is symmetric, so it is formed as P^T.QD: the operand whose rows the kernel
+    // walks (and stages in shared memory) is then P^T on L+S's range, not QD^T on R3
     if (mat) {
         LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 0, QDT, c->r1, 1, PT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, PT, c->r3, 1, QDT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
     } else {
-        LSQ_TRY(block_matmul(g, b, prec, c->r3, 1, c->QD.p, c->r1, 0, P, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, prec, c->r1, 1, P, c->r3, 0, c->QD.p, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
     }
     if (seg) {
         LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));

@@ -90,7 +90,7 @@ struct ProductPlan {
     int64_t triples = 0;   // block triples the plan executes
     int64_t nblocks = 0;
     int64_t nitems = 0;
-    int upper = 0;         // only blocks with j >= i are computed; the rest mirrored
+    int upper = 0;         // triangle computed: 0 all blocks, 1 j >= i (rest mirrored), 2 j <= i
     int variant[2] = {-1, -1};      // kernel schedule picked by the autotuner (f64, f32)
     int variant16[2] = {-1, -1};    // the fastest of those needing only 16-byte alignment
     float tuned_ms[2] = {0.f, 0.f};
@@ -147,8 +147,9 @@ int find_range(lsq_geom g, double R);
 // Truncated product C = alpha op(A) op(B) + beta C (see lsq_block_matmul).  sym = 1
 // declares the result symmetric (C = C^T in exact arithmetic): only blocks with j >= i
 // are computed and the others are their transposes.  sym = 2 computes the blocks with
-// j >= i only and leaves the others of C as they were (for a caller that needs only the
-// upper triangle of a product that is not itself symmetric).
+// j >= i (for a caller that needs only the upper triangle of a product that is not itself
+// symmetric); the other blocks of C are left unspecified.  sym = 3 likewise the blocks with
+// j <= i.
 int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
                  const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
                  cudaStream_t s, int sym = 0);

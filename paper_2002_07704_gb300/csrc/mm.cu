@@ -582,7 +582,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     if (b == 4 && al16) {
         // plan-driven form: op(A) rows and op(B)^T rows, transposing into scratch if needed
         ProductPlan *pp = nullptr;
-        int prc = plan_build(g, ra, rb, rc, (sym && beta == 0.0) ? 1 : 0, &pp, s);
+        int prc = plan_build(g, ra, rb, rc, sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0), &pp, s);
         if (prc == LSQ_OK) {
             if (triples) *triples = pp->triples;
             if (g->n == 0 || g->pats[rc].nnzb == 0) return LSQ_OK;
@@ -600,7 +600,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
                 LSQ_TRY(transpose_on(g, rb, b, dtype, B, g->scratch_x.p, s));
                 X = g->scratch_x.p;
             }
-            return plan_launch(g, dtype, *pp, ra, rb, rc, Aop, X, C, alpha, beta, s, sym != 2);
+            return plan_launch(g, dtype, *pp, ra, rb, rc, Aop, X, C, alpha, beta, s, sym == 1);
         }
         if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
         (void)cudaGetLastError();  // a failed allocation is not sticky; drop it
@@ -608,11 +608,11 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     } else {
         // any other block size (or unaligned 4 x 4 blocks): warp-per-block kernel, no scratch
         ProductPlan *pp = nullptr;
-        int prc = plan_build(g, ra, rb, rc, (sym && beta == 0.0) ? 1 : 0, &pp, s);
+        int prc = plan_build(g, ra, rb, rc, sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0), &pp, s);
         if (prc == LSQ_OK) {
             if (triples) *triples = pp->triples;
             if (g->n == 0 || g->pats[rc].nnzb == 0) return LSQ_OK;
-            return plan_launch_gen(g, b, dtype, *pp, ra, ta, rb, tb, rc, A, B, C, alpha, beta, s, sym != 2);
+            return plan_launch_gen(g, b, dtype, *pp, ra, ta, rb, tb, rc, A, B, C, alpha, beta, s, sym == 1);
         }
         if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
         (void)cudaGetLastError();

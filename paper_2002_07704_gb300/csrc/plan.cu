@@ -32,6 +32,12 @@
 
 namespace lsq {
 
+// Triangle of C a plan covers: 0 every block, 1 the blocks with j >= i, 2 those with j <= i.
+__device__ __forceinline__ bool tri_skip(int tri, int i, int j) {
+    return tri == 1 ? j < i : (tri == 2 ? j > i : false);
+}
+
+
 constexpr int kMaxPlanRow = 8192;  // longest row of C a plan handles (shared-memory sort)
 
 // ---- symbolic product: item count of every block of C -----------------------
@@ -54,7 +60,7 @@ __global__ void __launch_bounds__(512) k_plan_count(int n, const int64_t *__rest
         for (int64_t s = c_ptr[i] + warp; s < c_ptr[i + 1]; s += nwarps) {
             const int j = c_col[s];
             int c = 0;
-            if (!upper || j >= i)
+            if (!tri_skip(upper, i, j))
                 for (int64_t q = x_ptr[j] + lane; q < x_ptr[j + 1]; q += 32) c += amap[x_col[q]] >= 0;
             for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
             if (lane == 0) cnt[s] = c;
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(512) k_plan_fill(int n, const int64_t *__restr
         __syncthreads();
         for (int64_t s = c_ptr[i] + warp; s < c_ptr[i + 1]; s += nwarps) {
             const int j = c_col[s];
-            if (upper && j < i) continue;
+            if (tri_skip(upper, i, j)) continue;
             const int64_t x0 = x_ptr[j], x1 = x_ptr[j + 1];
             int64_t w = item_ptr[s];
             for (int64_t qb = x0; qb < x1; qb += 32) {
@@ -225,7 +231,7 @@ __device__ __forceinline__ void stage_row(T *As, const T *__restrict__ A, int64_
 
 struct PlanArgs {
     int n;                      // atoms (rows)
-    int upper;                  // compute only blocks with j >= i
+    int upper;                  // triangle of C computed: 0 all, 1 j >= i, 2 j <= i
     const int64_t *c_ptr;       // row pointers of C
     int64_t nblocks;            // blocks of C
     const int64_t *perm;        // blocks of C in processing order
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4(PlanArgs g) {
             const T *__restrict__ arow = A + 16 * g.a_ptr[i] + 4 * r;
             for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
                 const int64_t s = g.perm[e];
-                if (g.upper && g.c_col[s] < i) continue;  // lower block: mirrored afterwards
+                if (tri_skip(g.upper, i, g.c_col[s])) continue;  // outside the triangle
                 const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
                 const int64_t i0 = g.item_ptr[s];
                 const T v = plan_items<T, UNROLL>(g.items + i0, (int)(g.item_ptr[s + 1] - i0), arow, xrow);
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4(PlanArgs g) {
         for (int64_t t = team0; t < g.nblocks; t += nteams) {
             const int64_t s = g.perm[t];
             const int i = (int)g.c_row[s];
-            if (g.upper && g.c_col[s] < i) continue;
+            if (tri_skip(g.upper, i, g.c_col[s])) continue;
             const T *__restrict__ arow = A + 16 * g.a_ptr[i] + 4 * r;
             const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
             const int64_t i0 = g.item_ptr[s];
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(1024) k_mm_plan_b4_smem(PlanArgs g) {
         const T *arow = As + 4 * r;
         for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
             const int64_t s = g.perm[e];
-            if (g.upper && g.c_col[s] < i) continue;
+            if (tri_skip(g.upper, i, g.c_col[s])) continue;
             const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
             const int64_t i0 = g.item_ptr[s];
             const uint32_t *__restrict__ it = g.items + i0;
@@ -555,7 +561,7 @@ __global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
             }
             for (int64_t e = g.c_ptr[i] + team; e < g.c_ptr[i + 1]; e += nteams) {
                 const int64_t s = g.perm[e];
-                if (g.upper && g.c_col[s] < i) continue;
+                if (tri_skip(g.upper, i, g.c_col[s])) continue;
                 work(s, i, part);
             }
         }
@@ -565,7 +571,7 @@ __global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
         for (int64_t t = team0; t < g.nblocks; t += nteams) {
             const int64_t s = g.perm[t];
             const int i = (int)g.c_row[s];
-            if (g.upper && g.c_col[s] < i) continue;
+            if (tri_skip(g.upper, i, g.c_col[s])) continue;
             work(s, i, 0);
         }
     }
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
     for (int64_t t = w0; t < g.nblocks; t += nw) {
         const int64_t s = g.perm[t];
         const int i = (int)g.c_row[s];
-        if (g.upper && g.c_col[s] < i) continue;
+        if (tri_skip(g.upper, i, g.c_col[s])) continue;
         const int j = g.c_col[s];
         const int64_t abase = g.a_ptr[i], xbase = g.x_ptr[j];
         const int64_t i0 = g.item_ptr[s], i1 = g.item_ptr[s + 1];
@@ -689,7 +695,7 @@ __global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
     for (int64_t t = w0; t < g.nblocks; t += nw) {
         const int64_t s = g.perm[t];
         const int i = (int)g.c_row[s];
-        if (g.upper && g.c_col[s] < i) continue;
+        if (tri_skip(g.upper, i, g.c_col[s])) continue;
         const int j = g.c_col[s];
         const int64_t abase = g.a_ptr[i], xbase = g.x_ptr[j];
         const int64_t i0 = g.item_ptr[s], i1 = g.item_ptr[s + 1];
@@ -792,7 +798,7 @@ __global__ void k_rows_of(int n, const int64_t *__restrict__ c_ptr, int64_t *__r
 }
 
 int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out, cudaStream_t s) {
-    auto key = std::make_tuple(ra, rb, rc + (upper ? 1000 : 0));
+    auto key = std::make_tuple(ra, rb, rc + 1000 * upper);
     auto it = g->pplans.find(key);
     if (it != g->pplans.end()) {
         *out = &it->second;
@@ -993,14 +999,14 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
             p.tuned_ms[di] = best;
             if (std::getenv("LSQ_TUNE_LOG"))
                 std::fprintf(stderr, "lsq autotune: ranges (%g, %g, %g)%s %s: variant %d, %.3f ms\n",
-                             g->pats[ra].R, g->pats[rb].R, g->pats[rc].R, p.upper ? " upper" : "",
+                             g->pats[ra].R, g->pats[rb].R, g->pats[rc].R, p.upper == 1 ? " upper" : (p.upper == 2 ? " lower" : ""),
                              dtype == LSQ_F64 ? "f64" : "f32", bi, best);
         }
     }
     // a later call may pass operands that the tuned variant cannot read
     const int use = smem_for(choice) >= 0 ? choice : std::max(p.variant16[di], 0);
     LSQ_TRY(run_variant(g, v[use], a, p.nblocks, s, smem_for(use)));
-    if (p.upper && mirror) {
+    if (p.upper == 1 && mirror) {
         LSQ_TRY(ensure_tmap(g, rc, s));
         const int64_t m = g->pats[rc].nnzb * 16;
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16));
@@ -1056,7 +1062,7 @@ int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, 
         else go(t16 ? k_mm_plan_t16<float, false, false> : k_mm_plan_gen<float, false, false>);
     }
     LSQ_CHECK_LAUNCH();
-    if (p.upper && mirror) {
+    if (p.upper == 1 && mirror) {
         // C_ij = (C_ji)^T for j < i, any block size
         LSQ_TRY(mirror_lower_gen(g, rc, b, dtype, C, s));
     }
