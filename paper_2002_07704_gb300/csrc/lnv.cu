@@ -125,6 +125,13 @@ __global__ void k_cg_dir(int64_t m, double beta, const double *__restrict__ G, d
         D[e] = beta == 0.0 ? -G[e] : -G[e] + beta * D[e];
 }
 
+__global__ void k_axpy_f32(int64_t m, double a, const float *__restrict__ x, float *__restrict__ y) {
+    const float af = (float)a;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = fmaf(af, x[e], y[e]);
+}
+
 __global__ void k_axpy(int64_t m, double a, const double *__restrict__ x, double *__restrict__ y) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -404,6 +411,10 @@ struct lsq_lnv_s {
 
 static int64_t nvals(lsq_lnv c, int r) { return c->g->pats[r].nnzb * c->b * c->b; }
 
+// Steps between fresh products Q = H'LS in the single-system CG (Q is updated along the line
+// search in between).
+constexpr int kQFresh = 10;
+
 extern "C" int lsq_lnv_default_opts(lsq_lnv_opts *o) {
     clear_error();
     if (!o) return set_error(LSQ_ERR_INVALID_ARG, "opts is null");
@@ -595,8 +606,10 @@ int seg_trace(lsq_lnv c, int prec, int rx, const void *X, int ry, const void *Y,
 
 // Omega, N_e (scalars slots 0..3 hold the four traces) and, if G != null, the gradient.
 // seg: per-system sums into the batch slots, nothing fetched (omega, ne ignored).
+// reuse_q: c->Q already holds H'LS for this L (updated along the line search), skip its product.
 int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *G,
-                    double *omega, double *ne, cudaStream_t s, bool seg = false, bool want_ne = false) {
+                    double *omega, double *ne, cudaStream_t s, bool seg = false, bool want_ne = false,
+                    bool reuse_q = false) {
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
@@ -613,7 +626,8 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     const void *LSop = mat ? c->SL.p : c->LS.p;  // operand giving LS as op(B)
     const int tLS = mat ? 1 : 0;
     if (mat) LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, tLS, LSop, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
+    if (!reuse_q)
+        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, tLS, LSop, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
     auto tr = [&](int rx, const void *X, int ry, const void *Y, int slot) {
         return seg ? seg_trace(c, prec, rx, X, ry, Y, slot, s) : trace_into(g, b, prec, rx, X, ry, Y, slot, s);
     };
@@ -815,7 +829,11 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
         double gg_prev = 0.0;
         bool converged = false;
         for (int it = 0; it < budget; ++it) {
-            LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, c->G.p, nullptr, nullptr, s));
+            // Q = H'LS is linear in L: after L += a D it is Q + a H'DS, and H'DS is the line
+            // search's QD.  It is updated that way between fresh products every kQFresh steps
+            // (and at every CG restart and phase start), which saves one R3 product per step.
+            const bool reuse_q = it % std::min(o.cg_reset, kQFresh) != 0;
+            LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, c->G.p, nullptr, nullptr, s, false, false, reuse_q));
             LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
             LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
             double t[12];
@@ -849,6 +867,12 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
             }
             note_launch();
             k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L);
+            const int64_t n3 = nvals(c, c->r3);
+            note_launch();
+            if (prec == LSQ_F64)
+                k_axpy<<<grid_for(n3), 256, 0, s>>>(n3, a, (const double *)c->QD.p, (double *)c->Q.p);
+            else
+                k_axpy_f32<<<grid_for(n3), 256, 0, s>>>(n3, a, (const float *)c->QD.p, (float *)c->Q.p);
             LSQ_CHECK_LAUNCH();
             std::swap(c->G.p, c->Gp.p);
             gg_prev = gg;
