@@ -380,6 +380,19 @@ __global__ void k_batch_update(int n, int bb, const int64_t *__restrict__ rp, co
     }
 }
 
+// y += alpha_sys x on the rows of a pattern (alpha of the row's system): Q += a QD after the step.
+template <typename T>
+__global__ void k_batch_axpy_rows(int n, int bb, const int64_t *__restrict__ rp, const int *__restrict__ atom_sys,
+                                  const double *__restrict__ alpha, const T *__restrict__ x, T *__restrict__ y) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double a = alpha[atom_sys ? atom_sys[warp] : 0];
+    if (a == 0.0) return;
+    const T at = (T)a;
+    for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) y[e] = fma(at, x[e], y[e]);
+}
+
 
 static int grid_for(int64_t m) {
     int64_t g = (m + 255) / 256;
@@ -966,14 +979,15 @@ BatchDev batch_dev(lsq_lnv c) {
 }
 
 // One CG step of every system, enqueued on s with no host synchronisation.
+// reuse_q: Q was carried along the previous step's line search (see lsq_lnv_minimise).
 int batch_step(lsq_lnv c, double *L, const double *S, double spin, int prec, double tol, int cg_reset,
-               cudaStream_t s) {
+               cudaStream_t s, bool reuse_q) {
     lsq_geom g = c->g;
     const int ns = g->n_sys, bb = c->b * c->b;
     const int rows = (int)(((int64_t)g->n * 32 + 255) / 256);
     const int *asys = g->n_sys > 1 ? g->atom_sys.p : nullptr;
     BatchDev d = batch_dev(c);
-    LSQ_TRY(energy_gradient(c, L, S, spin, prec, c->G.p, nullptr, nullptr, s, true));
+    LSQ_TRY(energy_gradient(c, L, S, spin, prec, c->G.p, nullptr, nullptr, s, true, false, reuse_q));
     LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
     LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
     note_launch();
@@ -988,6 +1002,13 @@ int batch_step(lsq_lnv c, double *L, const double *S, double spin, int prec, dou
     note_launch();
     k_batch_update<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rL].row_ptr.p, asys, c->b_alpha.p, c->D.p, L,
                                         c->G.p, c->Gp.p);
+    note_launch();
+    if (prec == LSQ_F64)
+        k_batch_axpy_rows<double><<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->r3].row_ptr.p, asys, c->b_alpha.p,
+                                                        (const double *)c->QD.p, (double *)c->Q.p);
+    else
+        k_batch_axpy_rows<float><<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->r3].row_ptr.p, asys, c->b_alpha.p,
+                                                       (const float *)c->QD.p, (float *)c->Q.p);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -1088,22 +1109,33 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
         LSQ_CUDA_TRY(cudaMemsetAsync(c->b_step.p, 0, sizeof(int), s));
         // tol = 0 freezes nothing; the refinement uses tol = 0 (fixed number of steps)
         const double tol = phase == 0 ? o.tol_ha_per_atom : 0.0;
-        cudaGraphExec_t exec = nullptr;
-        cudaGraph_t graph = nullptr;
+        // Two step graphs: one that forms Q = H'LS afresh, one that carries it along the line
+        // search (every kQFresh-th step is fresh, as in the single-system minimiser).
+        struct StepGraphs {
+            cudaGraphExec_t exec[2] = {nullptr, nullptr};
+            cudaGraph_t graph[2] = {nullptr, nullptr};
+            ~StepGraphs() {
+                for (int k = 0; k < 2; ++k) {
+                    if (exec[k]) cudaGraphExecDestroy(exec[k]);
+                    if (graph[k]) cudaGraphDestroy(graph[k]);
+                }
+            }
+        } sg;
         for (int it = 0; it < budget; ++it) {
-            if (it == 1 && o.graph) {
-                // plans, maps and autotuning exist after the first step: capture one step
+            const int kind = it % std::min(o.cg_reset, kQFresh) != 0 ? 1 : 0;
+            if (it >= 1 && o.graph && !sg.exec[kind]) {
+                // plans, maps and autotuning exist after the first step: capture this kind of step
                 LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                int rc = batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s);
-                cudaError_t ec = cudaStreamEndCapture(s, &graph);
+                int rc = batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s, kind == 1);
+                cudaError_t ec = cudaStreamEndCapture(s, &sg.graph[kind]);
                 if (rc != LSQ_OK) return rc;
                 if (ec != cudaSuccess) return set_error(LSQ_ERR_CUDA, cudaGetErrorString(ec));
-                LSQ_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+                LSQ_CUDA_TRY(cudaGraphInstantiate(&sg.exec[kind], sg.graph[kind], 0));
             }
-            if (exec) {
-                LSQ_CUDA_TRY(cudaGraphLaunch(exec, s));
+            if (sg.exec[kind]) {
+                LSQ_CUDA_TRY(cudaGraphLaunch(sg.exec[kind], s));
             } else {
-                LSQ_TRY(batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s));
+                LSQ_TRY(batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s, kind == 1));
             }
             if (tol > 0.0 && (it + 1) % check_every == 0) {
                 LSQ_CUDA_TRY(cudaMemcpyAsync(frozen.data(), c->b_frozen.p, sizeof(int) * ns,
@@ -1114,8 +1146,6 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
                 if (all) break;
             }
         }
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));
         if (phase == 1) {
             std::vector<int> it_after(ns);
