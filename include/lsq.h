@@ -150,6 +150,26 @@ int lsq_block_matmul(lsq_geom g, int b, int precision,
                      int range_c, void *C_dev, double alpha, double beta,
                      int64_t *n_triples_host, void *stream);
 
+/*
+ * lsq_block_matmul restricted to one triangle of C's pattern (the products
+ * of the LNV step whose result is symmetric, or of which only one triangle
+ * is needed, Sec. 2.3.2):
+ *   triangle 0: every block (same as lsq_block_matmul);
+ *   triangle 1: C is symmetric in exact arithmetic: the blocks with j >= i
+ *               are computed and the others set to their transposes
+ *               (requires beta = 0);
+ *   triangle 2: only the blocks with j >= i are computed;
+ *   triangle 3: only the blocks with j <= i are computed.
+ * With 2 and 3 the other blocks of C are left unspecified.  n_triples_host
+ * receives the triples of the computed blocks.  Other arguments, errors
+ * and plan caching as for lsq_block_matmul (each triangle has its plan).
+ */
+int lsq_block_matmul_tri(lsq_geom g, int b, int precision,
+                         int range_a, int trans_a, const void *A_dev,
+                         int range_b, int trans_b, const void *B_dev,
+                         int range_c, void *C_dev, double alpha, double beta, int triangle,
+                         int64_t *n_triples_host, void *stream);
+
 /* out = alpha X^T on pattern range_out: out_ij = alpha (X_ji)^T where (j, i)
  * is stored in X's pattern, zero elsewhere (the adjoint of a trace and of a
  * truncation, Sec. 2.3.2).  out must not alias X.  Enqueued on stream; the

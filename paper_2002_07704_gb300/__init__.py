@@ -72,6 +72,7 @@ def load():
         "lsq_pattern": (I, [P, I, P, P, P]),
         "lsq_pattern_copy": (I, [P, I, P, P, P]),
         "lsq_block_matmul": (I, [P, I, I, I, I, P, I, I, P, I, P, D, D, P, P]),
+        "lsq_block_matmul_tri": (I, [P, I, I, I, I, P, I, I, P, I, P, D, D, I, P, P]),
         "lsq_trace": (I, [P, I, I, I, P, I, P, P, P]),
         "lsq_transpose": (I, [P, I, I, I, P, I, P, D, P]),
         "lsq_trace_static": (I, [P, I, I, I, P, I, P, P, P]),
@@ -96,7 +97,7 @@ def load():
 def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lsq_last_error", "lsq_version", "lsq_launch_count", "lsq_build_neighbour_lists", "lsq_geom_destroy",
-            "lsq_geom_info", "lsq_geom_concat", "lsq_geom_systems", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_trace", "lsq_transpose",
+            "lsq_geom_info", "lsq_geom_concat", "lsq_geom_systems", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_block_matmul_tri", "lsq_trace", "lsq_transpose",
             "lsq_trace_static",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
@@ -215,14 +216,24 @@ def concat_geometries(geoms, stream=None):
 
 
 def block_matmul(geom, b, A, range_a, B, range_b, C, range_c, precision=F64, trans_a=False,
-                 trans_b=False, alpha=1.0, beta=0.0, stream=None):
-    """C = alpha op(A) op(B) + beta C on C's range pattern; returns the triple count."""
+                 trans_b=False, alpha=1.0, beta=0.0, stream=None, triangle=0):
+    """C = alpha op(A) op(B) + beta C on C's range pattern; returns the triple count.
+
+    triangle: 0 every block; 1 symmetric result (upper blocks computed, lower ones
+    mirrored); 2 only blocks with j >= i; 3 only blocks with j <= i.
+    """
     import torch
     dt = torch.float64 if precision == F64 else torch.float32
     nt = ctypes.c_int64()
-    _check(load().lsq_block_matmul(geom.handle, b, precision, range_a, int(trans_a), _dev(A, dt),
-                                   range_b, int(trans_b), _dev(B, dt), range_c, _dev(C, dt),
-                                   float(alpha), float(beta), ctypes.byref(nt), _stream(stream)))
+    if triangle:
+        _check(load().lsq_block_matmul_tri(geom.handle, b, precision, range_a, int(trans_a),
+                                           _dev(A, dt), range_b, int(trans_b), _dev(B, dt), range_c,
+                                           _dev(C, dt), float(alpha), float(beta), int(triangle),
+                                           ctypes.byref(nt), _stream(stream)))
+    else:
+        _check(load().lsq_block_matmul(geom.handle, b, precision, range_a, int(trans_a), _dev(A, dt),
+                                       range_b, int(trans_b), _dev(B, dt), range_c, _dev(C, dt),
+                                       float(alpha), float(beta), ctypes.byref(nt), _stream(stream)))
     return nt.value
 
 

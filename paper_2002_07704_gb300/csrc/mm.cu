@@ -802,6 +802,18 @@ extern "C" int lsq_block_matmul(lsq_geom g, int b, int precision, int range_a, i
                         C, alpha, beta, n_triples, (cudaStream_t)stream);
 }
 
+extern "C" int lsq_block_matmul_tri(lsq_geom g, int b, int precision, int range_a, int trans_a,
+                                    const void *A, int range_b, int trans_b, const void *B, int range_c,
+                                    void *C, double alpha, double beta, int triangle, int64_t *n_triples,
+                                    void *stream) {
+    clear_error();
+    if (triangle < 0 || triangle > 3) return set_error(LSQ_ERR_INVALID_ARG, "triangle must be 0, 1, 2 or 3");
+    if (triangle == 1 && beta != 0.0)
+        return set_error(LSQ_ERR_INVALID_ARG, "triangle 1 (symmetric result) needs beta = 0");
+    return block_matmul(g, b, precision, range_a, trans_a != 0, A, range_b, trans_b != 0, B, range_c,
+                        C, alpha, beta, n_triples, (cudaStream_t)stream, triangle);
+}
+
 extern "C" int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X, int range_y,
                          const void *Y, double *out, void *stream) {
     clear_error();

@@ -97,6 +97,46 @@ def test_block_matmul_matches_oracle(n, b, ra, rb, rc, ta, tb, prec):
         assert np.abs(got - ref_val).max() <= 1e-5 * scale
 
 
+@pytest.mark.parametrize("b", [4, 13])
+@pytest.mark.parametrize("prec", [lsq.F64, lsq.F32])
+def test_block_matmul_triangles(b, prec):
+    """lsq_block_matmul_tri: the computed triangle equals the oracle's product there; with
+    triangle 1 the other blocks are the transposes of the computed ones."""
+    n = 2 if b == 4 else 1
+    pos, cell = si(n, 0.1, config_seed(0) + 91 + b)
+    ra, rb, rc = (16.6, 10.0, 10.0) if b == 4 else (4.0, 3.0, 4.0)
+    ranges = sorted(set([ra, rb, rc]))
+    g = gpu_geometry(pos, cell, ranges)
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in ranges}
+    rng = np.random.default_rng(500 + b)
+    A = oracle.Bsr(P[ra], b, _rand(P[ra], b, rng))
+    B = oracle.Bsr(P[rb], b, _rand(P[rb], b, rng))
+    ref, _ = oracle.matmul(A, B, P[rc])
+    pc = P[rc]
+    rows = np.repeat(np.arange(pc.n), np.diff(pc.ptr))
+    upper = pc.col >= rows
+    lower = pc.col <= rows
+    dt = torch.float64 if prec == lsq.F64 else torch.float32
+    absA, absB = oracle.Bsr(P[ra], b, np.abs(A.val)), oracle.Bsr(P[rb], b, np.abs(B.val))
+    bound = oracle.matmul(absA, absB, pc)[0].val.max()
+    tol = 1e-12 * np.abs(ref.val).max() if prec == lsq.F64 else 1e-5 * bound
+    for tri, mask in ((2, upper), (3, lower), (1, upper)):
+        C = torch.zeros((pc.nnzb, b, b), dtype=dt, device="cuda")
+        lsq.block_matmul(g, b, cuda(A.val, dt), g.range_id(ra), cuda(B.val, dt), g.range_id(rb), C,
+                         g.range_id(rc), precision=prec, triangle=tri)
+        got = C.double().cpu().numpy()
+        assert np.abs(got[mask] - ref.val[mask]).max() <= tol
+        if tri == 1:
+            # lower blocks hold the transposes of the upper ones, bit for bit
+            tpos = {(int(i), int(j)): k for k, (i, j) in enumerate(zip(rows, pc.col))}
+            for k in np.nonzero(~upper)[0]:
+                kt = tpos[(int(pc.col[k]), int(rows[k]))]
+                assert np.array_equal(got[k], got[kt].T)
+    with pytest.raises(lsq.LsqError):
+        lsq.block_matmul(g, b, cuda(A.val, dt), g.range_id(ra), cuda(B.val, dt), g.range_id(rb), C,
+                         g.range_id(rc), precision=prec, triangle=1, beta=0.5)
+
+
 def _at_offset(x, off):
     """A copy of x whose data starts `off` elements into a fresh allocation."""
     buf = torch.empty(x.numel() + off, dtype=x.dtype, device=x.device)
