@@ -340,6 +340,22 @@ def run_ours(args):
         except Exception:
             traffic = None
 
+    # --- the sparse inverse overlap (Hotelling) on L's range, the LNV metric ---
+    # float32 products from the scaled start, then float64 steps continuing from that X
+    hot = {}
+    Xh = torch.zeros((geom.nnzb(2), B, B), dtype=torch.float64, device="cuda")
+    lsq.hotelling_inverse(geom, B, Sd, 0, Xh, 2, 3, 1, precision=lsq.F32)   # plans, warm-up
+    lsq.hotelling_inverse(geom, B, Sd, 0, Xh, 2, 3, 1, precision=lsq.F64)
+    for prec, k, name, start in ((lsq.F32, 10, "f32", True), (lsq.F64, 3, "f64", False)):
+        barrier()
+        e0.record(stream)
+        dxs = lsq.hotelling_inverse(geom, B, Sd, 0, Xh, 2, 3, k, precision=prec, start=start)
+        e1.record(stream)
+        barrier()
+        hot[name] = {"ms_per_iteration": e0.elapsed_time(e1) / k, "iterations": k,
+                     "from": "scaled start" if start else "the float32 result",
+                     "last_dx_fro": dxs[-1]}
+
     # --- end to end through the public API, host buffers ---
     Lh = L0.cpu().pin_memory()
     Sh = Sd.cpu().pin_memory()
@@ -396,6 +412,8 @@ def run_ours(args):
                          "kernel": "k_mm_plan_b4_rb<float, ...> (schedule picked by the autotuner)",
                          "hbm_frac": abytes / rms / 1e6 / hbm_peak, "hbm_peak_kind": hbm_kind,
                          "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"},
+            "hotelling": dict(hot, workload="X = S^-1 approximated on the 10 A range by "
+                                             "X <- 2X - (X S) X from X0 = S / s^2, the LNV metric of Sec. 2.3.2"),
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": launches,

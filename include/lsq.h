@@ -207,6 +207,30 @@ int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
 int lsq_trace_static(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
                      int range_y, const void *Y_dev, double *out_dev, void *stream);
 
+/* ---- sparse inverse overlap (Sec. 2.3.2, after Eq. 8) ----------------- */
+
+/*
+ * Approximate sparse inverse of the overlap S by the Hotelling iteration,
+ * the metric the paper's LNV minimisation uses:
+ *     X_{n+1} = 2 X_n - (X_n S) X_n,
+ * with X S formed on pattern range_xs (which must cover the natural range
+ * R_X + R_S, else LSQ_ERR_INVALID_ARG) and X S X restricted to range_x.
+ * Untruncated, I - X_{n+1} S = (I - X_n S)^2.
+ *
+ * S_dev: float64 blocks on range_s, symmetric (S_ij = S_ji^T, as an overlap
+ * is).  X_dev: float64 blocks on range_x, in/out.  start != 0 first sets
+ * X_0 = S / s^2 on range_x, s the largest absolute row sum of S (this start
+ * converges for any symmetric positive definite S); start = 0 iterates
+ * from the X given (which must be symmetric).  n_iter steps are taken; if
+ * dx_host is not NULL, dx_host[n] receives |X_{n+1} - X_n|_F.
+ * precision: LSQ_F64, or LSQ_F32 for float32 products (X is updated in
+ * float64).  Allocates its workspace per call and synchronises stream
+ * before returning.
+ */
+int lsq_hotelling_inverse(lsq_geom g, int b, int precision, int range_s, const double *S_dev,
+                          int range_x, int range_xs, double *X_dev, int start, int n_iter,
+                          double *dx_host, void *stream);
+
 /* ---- LNV grand-potential minimisation (Sec. 2.3.2, Eq. 8) ----------- */
 
 typedef struct {

@@ -76,6 +76,7 @@ def load():
         "lsq_trace": (I, [P, I, I, I, P, I, P, P, P]),
         "lsq_transpose": (I, [P, I, I, I, P, I, P, D, P]),
         "lsq_trace_static": (I, [P, I, I, I, P, I, P, P, P]),
+        "lsq_hotelling_inverse": (I, [P, I, I, I, P, I, I, P, I, I, P, P]),
         "lsq_lnv_default_opts": (I, [P]),
         "lsq_lnv_required_ranges": (I, [D, D, D, P]),
         "lsq_lnv_create": (I, [P, I, D, D, D, P]),
@@ -98,7 +99,7 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lsq_last_error", "lsq_version", "lsq_launch_count", "lsq_build_neighbour_lists", "lsq_geom_destroy",
             "lsq_geom_info", "lsq_geom_concat", "lsq_geom_systems", "lsq_pattern", "lsq_pattern_copy", "lsq_block_matmul", "lsq_block_matmul_tri", "lsq_trace", "lsq_transpose",
-            "lsq_trace_static",
+            "lsq_trace_static", "lsq_hotelling_inverse",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
             "lsq_lnv_minimise_batch"]
@@ -266,6 +267,20 @@ def trace_static(geom, b, X, range_x, Y, range_y, out, precision=F64, stream=Non
     dt = torch.float64 if precision == F64 else torch.float32
     _check(load().lsq_trace_static(geom.handle, b, precision, range_x, _dev(X, dt), range_y,
                                    _dev(Y, dt), _dev(out, torch.float64), _stream(stream)))
+
+
+def hotelling_inverse(geom, b, S, range_s, X, range_x, range_xs, n_iter, precision=F64, start=True,
+                      stream=None):
+    """Approximate sparse inverse of S on range_x by the Hotelling iteration (in place in X).
+
+    Returns the list of |X_{n+1} - X_n|_F (one per step).  See lsq_hotelling_inverse.
+    """
+    import torch
+    dx = (ctypes.c_double * max(int(n_iter), 1))()
+    _check(load().lsq_hotelling_inverse(geom.handle, b, precision, range_s, _dev(S, torch.float64),
+                                        range_x, range_xs, _dev(X, torch.float64), int(bool(start)),
+                                        int(n_iter), dx, _stream(stream)))
+    return [dx[k] for k in range(int(n_iter))]
 
 
 def lnv_required_ranges(R_S, R_H, R_L):
