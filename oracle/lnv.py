@@ -22,7 +22,8 @@ Readings taken here (the paper gives no formula for them):
     arithmetic; taking it explicitly stops rounding from seeding an
     antisymmetric component, along which Omega is unbounded below;
   * conjugate gradients of Polak-Ribiere form, beta = max(0, beta_PR),
-    direction reset to -G every 40 steps, and an exact line minimisation:
+    direction reset to -G every 40 steps (or to -X G X with the metric X of
+    metric_gradient), and an exact line minimisation:
     Omega(L + a D) is a cubic c0 + c1 a + c2 a^2 + c3 a^3 in a and the step
     is its local minimum.
 Intermediate products are kept at their natural range (the sum of their
@@ -184,29 +185,49 @@ def line_minimum(c1, c2, c3):
     return None
 
 
-def minimise(lnv, L0, n_iter, reset=40, tol_ha_per_atom=None):
+def metric_gradient(lnv, G, X):
+    """The gradient in the metric X ~ S^-1: P = (X G X) restricted to L's range.
+
+    Sec. 2.3.2 (after Eq. 8): the minimisation uses an approximate sparse
+    inverse overlap as its metric.  G is covariant in the non-orthogonal
+    basis; X G X is the corresponding contravariant direction.  X G is kept
+    at its natural range, then (X G) X is restricted to L's range and
+    symmetrised like G.
+    """
+    m = lnv.sys
+    XG = mm(m, X, G)
+    P = mm(m, XG, X, R=lnv.pat_L.R)
+    return 0.5 * (P + transpose(P, P.pat))
+
+
+def minimise(lnv, L0, n_iter, reset=40, tol_ha_per_atom=None, metric=None):
     """Polak-Ribiere CG on Omega(L) with exact cubic line minimisation.
 
+    metric: None (plain gradients), or an approximate inverse overlap X on
+    its own range, with which the search directions are built from
+    P = X G X (preconditioned Polak-Ribiere: beta = <G, P - P_prev> /
+    <G_prev, P_prev>).
     Returns (L, history); history[k] holds Omega (eV), N_e, the predicted
     Omega after the step, alpha, beta and max |G| of step k.
     """
     L = L0.copy()
-    D = Gp = None
+    D = Gp = Pp = None
     hist = []
     n = lnv.sys.n
     for it in range(n_iter):
         om, ne = lnv.energy(L)
         G = lnv.gradient(L)
         G = 0.5 * (G + transpose(G, G.pat))
+        P = G if metric is None else metric_gradient(lnv, G, metric)
         beta = 0.0
         if D is None or it % reset == 0:
-            D = -1.0 * G
+            D = -1.0 * P
         else:
-            beta = max(0.0, dot(G, G - Gp) / dot(Gp, Gp))
-            D = -1.0 * G + beta * D
+            beta = max(0.0, dot(G, P - Pp) / dot(Gp, Pp))
+            D = -1.0 * P + beta * D
         c1, c2, c3 = lnv.cubic(L, D, G)
         if c1 >= 0.0:                       # not a descent direction: restart
-            D = -1.0 * G
+            D = -1.0 * P
             beta = 0.0
             c1, c2, c3 = lnv.cubic(L, D, G)
         a = line_minimum(c1, c2, c3)
@@ -216,7 +237,7 @@ def minimise(lnv, L0, n_iter, reset=40, tol_ha_per_atom=None):
         om_next = om + c1 * a + c2 * a * a + c3 * a * a * a
         hist.append(dict(omega=om, ne=ne, omega_next=om_next, alpha=a, beta=beta,
                          gmax=float(np.abs(G.val).max()), c=(c1, c2, c3)))
-        Gp = G
+        Gp, Pp = G, P
         if tol_ha_per_atom is not None and abs(om_next - om) / HA_EV / n < tol_ha_per_atom:
             break
     return L, hist
