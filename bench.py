@@ -356,6 +356,31 @@ def run_ours(args):
                      "from": "scaled start" if start else "the float32 result",
                      "last_dx_fro": dxs[-1]}
 
+    # --- steps to a tolerance: plain CG against CG in the metric X ~ S^-1 (X on S's range) ---
+    tol = 1e-6
+    mcg = {"tol_ha_per_atom": tol}
+    Xs = torch.zeros((geom.nnzb(0), B, B), dtype=torch.float64, device="cuda")
+    barrier()
+    e0.record(stream)
+    lsq.hotelling_inverse(geom, B, Sd, 0, Xs, 0, 3, 12, precision=lsq.F32)
+    lsq.hotelling_inverse(geom, B, Sd, 0, Xs, 0, 3, 2, precision=lsq.F64, start=False)
+    e1.record(stream)
+    barrier()
+    mcg["hotelling_ms"] = e0.elapsed_time(e1)
+    for name, metric in (("plain", False), ("metric", True)):
+        if metric:
+            ctx.set_metric(Xs, 0, 3)
+        Lt = L0.clone()
+        barrier()
+        e0.record(stream)
+        rt = ctx.minimise(Lt, Sd, Hd, MU, max_iter=300, tol_ha_per_atom=tol, precision=lsq.F32,
+                          refine_iter=0, final_eval=False)
+        e1.record(stream)
+        barrier()
+        mcg[name] = {"iterations": int(rt["iterations"]), "ms": e0.elapsed_time(e1),
+                     "status": int(rt["status"])}
+    ctx.set_metric(None, 0, 3)
+
     # --- end to end through the public API, host buffers ---
     Lh = L0.cpu().pin_memory()
     Sh = Sd.cpu().pin_memory()
@@ -414,6 +439,9 @@ def run_ours(args):
                          "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"},
             "hotelling": dict(hot, workload="X = S^-1 approximated on the 10 A range by "
                                              "X <- 2X - (X S) X from X0 = S / s^2, the LNV metric of Sec. 2.3.2"),
+            "metric_cg": dict(mcg, workload="mixed-precision CG from L0 until |dOmega|/N < tol; "
+                                               "metric: X from 12 float32 + 2 float64 Hotelling steps "
+                                               "on the 6.6 A range"),
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": launches,

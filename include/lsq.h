@@ -295,6 +295,20 @@ int lsq_lnv_energy_gradient(lsq_lnv ctx, const double *L_dev, const double *S_de
                             double *omega_host, double *ne_host, double *G_dev, void *stream);
 
 /*
+ * Sets the metric of lsq_lnv_minimise's conjugate gradients (Sec. 2.3.2:
+ * an approximate sparse inverse overlap, e.g. from lsq_hotelling_inverse,
+ * is the metric of the minimisation).  With a metric X the search
+ * directions come from P = (X G X) on L's range instead of the gradient G,
+ * and Polak-Ribiere takes beta = <G, P - P_prev> / <G_prev, P_prev>; the
+ * line search is unchanged.  X_dev: float64 blocks on range_x, symmetric;
+ * the context keeps its own copy.  range_xg: pattern for X G, covering
+ * R_X + R_L (else LSQ_ERR_INVALID_ARG).  X_dev = NULL removes the metric.
+ * The batched minimiser does not take a metric (LSQ_ERR_UNSUPPORTED while
+ * one is set).  Allocates; synchronises stream.
+ */
+int lsq_lnv_set_metric(lsq_lnv ctx, int range_x, const double *X_dev, int range_xg, void *stream);
+
+/*
  * Conjugate-gradient minimisation of Omega over symmetric L on L's range:
  * Polak-Ribiere direction (beta = max(0, beta_PR)) restarted every
  * cg_reset steps, exact line minimisation of the cubic Omega(L + a D).

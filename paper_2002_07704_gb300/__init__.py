@@ -85,6 +85,7 @@ def load():
         "lsq_lnv_energy_gradient": (I, [P, P, P, P, D, D, I, P, P, P, P]),
         "lsq_lnv_minimise": (I, [P, P, P, P, D, P, P, P]),
         "lsq_lnv_minimise_batch": (I, [P, P, P, P, P, P, P, P]),
+        "lsq_lnv_set_metric": (I, [P, I, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -102,7 +103,7 @@ def exported_symbols():
             "lsq_trace_static", "lsq_hotelling_inverse",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
-            "lsq_lnv_minimise_batch"]
+            "lsq_lnv_minimise_batch", "lsq_lnv_set_metric"]
 
 
 def launch_count():
@@ -327,6 +328,12 @@ class Lnv:
         if rc != 0 and (raise_on_status or rc not in (5, 6)):
             _check(rc)
         return rep.as_dict()
+
+    def set_metric(self, X, range_x, range_xg, stream=None):
+        """CG metric X ~ S^-1 (float64 blocks on range_x; None removes it)."""
+        import torch
+        ptr = None if X is None else _dev(X, torch.float64)
+        _check(_lib.lsq_lnv_set_metric(self.handle, int(range_x), ptr, int(range_xg), _stream(stream)))
 
     def minimise_batch(self, L, S, H, mu, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
                        precision=F64, refine_iter=2, spin=2.0, graph=True, stream=None,

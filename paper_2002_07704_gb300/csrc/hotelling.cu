@@ -64,21 +64,6 @@ __global__ void k_scaled_start(int64_t nnzb, int bb, const int64_t *__restrict__
     }
 }
 
-// Diagonal blocks of a symmetric result computed as upper triangle + mirror: the lower element
-// of each pair inside a diagonal block takes the upper one, so the whole matrix is symmetric to
-// the last bit (the product computes both elements of such a pair separately).
-template <typename T>
-__global__ void k_sym_diag_blocks(int64_t nnzb, int b, const int64_t *__restrict__ tm, T *__restrict__ U) {
-    const int bb = b * b;
-    const int64_t m = nnzb * bb;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = e / bb;
-        if (tm[p] != p) continue;
-        const int rc = (int)(e - p * bb), r = rc / b, c = rc - r * b;
-        if (r > c) U[e] = U[p * bb + c * b + r];
-    }
-}
-
 __global__ void k_f64_to_f32(int64_t m, const double *__restrict__ x, float *__restrict__ y) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
         y[e] = (float)x[e];
@@ -189,12 +174,7 @@ extern "C" int lsq_hotelling_inverse(lsq_geom g, int b, int precision, int range
                              nullptr, s, 1));
         // U exactly symmetric keeps X exactly symmetric.  (The second product reads X as X^T;
         // an antisymmetric part of X would double at every step.)
-        LSQ_TRY(ensure_tmap(g, range_x, s));
-        note_launch();
-        if (precision == LSQ_F64)
-            k_sym_diag_blocks<double><<<grid_of(mx), 256, 0, s>>>(PX.nnzb, b, PX.tmap.p, (double *)U.p);
-        else
-            k_sym_diag_blocks<float><<<grid_of(mx), 256, 0, s>>>(PX.nnzb, b, PX.tmap.p, (float *)U.p);
+        LSQ_TRY(sym_diag_on(g, range_x, b, precision, U.p, s));
         note_launch();
         if (precision == LSQ_F64)
             k_hot_update<double><<<kHotBlocks, kHotThreads, 0, s>>>(mx, (const double *)U.p, X, red.p);

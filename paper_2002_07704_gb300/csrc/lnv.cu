@@ -47,6 +47,11 @@ __global__ void k_to_f32(int64_t m, const double *__restrict__ x, float *__restr
         y[e] = (float)x[e];
 }
 
+__global__ void k_f32_to_f64(int64_t m, const float *__restrict__ x, double *__restrict__ y) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = (double)x[e];
+}
+
 // H' = H - mu S_H and S_H (S placed on H's pattern; zero where S has no block).
 __global__ void k_hprime(int64_t nnzb, int bb, const double *__restrict__ H,
                          const double *__restrict__ S, const int64_t *__restrict__ pos_s, double mu,
@@ -414,6 +419,10 @@ struct lsq_lnv_s {
     // product buffers, sized for float64 and reused for float32
     DevBuf<char> LS, SL, LSL, Q, QT, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
     DevBuf<double> om_rows;  // per-row energy terms formed with the gradient (2 x n)
+    // metric of the CG (lsq_lnv_set_metric): X ~ S^-1 on range rX, X G on range rXG
+    int rX = -1, rXG = -1;
+    DevBuf<double> Xm, Pm, Pmp;   // X (float64), P = X G X and the previous P
+    DevBuf<char> Xmc, XG, Pc;     // float32 copy of X, X G, P in the working precision
     const int64_t *pos_s_in_h = nullptr;
     // batched minimisation state (allocated by the first batch call)
     int b_nsys = 0;
@@ -811,6 +820,76 @@ extern "C" int lsq_lnv_energy_gradient(lsq_lnv c, const double *L, const double 
     return LSQ_OK;
 }
 
+extern "C" int lsq_lnv_set_metric(lsq_lnv c, int range_x, const double *X, int range_xg, void *stream) {
+    clear_error();
+    if (!c) return set_error(LSQ_ERR_INVALID_ARG, "null context");
+    lsq_geom g = c->g;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!X) {
+        c->rX = c->rXG = -1;
+        c->Xm.release();
+        c->Pm.release();
+        c->Pmp.release();
+        c->Xmc.release();
+        c->XG.release();
+        c->Pc.release();
+        return LSQ_OK;
+    }
+    LSQ_TRY(geom_check(g, range_x));
+    LSQ_TRY(geom_check(g, range_xg));
+    if (g->pats[range_xg].R < g->pats[range_x].R + g->pats[c->rL].R - 1e-9)
+        return set_error(LSQ_ERR_INVALID_ARG, "range_xg must cover the natural range R_X + R_L of X G");
+    const int bb = c->b * c->b;
+    const int64_t nx = g->pats[range_x].nnzb * bb, nxg = g->pats[range_xg].nnzb * bb, nl = nvals(c, c->rL);
+    LSQ_TRY(c->Xm.alloc((size_t)std::max<int64_t>(nx, 1)));
+    LSQ_TRY(c->Pm.alloc((size_t)std::max<int64_t>(nl, 1)));
+    LSQ_TRY(c->Pmp.alloc((size_t)std::max<int64_t>(nl, 1)));
+    LSQ_TRY(c->Xmc.alloc(4 * (size_t)std::max<int64_t>(nx, 1)));
+    LSQ_TRY(c->XG.alloc(8 * (size_t)std::max<int64_t>(nxg, 1)));
+    LSQ_TRY(c->Pc.alloc(8 * (size_t)std::max<int64_t>(nl, 1)));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(c->Xm.p, X, sizeof(double) * nx, cudaMemcpyDeviceToDevice, s));
+    if (nx > 0) {
+        note_launch();
+        k_to_f32<<<grid_for(nx), 256, 0, s>>>(nx, c->Xm.p, (float *)c->Xmc.p);
+        LSQ_CHECK_LAUNCH();
+    }
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    c->rX = range_x;
+    c->rXG = range_xg;
+    return LSQ_OK;
+}
+
+namespace {
+
+// P = (X G X) on L's range, symmetric to the last bit, in float64 (into c->Pm): the gradient
+// in the metric X.  G and X are symmetric, so both products read their second factor as rows.
+int metric_apply(lsq_lnv c, int prec, const double *G, cudaStream_t s) {
+    lsq_geom g = c->g;
+    const int b = c->b;
+    const int64_t nl = nvals(c, c->rL);
+    const void *Gop = G, *Xop = c->Xm.p;
+    if (prec == LSQ_F32) {
+        note_launch();
+        k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, G, (float *)c->Dc.p);  // D's float32 copy is free here
+        LSQ_CHECK_LAUNCH();
+        Gop = c->Dc.p;
+        Xop = c->Xmc.p;
+    }
+    LSQ_TRY(block_matmul(g, b, prec, c->rX, 0, Xop, c->rL, 1, Gop, c->rXG, c->XG.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, prec, c->rXG, 0, c->XG.p, c->rX, 1, Xop, c->rL, c->Pc.p, 1.0, 0.0, nullptr, s, 1));
+    LSQ_TRY(sym_diag_on(g, c->rL, b, prec, c->Pc.p, s));
+    if (prec == LSQ_F64) {
+        LSQ_CUDA_TRY(cudaMemcpyAsync(c->Pm.p, c->Pc.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+    } else {
+        note_launch();
+        k_f32_to_f64<<<grid_for(nl), 256, 0, s>>>(nl, (const float *)c->Pc.p, c->Pm.p);
+        LSQ_CHECK_LAUNCH();
+    }
+    return LSQ_OK;
+}
+
+}  // namespace
+
 extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const double *H, double mu,
                                 const lsq_lnv_opts *opts, lsq_lnv_report *rep, void *stream) {
     clear_error();
@@ -829,6 +908,7 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
     LSQ_TRY(prepare_hs(c, S, H, mu, LSQ_F64, s));
     if (o.precision == LSQ_F32) LSQ_TRY(prepare_hs(c, S, H, mu, LSQ_F32, s));
     LSQ_CUDA_TRY(cudaMemsetAsync(c->Gp.p, 0, sizeof(double) * nl, s));
+    if (c->rX >= 0) LSQ_CUDA_TRY(cudaMemsetAsync(c->Pmp.p, 0, sizeof(double) * nl, s));
     // Phase 0: the requested precision for max_iter steps (or until converged);
     // phase 1 (mixed path only): refine_iter float64 steps from a fresh direction.
     int status = (o.tol_ha_per_atom > 0.0) ? LSQ_ERR_NOT_CONVERGED : LSQ_OK;
@@ -836,6 +916,7 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
     double last_d = 0.0;
     const int nphase = o.precision == LSQ_F32 ? 2 : 1;
     double om_pred = 0.0, ne_last = std::nan("");
+    bool converged0 = false;  // the first phase reached tol
     for (int phase = 0; phase < nphase && status != LSQ_ERR_UNSTABLE; ++phase) {
         const int prec = phase == 0 ? o.precision : LSQ_F64;
         const int budget = phase == 0 ? o.max_iter : o.refine_iter;
@@ -847,8 +928,13 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
             // (and at every CG restart and phase start), which saves one R3 product per step.
             const bool reuse_q = it % std::min(o.cg_reset, kQFresh) != 0;
             LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, c->G.p, nullptr, nullptr, s, false, false, reuse_q));
-            LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
-            LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
+            // search directions from P = X G X in the metric X (lsq_lnv_set_metric), else from G;
+            // Polak-Ribiere with beta = <G, P - P_prev> / <G_prev, P_prev>
+            const bool metric = c->rX >= 0;
+            if (metric) LSQ_TRY(metric_apply(c, prec, c->G.p, s));
+            const double *Pdir = metric ? c->Pm.p : c->G.p;
+            LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, Pdir, 10, s));
+            LSQ_TRY(dot_into(c->g, c->b, LSQ_F64, c->rL, c->G.p, metric ? c->Pmp.p : c->Gp.p, 11, s));
             double t[12];
             LSQ_TRY(fetch_scalars(c->g, 12, t, s));
             const double om = o.spin * (3.0 * t[0] - 2.0 * t[1]);
@@ -860,13 +946,13 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
             double beta = 0.0;
             if (it % o.cg_reset != 0 && gg_prev > 0.0) beta = std::max(0.0, (gg - ggp) / gg_prev);
             note_launch();
-            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, c->G.p, c->D.p);
+            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, beta, Pdir, c->D.p);
             LSQ_CHECK_LAUNCH();
             double cc[3];
             LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
             if (cc[0] >= 0.0 && beta != 0.0) {  // not a descent direction: restart
                 note_launch();
-                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, c->G.p, c->D.p);
+                k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, 0.0, Pdir, c->D.p);
                 LSQ_CHECK_LAUNCH();
                 LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
             }
@@ -888,6 +974,7 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
                 k_axpy_f32<<<grid_for(n3), 256, 0, s>>>(n3, a, (const float *)c->QD.p, (float *)c->Q.p);
             LSQ_CHECK_LAUNCH();
             std::swap(c->G.p, c->Gp.p);
+            if (metric) std::swap(c->Pm.p, c->Pmp.p);
             gg_prev = gg;
             ++iters;
             if (prec == LSQ_F64) ++iters64;
@@ -906,9 +993,12 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
             }
         }
         if (status == LSQ_ERR_UNSTABLE) break;
+        if (phase == 0) converged0 = converged;
         if (phase == nphase - 1 && o.tol_ha_per_atom > 0.0) {
-            // converged if the last phase converged, or (mixed path) the FP64 steps stayed below tol
-            if (converged || (nphase == 2 && iters64 > 0 && last_d < o.tol_ha_per_atom))
+            // converged if the last phase converged, or (mixed path) the FP64 steps stayed below
+            // tol, or no FP64 steps were asked for and the mixed ones converged
+            if (converged || (nphase == 2 && iters64 > 0 && last_d < o.tol_ha_per_atom) ||
+                (nphase == 2 && budget == 0 && converged0))
                 status = LSQ_OK;
         }
     }
@@ -1040,6 +1130,8 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
                                       const double *mu_host, const lsq_lnv_opts *opts,
                                       lsq_lnv_report *reps, void *stream) {
     clear_error();
+    if (c && c->rX >= 0)
+        return set_error(LSQ_ERR_UNSUPPORTED, "the batched minimiser has no metric; clear it with a null X");
     if (!c || !L || !S || !H || !mu_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
     lsq_lnv_opts o;
     lsq_lnv_default_opts(&o);

@@ -164,6 +164,8 @@ int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, 
                     bool mirror = true);
 // out = X^T on the (symmetric) pattern r: out_ij = (X_ji)^T.
 int transpose_on(lsq_geom g, int r, int b, int dtype, const void *X, void *out, cudaStream_t s);
+// Makes the diagonal blocks of X (pattern r) symmetric: X_ii[r][c] = X_ii[c][r] for r > c.
+int sym_diag_on(lsq_geom g, int r, int b, int dtype, void *X, cudaStream_t s);
 // out = X + X^T on the (symmetric) pattern r: out_ij = X_ij + (X_ji)^T.
 int sym_sum_on(lsq_geom g, int r, int b, int dtype, const void *X, void *out, cudaStream_t s);
 

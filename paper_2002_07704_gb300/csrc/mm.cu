@@ -413,6 +413,33 @@ int sym_sum_on(lsq_geom g, int r, int b, int prec, const void *X, void *out, cud
     return LSQ_OK;
 }
 
+// Diagonal blocks of a symmetric result formed as upper triangle + mirror: the lower element of
+// each pair inside a diagonal block takes the upper one, so the whole matrix is symmetric to
+// the last bit (the product computes the two elements of such a pair separately).
+template <typename T>
+__global__ void k_sym_diag_blocks(int64_t nnzb, int b, const int64_t *__restrict__ tm, T *__restrict__ U) {
+    const int bb = b * b;
+    const int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / bb;
+        if (tm[p] != p) continue;
+        const int rc = (int)(e - p * bb), r = rc / b, c = rc - r * b;
+        if (r > c) U[e] = U[p * bb + c * b + r];
+    }
+}
+
+int sym_diag_on(lsq_geom g, int r, int b, int prec, void *X, cudaStream_t s) {
+    LSQ_TRY(ensure_tmap(g, r, s));
+    const int64_t m = g->pats[r].nnzb * b * b;
+    note_launch();
+    if (prec == LSQ_F64)
+        k_sym_diag_blocks<double><<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, (double *)X);
+    else
+        k_sym_diag_blocks<float><<<tgrid(m), 256, 0, s>>>(g->pats[r].nnzb, b, g->pats[r].tmap.p, (float *)X);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
 // ---- index-cost estimate of the two forms ---------------------------------
 __global__ void k_mm_cost(int n, const int64_t *__restrict__ a_ptr, const int32_t *__restrict__ a_col,
                           const int64_t *__restrict__ b_ptr, const int64_t *__restrict__ c_ptr,

@@ -293,3 +293,35 @@ def test_lnv_mixed_precision_reaches_float64_minimum():
     # the returned Omega is a float64 evaluation of the returned L
     om_chk, _ = ref.energy(oracle.Bsr(ref.pat_L, 4, Lg.cpu().numpy()))
     assert abs(rep["omega_ev"] - om_chk) <= 1e-10 * abs(om_chk)
+
+
+def test_lnv_metric_cg_matches_oracle_trajectory():
+    """CG in the inverse-overlap metric (lsq_lnv_set_metric): 15 steps against the oracle;
+    the identity metric reproduces plain CG; the batched minimiser refuses a metric."""
+    from oracle import hotelling as OH
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    X, _ = OH.hotelling(ref.sys, Sb, R_S, 30)
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    Lr, _ = OL.minimise(ref, L0, 15, metric=X)
+    r_x, r_xg = g.range_id(R_S), 3          # X on S's range; X G on L + S's range
+    ctx.set_metric(cuda(X.val), r_x, r_xg)
+    Lg = cuda(L0.val)
+    rep = ctx.minimise(Lg, cuda(Sb.val), cuda(Hb.val), MU, max_iter=15)
+    om_ref, _ = ref.energy(Lr)
+    assert rep["iterations"] == 15
+    assert abs(rep["omega_ev"] - om_ref) <= 1e-9 * abs(om_ref)
+    assert rel_err(Lg.cpu().numpy(), Lr.val) <= 1e-7
+    with pytest.raises(lsq.LsqError):
+        ctx.minimise_batch(cuda(L0.val), cuda(Sb.val), cuda(Hb.val), [MU], max_iter=1)
+    # identity blocks as the metric: the plain trajectory
+    pX = ref.sys.pattern(R_S)
+    eye = np.zeros((pX.nnzb, 4, 4))
+    eye[pX.rows() == pX.col] = np.eye(4)
+    ctx.set_metric(cuda(eye), r_x, r_xg)
+    L1 = cuda(L0.val)
+    rep1 = ctx.minimise(L1, cuda(Sb.val), cuda(Hb.val), MU, max_iter=6)
+    ctx.set_metric(None, r_x, r_xg)
+    L2 = cuda(L0.val)
+    rep2 = ctx.minimise(L2, cuda(Sb.val), cuda(Hb.val), MU, max_iter=6)
+    assert abs(rep1["omega_ev"] - rep2["omega_ev"]) <= 1e-12 * abs(rep2["omega_ev"])
+    assert rel_err(L1.cpu().numpy(), L2.cpu().numpy()) <= 1e-12
