@@ -295,6 +295,28 @@ int lsq_lnv_energy_gradient(lsq_lnv ctx, const double *L_dev, const double *S_de
                             double *omega_host, double *ne_host, double *G_dev, void *stream);
 
 /*
+ * Initial L from the Hamiltonian (Sec. 2.3.2: the initial density matrix is
+ * generated from H by an iterative generalisation of the McWeeny transform):
+ * grand-canonical purification at mu with an approximate inverse overlap X:
+ *     K_0 = (lam/2) (mu X - X H X) + X/2,  lam = min(1/(e_max - mu), 1/(mu - e_min)),
+ *     K_{n+1} = 3 K S K - 2 K S K S K,
+ * (the symmetric part of the right side, since K S K is truncated before
+ * the last product), [e_min, e_max] the Gershgorin bounds of X H (its
+ * scalar rows), X H on
+ * range_xh (covering R_X + R_H, else LSQ_ERR_INVALID_ARG; at most as large
+ * as the context's widest range), X H X, K S K and K S K S K on L's range.
+ * K_n is written to L_dev (float64, L's range), the start for
+ * lsq_lnv_minimise.  S_dev on R_S, H_dev on R_H, X_dev on range_x (all
+ * float64, symmetric).  precision: LSQ_F64, or LSQ_F32 for float32 products
+ * in the McWeeny steps.  dk_host (optional, [n_iter]): |K_{n+1} - K_n|_F.
+ * mu outside [e_min, e_max]: LSQ_ERR_INVALID_ARG.  Uses the context's
+ * workspace; synchronises stream.
+ */
+int lsq_lnv_init_purify(lsq_lnv ctx, const double *S_dev, const double *H_dev, double mu, int range_x,
+                        const double *X_dev, int range_xh, int n_iter, int precision, double *L_dev,
+                        double *dk_host, void *stream);
+
+/*
  * Sets the metric of lsq_lnv_minimise's conjugate gradients (Sec. 2.3.2:
  * an approximate sparse inverse overlap, e.g. from lsq_hotelling_inverse,
  * is the metric of the minimisation).  With a metric X the search

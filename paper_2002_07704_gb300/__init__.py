@@ -86,6 +86,7 @@ def load():
         "lsq_lnv_minimise": (I, [P, P, P, P, D, P, P, P]),
         "lsq_lnv_minimise_batch": (I, [P, P, P, P, P, P, P, P]),
         "lsq_lnv_set_metric": (I, [P, I, P, I, P]),
+        "lsq_lnv_init_purify": (I, [P, P, P, D, I, P, I, I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -103,7 +104,7 @@ def exported_symbols():
             "lsq_trace_static", "lsq_hotelling_inverse",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
-            "lsq_lnv_minimise_batch", "lsq_lnv_set_metric"]
+            "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify"]
 
 
 def launch_count():
@@ -328,6 +329,19 @@ class Lnv:
         if rc != 0 and (raise_on_status or rc not in (5, 6)):
             _check(rc)
         return rep.as_dict()
+
+    def init_purify(self, S, H, mu, X, range_x, range_xh, L, n_iter, precision=F64, stream=None):
+        """L = McWeeny purification of the grand-canonical start built from H, S^-1 ~ X and mu.
+
+        Returns |K_{n+1} - K_n|_F per step.  See lsq_lnv_init_purify.
+        """
+        import torch
+        dk = (ctypes.c_double * max(int(n_iter), 1))()
+        f = torch.float64
+        _check(_lib.lsq_lnv_init_purify(self.handle, _dev(S, f), _dev(H, f), float(mu), int(range_x),
+                                        _dev(X, f), int(range_xh), int(n_iter), int(precision),
+                                        _dev(L, f), dk, _stream(stream)))
+        return [dk[k] for k in range(int(n_iter))]
 
     def set_metric(self, X, range_x, range_xg, stream=None):
         """CG metric X ~ S^-1 (float64 blocks on range_x; None removes it)."""

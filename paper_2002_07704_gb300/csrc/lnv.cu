@@ -861,6 +861,192 @@ extern "C" int lsq_lnv_set_metric(lsq_lnv c, int range_x, const double *X, int r
 
 namespace {
 
+// Gershgorin discs of the scalar rows of XH (pattern rp/col): lo = d - r, hi = d + r with d the
+// diagonal element and r the sum of the other absolute values of the row.
+__global__ void k_gersh_rows(int n, int b, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const double *__restrict__ XH, double *__restrict__ lo, double *__restrict__ hi) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * b) return;
+    const int i = (int)(t / b), r = (int)(t - (int64_t)i * b);
+    const int bb = b * b;
+    double a = 0.0, d = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        for (int c = 0; c < b; ++c) a += fabs(XH[p * bb + r * b + c]);
+        if (col[p] == i) d = XH[p * bb + r * b + r];
+    }
+    const double rad = a - fabs(d);
+    lo[t] = d - rad;
+    hi[t] = d + rad;
+}
+
+// out[0] = min of lo, out[1] = max of hi (one block).
+__global__ void k_minmax(int64_t m, const double *__restrict__ lo, const double *__restrict__ hi,
+                         double *__restrict__ out) {
+    __shared__ double a[1024], z[1024];
+    double mn = 1e300, mx = -1e300;
+    for (int64_t k = threadIdx.x; k < m; k += blockDim.x) {
+        mn = fmin(mn, lo[k]);
+        mx = fmax(mx, hi[k]);
+    }
+    a[threadIdx.x] = mn;
+    z[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            a[threadIdx.x] = fmin(a[threadIdx.x], a[threadIdx.x + w]);
+            z[threadIdx.x] = fmax(z[threadIdx.x], z[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = a[0];
+        out[1] = z[0];
+    }
+}
+
+// K_0 = (lam / 2) (mu X - X H X) + X / 2 on L's range (pos: blocks of L's pattern in X's).
+__global__ void k_pm_start(int64_t nnzb, int bb, const int64_t *__restrict__ pos, const double *__restrict__ X,
+                           const double *__restrict__ XHX, double half_lam, double mu, double *__restrict__ K) {
+    const int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / bb;
+        const int rc = (int)(e - p * bb);
+        const double xl = pos[p] >= 0 ? X[pos[p] * bb + rc] : 0.0;
+        K[e] = half_lam * (mu * xl - XHX[e]) + 0.5 * xl;
+    }
+}
+
+// K = 3 B - (C + C^T) (the symmetric part of 3 B - 2 C; C = (K S)(K S K) is not symmetric once
+// K S K is truncated) with per-block partial sums of the change squared; tm: L's transpose map.
+template <typename T>
+__global__ void k_pm_update(int64_t nnzb, int b, const int64_t *__restrict__ tm, const T *__restrict__ B,
+                            const T *__restrict__ C, double *__restrict__ K, double *__restrict__ partial) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    const int bb = b * b;
+    const int64_t m = nnzb * bb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / bb;
+        const int rc = (int)(e - p * bb), r = rc / b, c = rc - r * b;
+        const double kn = 3.0 * (double)B[e] - ((double)C[e] + (double)C[tm[p] * bb + c * b + r]);
+        const double d = kn - K[e];
+        K[e] = kn;
+        acc = fma(d, d, acc);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partial(int m, const double *__restrict__ partial, double *__restrict__ out) {
+    __shared__ double sh[1024];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) acc += partial[k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sqrt(sh[0]);
+}
+
+}  // namespace
+
+extern "C" int lsq_lnv_init_purify(lsq_lnv c, const double *S, const double *H, double mu, int range_x,
+                                   const double *X, int range_xh, int n_iter, int precision, double *L,
+                                   double *dk_host, void *stream) {
+    clear_error();
+    if (!c || !S || !H || !X || !L) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    lsq_geom g = c->g;
+    LSQ_TRY(geom_check(g, range_x));
+    LSQ_TRY(geom_check(g, range_xh));
+    if (precision != LSQ_F64 && precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    if (n_iter < 0) return set_error(LSQ_ERR_INVALID_ARG, "n_iter must be >= 0");
+    if (g->pats[range_xh].R < g->pats[range_x].R + g->pats[c->rH].R - 1e-9)
+        return set_error(LSQ_ERR_INVALID_ARG, "range_xh must cover the natural range R_X + R_H of X H");
+    if (g->pats[range_xh].nnzb > g->pats[c->r3].nnzb)
+        return set_error(LSQ_ERR_UNSUPPORTED, "range_xh is larger than the workspace's widest range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int b = c->b, bb = b * b;
+    const int n = g->n;
+    const int64_t nl = nvals(c, c->rL);
+    if (n == 0) return LSQ_OK;
+    // X H (the workspace's Q storage), its Gershgorin bounds, X H X on L's range (G1 storage)
+    double *XH = reinterpret_cast<double *>(c->Q.p), *XHX = reinterpret_cast<double *>(c->G1.p);
+    LSQ_TRY(block_matmul(g, b, LSQ_F64, range_x, 0, X, c->rH, 1, H, range_xh, XH, 1.0, 0.0, nullptr, s));
+    DevBuf<double> lohi, red;
+    LSQ_TRY(lohi.alloc((size_t)2 * n * b));
+    LSQ_TRY(red.alloc(1024 + 4));
+    note_launch();
+    k_gersh_rows<<<(int)(((int64_t)n * b + 255) / 256), 256, 0, s>>>(n, b, g->pats[range_xh].row_ptr.p,
+                                                                      g->pats[range_xh].col.p, XH, lohi.p,
+                                                                      lohi.p + (int64_t)n * b);
+    note_launch();
+    k_minmax<<<1, 1024, 0, s>>>((int64_t)n * b, lohi.p, lohi.p + (int64_t)n * b, red.p + 1024);
+    LSQ_CHECK_LAUNCH();
+    double eb[2];
+    LSQ_CUDA_TRY(cudaMemcpyAsync(eb, red.p + 1024, sizeof(eb), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!(eb[1] > mu && mu > eb[0]))
+        return set_error(LSQ_ERR_INVALID_ARG, "mu lies outside the spectral bounds of X H");
+    const double lam = std::min(1.0 / (eb[1] - mu), 1.0 / (mu - eb[0]));
+    LSQ_TRY(block_matmul(g, b, LSQ_F64, range_xh, 0, XH, range_x, 1, X, c->rL, XHX, 1.0, 0.0, nullptr, s, 1));
+    LSQ_TRY(sym_diag_on(g, c->rL, b, LSQ_F64, XHX, s));
+    const int64_t *pos = nullptr;
+    LSQ_TRY(get_posmap(g, c->rL, range_x, 0, &pos, s));
+    note_launch();
+    k_pm_start<<<grid_for(nl), 256, 0, s>>>(g->pats[c->rL].nnzb, bb, pos, X, XHX, 0.5 * lam, mu, L);
+    LSQ_CHECK_LAUNCH();
+    // McWeeny steps: K S at its natural range (LS storage), (K S) K and (K S)(K S K) on L's range
+    const void *Sop = S, *Kop = L;
+    if (precision == LSQ_F32) {
+        const int64_t ns = nvals(c, c->rS);
+        note_launch();
+        k_to_f32<<<grid_for(ns), 256, 0, s>>>(ns, S, (float *)c->Sc.p);
+        LSQ_CHECK_LAUNCH();
+        Sop = c->Sc.p;
+        Kop = c->Lc.p;
+    }
+    void *KS = c->LS.p, *Bm = c->G1.p, *Cm = c->G2.p;
+    for (int it = 0; it < n_iter; ++it) {
+        if (precision == LSQ_F32) {
+            note_launch();
+            k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p);
+            LSQ_CHECK_LAUNCH();
+        }
+        LSQ_TRY(block_matmul(g, b, precision, c->rL, 0, Kop, c->rS, 1, Sop, c->r1, KS, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, precision, c->r1, 0, KS, c->rL, 1, Kop, c->rL, Bm, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(sym_diag_on(g, c->rL, b, precision, Bm, s));
+        // (K S)(K S K) on every block (truncated K S K makes it unsymmetric); the second factor
+        // read as rows of its transpose, which it equals
+        LSQ_TRY(block_matmul(g, b, precision, c->r1, 0, KS, c->rL, 1, Bm, c->rL, Cm, 1.0, 0.0, nullptr, s));
+        const int64_t *tmL = g->pats[c->rL].tmap.p;
+        note_launch();
+        if (precision == LSQ_F64)
+            k_pm_update<double><<<1024, 256, 0, s>>>(g->pats[c->rL].nnzb, b, tmL, (const double *)Bm,
+                                                     (const double *)Cm, L, red.p);
+        else
+            k_pm_update<float><<<1024, 256, 0, s>>>(g->pats[c->rL].nnzb, b, tmL, (const float *)Bm,
+                                                    (const float *)Cm, L, red.p);
+        note_launch();
+        k_sum_partial<<<1, 1024, 0, s>>>(1024, red.p, red.p + 1026);
+        LSQ_CHECK_LAUNCH();
+        if (dk_host) {
+            LSQ_CUDA_TRY(cudaMemcpyAsync(dk_host + it, red.p + 1026, sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+    }
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    return LSQ_OK;
+}
+
+namespace {
+
 // P = (X G X) on L's range, symmetric to the last bit, in float64 (into c->Pm): the gradient
 // in the metric X.  G and X are symmetric, so both products read their second factor as rows.
 int metric_apply(lsq_lnv c, int prec, const double *G, cudaStream_t s) {

@@ -325,3 +325,27 @@ def test_lnv_metric_cg_matches_oracle_trajectory():
     rep2 = ctx.minimise(L2, cuda(Sb.val), cuda(Hb.val), MU, max_iter=6)
     assert abs(rep1["omega_ev"] - rep2["omega_ev"]) <= 1e-12 * abs(rep2["omega_ev"])
     assert rel_err(L1.cpu().numpy(), L2.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,n_iter", [(lsq.F64, 20), (lsq.F32, 12)])
+def test_lnv_purified_start_matches_oracle(prec, n_iter):
+    """lsq_lnv_init_purify: the McWeeny-purified start from H against the oracle (64 atoms,
+    L range 8 A, X from 30 Hotelling steps on S's range)."""
+    from oracle import hotelling as OH
+    from oracle import purify as OP
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    X, _ = OH.hotelling(ref.sys, Sb, R_S, 30)
+    Kr, hr, _ = OP.purify(ref.sys, Sb, Hb, X, MU, 8.0, n_iter)
+    L = torch.zeros((g.nnzb(2), 4, 4), dtype=torch.float64, device="cuda")
+    dk = ctx.init_purify(cuda(Sb.val), cuda(Hb.val), MU, cuda(X.val), g.range_id(R_S), 3, L, n_iter,
+                         precision=prec)
+    tol = 1e-10 if prec == lsq.F64 else 1e-4
+    assert rel_err(L.cpu().numpy(), Kr.val) <= tol
+    if prec == lsq.F64:
+        for a, r in zip(dk, hr):
+            assert abs(a - r) <= 1e-8 * r + 1e-12
+    # the purified start is a better start: lower Omega than the on-site one
+    L0 = cuda(OL.onsite_inverse_half(Sb, ref.pat_L).val)
+    om_p, _ = ctx.energy_gradient(L, cuda(Sb.val), cuda(Hb.val), MU)
+    om_0, _ = ctx.energy_gradient(L0, cuda(Sb.val), cuda(Hb.val), MU)
+    assert om_p < om_0
