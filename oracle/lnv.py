@@ -241,3 +241,62 @@ def minimise(lnv, L0, n_iter, reset=40, tol_ha_per_atom=None, metric=None):
         if tol_ha_per_atom is not None and abs(om_next - om) / HA_EV / n < tol_ha_per_atom:
             break
     return L, hist
+
+
+def minimise_canonical(lnv_e, lnv_n, L0, n_electrons, n_iter, reset=40, tol_ha_per_atom=None,
+                       tol_ne=1e-9, max_correct=5):
+    """CG on E_band = 2 Tr[K H] at fixed electron number N_e = 2 Tr[K S] (canonical LNV).
+
+    Sec. 2.3.2: during the optimisation the electron number is constrained
+    (the paper cites Hernandez, Gillan and Goringe for it).  Reading taken
+    here: lnv_e is an Lnv with mu = 0 (so its Omega is E_band and its second
+    value N_e), lnv_n the same with H replaced by S (its gradient is
+    dN_e/dL).  Each step first restores N_e by moves L += d G_N along the
+    electron-number gradient, d = (N0 - N_e) / <G_N, G_N> (Newton on the
+    linearisation, at most max_correct moves, until |N_e - N0| <= tol_ne N0);
+    then the energy gradient is projected on constant N_e,
+    G = G_E - lam G_N with lam = <G_E, G_N> / <G_N, G_N> (the Lagrange
+    multiplier, i.e. the chemical potential), Polak-Ribiere directions are
+    built from G and projected again, and the step is the exact cubic line
+    minimum of E_band.  Returns (L, history) with E_band, N_e, lam, alpha,
+    beta per step.
+    """
+    L = L0.copy()
+    D = Gp = None
+    hist = []
+    n = lnv_e.sys.n
+    for it in range(n_iter):
+        for c in range(max_correct + 1):
+            E, N = lnv_e.energy(L)
+            GN = lnv_n.gradient(L)
+            GN = 0.5 * (GN + transpose(GN, GN.pat))
+            gnn = dot(GN, GN)
+            if abs(N - n_electrons) <= tol_ne * abs(n_electrons) or c == max_correct:
+                break
+            L = L + ((n_electrons - N) / gnn) * GN
+        GE = lnv_e.gradient(L)
+        GE = 0.5 * (GE + transpose(GE, GE.pat))
+        lam = dot(GE, GN) / gnn
+        G = GE - lam * GN
+        beta = 0.0
+        if D is None or it % reset == 0:
+            D = -1.0 * G
+        else:
+            beta = max(0.0, dot(G, G - Gp) / dot(Gp, Gp))
+            D = -1.0 * G + beta * D
+        D = D - (dot(D, GN) / gnn) * GN
+        c1, c2, c3 = lnv_e.cubic(L, D, GE)
+        if c1 >= 0.0:
+            D = -1.0 * G
+            beta = 0.0
+            c1, c2, c3 = lnv_e.cubic(L, D, GE)
+        a = line_minimum(c1, c2, c3)
+        if a is None:
+            raise FloatingPointError("no local minimum along the search direction")
+        L = L + a * D
+        e_next = E + c1 * a + c2 * a * a + c3 * a * a * a
+        hist.append(dict(energy=E, ne=N, lam=lam, energy_next=e_next, alpha=a, beta=beta))
+        Gp = G
+        if tol_ha_per_atom is not None and abs(e_next - E) / HA_EV / n < tol_ha_per_atom:
+            break
+    return L, hist
