@@ -398,6 +398,22 @@ def run_ours(args):
                                    "status": int(rt["status"])}
     ctx.set_metric(None, 0, 3)
 
+    # --- canonical LNV: CG steps at fixed N_e (N0 from the grand-canonical iterate L) ---
+    _, n0 = ctx.energy_gradient(L, Sd, Hd, MU)
+    Lc = L.clone()
+    ctx.minimise_canonical(Lc, Sd, Hd, n0, max_iter=2, precision=lsq.F32)   # warm-up
+    Lc = L.clone()
+    barrier()
+    e0.record(stream)
+    rc_, lam_ = ctx.minimise_canonical(Lc, Sd, Hd, n0, max_iter=args.steps, precision=lsq.F32)
+    e1.record(stream)
+    barrier()
+    canon = {"steps_per_s": 1000.0 * int(rc_["iterations"]) / e0.elapsed_time(e1),
+             "ms_per_step": e0.elapsed_time(e1) / max(int(rc_["iterations"]), 1),
+             "steps": int(rc_["iterations"]), "n_electrons": n0,
+             "ne_error_rel": abs(rc_["ne"] - n0) / n0, "lambda_ev": lam_,
+             "workload": "mixed precision, N_e fixed at its value at the grand-canonical iterate"}
+
     # --- end to end through the public API, host buffers ---
     Lh = L0.cpu().pin_memory()
     Sh = Sd.cpu().pin_memory()
@@ -456,6 +472,7 @@ def run_ours(args):
                          "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"},
             "hotelling": dict(hot, workload="X = S^-1 approximated on the 10 A range by "
                                              "X <- 2X - (X S) X from X0 = S / s^2, the LNV metric of Sec. 2.3.2"),
+            "canonical": canon,
             "metric_cg": dict(mcg, workload="mixed-precision CG from L0 until |dOmega|/N < tol; "
                                                "metric: X from 12 float32 + 2 float64 Hotelling steps "
                                                "on the 6.6 A range"),

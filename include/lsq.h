@@ -295,6 +295,25 @@ int lsq_lnv_energy_gradient(lsq_lnv ctx, const double *L_dev, const double *S_de
                             double *omega_host, double *ne_host, double *G_dev, void *stream);
 
 /*
+ * Canonical LNV: minimises E_band = 2 Tr[K H] at fixed electron number
+ * N_e = 2 Tr[K S] = n_electrons (Sec. 2.3.2: the electron number is
+ * constrained during the optimisation).  Each CG step first restores N_e
+ * by Newton moves along dN_e/dL (at most 5, to 1e-9 relative in FP64, 1e-6
+ * with FP32 products), projects the energy gradient on constant N_e (its
+ * multiplier lambda, the chemical potential, goes to *lambda_out), builds
+ * Polak-Ribiere directions from the projected gradient, projects them
+ * again and takes the exact cubic minimum of E_band.  opts as for
+ * lsq_lnv_minimise, with precision applying to every step (no separate
+ * FP64 refinement) and refine_iter, final_eval and graph ignored; the
+ * report's omega_ev is E_band and ne the last N_e measured.  Near exact
+ * idempotency dN_e/dL vanishes and the constraint cannot be held: the call
+ * then returns LSQ_ERR_UNSTABLE.  No metric may be set (LSQ_ERR_UNSUPPORTED).
+ */
+int lsq_lnv_minimise_canonical(lsq_lnv ctx, double *L_dev, const double *S_dev, const double *H_dev,
+                               double n_electrons, const lsq_lnv_opts *opts, lsq_lnv_report *report_host,
+                               double *lambda_out, void *stream);
+
+/*
  * Initial L from the Hamiltonian (Sec. 2.3.2: the initial density matrix is
  * generated from H by an iterative generalisation of the McWeeny transform):
  * grand-canonical purification at mu with an approximate inverse overlap X:

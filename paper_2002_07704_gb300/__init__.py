@@ -87,6 +87,7 @@ def load():
         "lsq_lnv_minimise_batch": (I, [P, P, P, P, P, P, P, P]),
         "lsq_lnv_set_metric": (I, [P, I, P, I, P]),
         "lsq_lnv_init_purify": (I, [P, P, P, D, I, P, I, I, I, P, P, P]),
+        "lsq_lnv_minimise_canonical": (I, [P, P, P, P, D, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -104,7 +105,8 @@ def exported_symbols():
             "lsq_trace_static", "lsq_hotelling_inverse",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
-            "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify"]
+            "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
+            "lsq_lnv_minimise_canonical"]
 
 
 def launch_count():
@@ -329,6 +331,21 @@ class Lnv:
         if rc != 0 and (raise_on_status or rc not in (5, 6)):
             _check(rc)
         return rep.as_dict()
+
+    def minimise_canonical(self, L, S, H, n_electrons, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
+                           precision=F64, spin=2.0, verbose=False, stream=None, raise_on_status=False):
+        """Minimises E_band at fixed N_e (in place in L).  Returns (report dict, lambda = mu)."""
+        import torch
+        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, 0, spin, 0, int(bool(verbose)), 0)
+        rep = LnvReport()
+        lam = ctypes.c_double()
+        f = torch.float64
+        rc = _lib.lsq_lnv_minimise_canonical(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),
+                                             float(n_electrons), ctypes.byref(o), ctypes.byref(rep),
+                                             ctypes.byref(lam), _stream(stream))
+        if rc != 0 and (raise_on_status or rc not in (5, 6)):
+            _check(rc)
+        return rep.as_dict(), lam.value
 
     def init_purify(self, S, H, mu, X, range_x, range_xh, L, n_iter, precision=F64, stream=None):
         """L = McWeeny purification of the grand-canonical start built from H, S^-1 ~ X and mu.

@@ -629,12 +629,15 @@ int seg_trace(lsq_lnv c, int prec, int rx, const void *X, int ry, const void *Y,
 // Omega, N_e (scalars slots 0..3 hold the four traces) and, if G != null, the gradient.
 // seg: per-system sums into the batch slots, nothing fetched (omega, ne ignored).
 // reuse_q: c->Q already holds H'LS for this L (updated along the line search), skip its product.
+// s_as_h: S (on H's range) takes the place of H' everywhere, so that "Omega" is N_e and G is
+// dN_e/dL (the canonical minimiser's electron-number gradient).
 int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *G,
                     double *omega, double *ne, cudaStream_t s, bool seg = false, bool want_ne = false,
-                    bool reuse_q = false) {
+                    bool reuse_q = false, bool s_as_h = false) {
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
+    if (s_as_h) o.Hp = o.Sh;
     // scalar slots: 0 = Tr[H' LSL], 1 = Tr[LSLSL H'] (= <LSL, Q>), 2 = Tr[S LSL], 3 = <LSL, SLS>.
     // With the gradient, slots 0 and 1 come from <L, Q> and <L, M> / 3 (see the header) and LSL
     // is formed only for N_e.
@@ -1200,6 +1203,131 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
         rep->omega_ha_per_atom = om / kHartreeEv / std::max(n, 1);
         rep->last_domega_ha_per_atom = last_d;
         rep->seconds = std::chrono::duration<double>(t1 - t0).count();
+    }
+    if (status == LSQ_ERR_UNSTABLE) return set_error(status, "no local minimum along the CG direction");
+    if (status == LSQ_ERR_NOT_CONVERGED) return set_error(status, "iteration limit reached");
+    return LSQ_OK;
+}
+
+extern "C" int lsq_lnv_minimise_canonical(lsq_lnv c, double *L, const double *S, const double *H,
+                                          double n_electrons, const lsq_lnv_opts *opts, lsq_lnv_report *rep,
+                                          double *lambda_out, void *stream) {
+    clear_error();
+    if (!c || !L || !S || !H) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    lsq_lnv_opts o;
+    lsq_lnv_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != LSQ_F64 && o.precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    if (o.max_iter < 0 || o.cg_reset < 1) return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
+    if (!(n_electrons > 0.0)) return set_error(LSQ_ERR_INVALID_ARG, "n_electrons must be positive");
+    if (c->rX >= 0) return set_error(LSQ_ERR_UNSUPPORTED, "the canonical minimiser has no metric; clear it");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    lsq_geom g = c->g;
+    const int n = g->n, b = c->b;
+    const int64_t nl = nvals(c, c->rL);
+    const int prec = o.precision;
+    const double tol_ne = (prec == LSQ_F64 ? 1e-9 : 1e-6) * n_electrons;
+    const int max_correct = 5;
+    // mu = 0: H' = H, so the grand potential of energy_gradient is E_band
+    LSQ_TRY(prepare_hs(c, S, H, 0.0, LSQ_F64, s));
+    if (prec == LSQ_F32) LSQ_TRY(prepare_hs(c, S, H, 0.0, LSQ_F32, s));
+    DevBuf<double> GN;
+    LSQ_TRY(GN.alloc((size_t)std::max<int64_t>(nl, 1)));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->Gp.p, 0, sizeof(double) * nl, s));
+    int status = o.tol_ha_per_atom > 0.0 ? LSQ_ERR_NOT_CONVERGED : LSQ_OK;
+    int iters = 0;
+    double gg_prev = 0.0, E = 0.0, N = 0.0, lam = 0.0, last_d = 0.0;
+    auto dot2 = [&](const double *x, const double *y, const double *u, const double *v, double *out) {
+        LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, x, y, 10, s));
+        LSQ_TRY(dot_into(g, b, LSQ_F64, c->rL, u, v, 11, s));
+        double t[12];
+        LSQ_TRY(fetch_scalars(g, 12, t, s));
+        out[0] = t[10];
+        out[1] = t[11];
+        return LSQ_OK;
+    };
+    for (int it = 0; it < o.max_iter; ++it) {
+        // restore N_e along dN_e/dL
+        double gnn = 0.0;
+        for (int corr = 0;; ++corr) {
+            LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, GN.p, &N, nullptr, s, false, false, false, true));
+            double t2[2];
+            LSQ_TRY(dot2(GN.p, GN.p, GN.p, GN.p, t2));
+            gnn = t2[0];
+            if (!(gnn > 0.0)) return set_error(LSQ_ERR_UNSTABLE, "the electron-number gradient vanished");
+            if (std::fabs(N - n_electrons) <= tol_ne || corr == max_correct) break;
+            note_launch();
+            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, (n_electrons - N) / gnn, GN.p, L);
+            LSQ_CHECK_LAUNCH();
+        }
+        // energy gradient, projected on constant N_e; lam is the chemical potential
+        LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, c->G.p, &E, nullptr, s));
+        double t2[2];
+        LSQ_TRY(dot2(c->G.p, GN.p, c->G.p, c->Gp.p, t2));
+        lam = t2[0] / gnn;
+        note_launch();
+        k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, -lam, GN.p, c->G.p);
+        LSQ_CHECK_LAUNCH();
+        LSQ_TRY(dot2(c->G.p, c->G.p, c->G.p, c->Gp.p, t2));
+        const double gg = t2[0], ggp = t2[1];
+        if (gg == 0.0) {
+            status = LSQ_OK;
+            break;
+        }
+        double beta = 0.0;
+        if (it % o.cg_reset != 0 && gg_prev > 0.0) beta = std::max(0.0, (gg - ggp) / gg_prev);
+        auto direction = [&](double bt) {
+            note_launch();
+            k_cg_dir<<<grid_for(nl), 256, 0, s>>>(nl, bt, c->G.p, c->D.p);
+            LSQ_CHECK_LAUNCH();
+            double d2[2];
+            LSQ_TRY(dot2(c->D.p, GN.p, c->D.p, GN.p, d2));
+            note_launch();
+            k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, -d2[0] / gnn, GN.p, c->D.p);
+            LSQ_CHECK_LAUNCH();
+            return LSQ_OK;
+        };
+        LSQ_TRY(direction(beta));
+        double cc[3];
+        LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
+        if (cc[0] >= 0.0 && beta != 0.0) {
+            LSQ_TRY(direction(0.0));
+            LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, cc, s));
+        }
+        double a = 0.0;
+        if (!(cc[0] < 0.0) || !line_minimum(cc[0], cc[1], cc[2], &a)) {
+            status = LSQ_ERR_UNSTABLE;
+            break;
+        }
+        note_launch();
+        k_axpy<<<grid_for(nl), 256, 0, s>>>(nl, a, c->D.p, L);
+        LSQ_CHECK_LAUNCH();
+        std::swap(c->G.p, c->Gp.p);
+        gg_prev = gg;
+        ++iters;
+        const double de = cc[0] * a + cc[1] * a * a + cc[2] * a * a * a;
+        last_d = std::fabs(de) / kHartreeEv / std::max(n, 1);
+        if (o.verbose)
+            std::fprintf(stderr, "lnv canonical step %d E %.12e eV N_e %.12f lambda %.6f alpha %.6e\n", iters - 1, E,
+                         N, lam, a);
+        if (o.tol_ha_per_atom > 0.0 && last_d < o.tol_ha_per_atom) {
+            status = LSQ_OK;
+            break;
+        }
+    }
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (lambda_out) *lambda_out = lam;
+    if (rep) {
+        rep->iterations = iters;
+        rep->iterations_fp64 = prec == LSQ_F64 ? iters : 0;
+        rep->status = status;
+        rep->omega_ev = E;
+        rep->ne = N;
+        rep->omega_ha_per_atom = E / kHartreeEv / std::max(n, 1);
+        rep->last_domega_ha_per_atom = last_d;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     if (status == LSQ_ERR_UNSTABLE) return set_error(status, "no local minimum along the CG direction");
     if (status == LSQ_ERR_NOT_CONVERGED) return set_error(status, "iteration limit reached");

@@ -349,3 +349,30 @@ def test_lnv_purified_start_matches_oracle(prec, n_iter):
     om_p, _ = ctx.energy_gradient(L, cuda(Sb.val), cuda(Hb.val), MU)
     om_0, _ = ctx.energy_gradient(L0, cuda(Sb.val), cuda(Hb.val), MU)
     assert om_p < om_0
+
+
+@pytest.mark.parametrize("prec", [lsq.F64, lsq.F32])
+def test_lnv_canonical_matches_oracle_trajectory(prec):
+    """Canonical LNV (lsq_lnv_minimise_canonical): 12 steps at N0 = 174 against the oracle."""
+    g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
+    pH = Hb.pat
+    le = OL.Lnv(ref.sys, Sb, Hb, 8.0, 0.0)
+    ln = OL.Lnv(ref.sys, Sb, oracle.restrict(Sb, pH), 8.0, 0.0)
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    n0 = 174.0
+    Lr, hr = OL.minimise_canonical(le, ln, L0, n0, 12)
+    Lg = cuda(L0.val)
+    rep, lam = ctx.minimise_canonical(Lg, cuda(Sb.val), cuda(Hb.val), n0, max_iter=12, precision=prec)
+    assert rep["iterations"] == 12
+    if prec == lsq.F64:
+        assert abs(rep["omega_ev"] - hr[-1]["energy"]) <= 1e-9 * abs(hr[-1]["energy"])
+        assert abs(lam - hr[-1]["lam"]) <= 1e-7 * max(1.0, abs(hr[-1]["lam"]))
+        assert rel_err(Lg.cpu().numpy(), Lr.val) <= 1e-7
+        assert abs(rep["ne"] - n0) <= 1e-8 * n0
+    else:
+        # float32 products: the trajectory stays within float32 accuracy of the oracle's
+        E, N = le.energy(oracle.Bsr(ref.pat_L, 4, Lg.cpu().numpy()))
+        Er, Nr = le.energy(Lr)
+        assert abs(E - Er) <= 1e-4 * abs(Er)
+        assert abs(N - Nr) <= 1e-4 * n0          # the last step's drift, before its correction
+        assert abs(rep["ne"] - n0) <= 1e-5 * n0  # N_e held at the start of the last step
