@@ -11,6 +11,8 @@ public API with host buffers, and the CPU oracle timed on a row sample
 of the same workload are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload batch     # 48 independent systems, 4x4 and 13x13 blocks
+  python bench.py --workload sizes     # ms/step against atoms, 512 ... 32768 (O(N))
 
 With N > 1 (torchrun) every rank runs an independent replica of the
 workload on its own GPU (the path has no exchange step).
@@ -50,7 +52,9 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--cpu-sample-rows", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="si4096", choices=["si4096", "batch"],
+    p.add_argument("--cells", default="4,6,8,10,12,16",
+                   help="--workload sizes: diamond cells per edge of each system (8 n^3 atoms)")
+    p.add_argument("--workload", default="si4096", choices=["si4096", "batch", "sizes"],
                    help="si4096: the 4096-atom headline (default); batch: the 48-system batched "
                         "workload (24 systems with 4x4 blocks, 24 with 13x13)")
     p.add_argument("--only-product", nargs="?", const="sl_qt", choices=["sl_qt", "ls_l"],
@@ -578,12 +582,70 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_sizes(args):
+    """Mixed-precision step time against system size (the O(N) claim of Sec. 2.3.2): the
+    si4096 workload's recipe at n x n x n diamond cells for each n of --cells, one line."""
+    import torch
+    import paper_2002_07704_gb300 as lsq
+    torch.cuda.set_device(0)
+    lsq.build()
+    lsq.load()
+    stream = torch.cuda.current_stream()
+    ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
+    out = []
+    for nc in [int(x) for x in args.cells.split(",")]:
+        pos, cell = diamond_si_positions(nc, SIGMA, config_seed(1))
+        free0, total = torch.cuda.mem_get_info()
+        geom = lsq.Geometry(torch.from_numpy(pos).cuda(), cell, ranges)
+        rp, col = geom.pattern(1)
+        rp, col = rp.cpu().numpy(), col.cpu().numpy()
+        rows = np.repeat(np.arange(geom.n_atoms), np.diff(rp))
+        H, S = sk_blocks(pos, cell, rows, col)
+        Hd, Sd = torch.from_numpy(H).cuda(), torch.from_numpy(S).cuda()
+        ctx = lsq.Lnv(geom, B, R_S, R_H, R_L)
+        L0 = torch.zeros((geom.nnzb(2), B, B), dtype=torch.float64, device="cuda")
+        ctx.init_L(Sd, L0)
+        L = L0.clone()
+        ctx.minimise(L, Sd, Hd, MU, max_iter=args.warmup, precision=lsq.F32, refine_iter=0, final_eval=False)
+        L = L0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rep = ctx.minimise(L, Sd, Hd, MU, max_iter=args.steps, precision=lsq.F32, refine_iter=0,
+                           final_eval=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        done = max(int(rep["iterations"]), 1)
+        ms = e0.elapsed_time(e1) / done
+        free1, _ = torch.cuda.mem_get_info()
+        n = geom.n_atoms
+        out.append({"atoms": n, "cells": nc, "steps": done, "ms_per_step": ms,
+                    "us_per_atom_step": ms * 1e3 / n,
+                    "nnzb": {"S": geom.nnzb(0), "L": geom.nnzb(2), "LSL": geom.nnzb(5)},
+                    "device_gb": (free0 - free1) / 1e9})
+        print("sizes: %d atoms, %.3f ms/step, %.3f us/atom-step, %.1f GB" %
+              (n, ms, ms * 1e3 / n, (free0 - free1) / 1e9), file=sys.stderr)
+        ctx.close()
+        geom.close()
+        del ctx, geom, L, L0, Hd, Sd
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "mixed-precision LNV ms/step against atoms (O(N))", "unit": "ms/step",
+                      "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "Si diamond n x n x n cells, sigma 0.05 A, R_S=R_H=6.6 A, "
+                                             "R_L=10 A, 4x4 blocks, mu=-2 eV"},
+                      "sizes": out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "sizes":
+        run_sizes(args)
     else:
         run_ours(args)
 
