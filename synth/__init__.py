@@ -8,5 +8,5 @@ Both the oracle and the GPU path call it with their own pair lists.
 """
 from .silicon import (  # noqa: F401
     A_SI, SEED_BASE, diamond_si_positions, sk_blocks, SK_H, SK_S, config_seed,
-    batch_system_seed, batch_workload,
+    batch_system_seed, batch_workload, md_trajectory,
 )

@@ -83,6 +83,34 @@ def diamond_si_positions(n, sigma, seed, a=A_SI):
     return np.ascontiguousarray(pos, dtype=np.float64), cell
 
 
+def md_trajectory(pos0, cell, n_steps, seed, amp=0.05, period=(20.0, 40.0)):
+    """A prescribed atomic motion standing in for a molecular-dynamics run of the crystal.
+
+    Every atom oscillates about its starting position:
+    r_i(t_n) = r_i(0) + u_i sin(2 pi n / T_i + phi_i), with a seeded direction
+    and amplitude u_i (Gaussian components of standard deviation amp,
+    Angstrom), a period T_i uniform in `period` (steps) and a phase phi_i
+    uniform in [0, 2 pi).  With amp = 0.05 A and periods of 20-40 steps
+    an atom moves ~0.01 A per step, the scale of a 1 fs step of Si at room
+    temperature.  Returns [n_steps + 1, N, 3] float64, wrapped into the cell.
+    """
+    pos0 = np.asarray(pos0, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    n = pos0.shape[0]
+    u = rng.normal(0.0, amp, size=(n, 3))
+    T = rng.uniform(period[0], period[1], size=n)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    L = np.asarray(cell, dtype=np.float64)
+    out = np.empty((n_steps + 1, n, 3))
+    for k in range(n_steps + 1):
+        p = pos0 + u * np.sin(2.0 * np.pi * k / T + phi)[:, None]
+        p = np.mod(p, L)
+        p[p >= L] -= L[np.nonzero(p >= L)[1]]
+        p[p < 0.0] = 0.0
+        out[k] = p
+    return out
+
+
 def _cutoff(r):
     """Smooth cutoff: 1 below 5.6, cosine taper to 0 at 6.6, 0 beyond."""
     f = np.where(r <= RC_INNER, 1.0, 0.5 * (1.0 + np.cos(np.pi * (r - RC_INNER) / (RC - RC_INNER))))
