@@ -30,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import batch_workload, config_seed, diamond_si_positions, sk_blocks  # noqa: E402
+from synth import batch_workload, config_seed, diamond_si_positions, md_trajectory, sk_blocks  # noqa: E402
 
 N_CELLS = 8
 SIGMA = 0.05
@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--cpu-sample-rows", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--md-steps", type=int, default=4,
+                   help="extended-Lagrangian MD steps of the 4096-atom system (0: skip)")
     p.add_argument("--cells", default="4,6,8,10,12,16",
                    help="--workload sizes: diamond cells per edge of each system (8 n^3 atoms)")
     p.add_argument("--workload", default="si4096", choices=["si4096", "batch", "sizes"],
@@ -199,6 +201,87 @@ def roofline_product(lsq, geom, SL, Q, out):
     gradient terms and the line search's Z are products of this shape, three per step)."""
     return lsq.block_matmul(geom, B, SL, 3, Q, 5, out, 2, precision=lsq.F32, trans_b=True,
                             triangle=2)
+def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
+    """Extended-Lagrangian MD steps of the headline system (Sec. 3.3) along a prescribed
+    trajectory: per MD step the geometry, H and S, S^-1 (Hotelling on R_L), the propagated X
+    moved to the new patterns, L_0 = sym(X S^-1), and mixed-precision CG to tol.  Reports the
+    CG iterations from that start against the previous step's L (moved to the new patterns)
+    and the on-site start, and the device time of the XL work (propagation, the moves of the
+    history, the initial L)."""
+    K = 5
+    kappa, alpha, c = lsq.XL_DISSIPATION_K5
+    pos0, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1))
+    traj = md_trajectory(pos0, cell, n_md, seed=config_seed(1) + 77)
+    ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
+    f64 = torch.float64
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = {"xl": [], "previous_L": [], "onsite": []}
+    xl_ms, prop_ms, move_ms, init_ms = [], [], [], []
+    prev = None
+    for n in range(n_md + 1):
+        g = lsq.Geometry(torch.from_numpy(traj[n]).cuda(), cell, ranges)
+        rS, rL, rLS = g.range_id(R_S), g.range_id(R_L), g.range_id(R_L + R_S)
+        rp, col = g.pattern(1)
+        rp, col = rp.cpu().numpy(), col.cpu().numpy()
+        H, S = sk_blocks(traj[n], cell, np.repeat(np.arange(g.n_atoms), np.diff(rp)), col)
+        Hd, Sd = torch.from_numpy(H).cuda(), torch.from_numpy(S).cuda()
+        ctx = lsq.Lnv(g, B, R_S, R_H, R_L)
+        Xi = torch.zeros((g.nnzb(rL), B, B), dtype=f64, device="cuda")
+        lsq.hotelling_inverse(g, B, Sd, rS, Xi, rL, rLS, 12, precision=lsq.F32)
+        lsq.hotelling_inverse(g, B, Sd, rS, Xi, rL, rLS, 2, precision=lsq.F64, start=False)
+        L = torch.zeros((g.nnzb(rL), B, B), dtype=f64, device="cuda")
+        if n == 0:
+            ctx.init_L(Sd, L)
+            ctx.minimise(L, Sd, Hd, MU, max_iter=300, tol_ha_per_atom=tol, precision=lsq.F32)
+        else:
+            gp, ctxp, hist, LSp, Lp_prev = prev
+            rLSp = gp.range_id(R_L + R_S)
+            lsq.xl_initial_L(g, B, rLS, torch.zeros((g.nnzb(rLS), B, B), dtype=f64, device="cuda"),
+                             rL, Xi, rL, L)                         # builds this geometry's plan
+            torch.cuda.synchronize()
+            Xn = torch.empty_like(hist[0])
+            moved = [torch.empty((g.nnzb(rLS), B, B), dtype=f64, device="cuda") for _ in range(K + 1)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            lsq.xl_propagate(gp, B, rLSp, hist, LSp, Xn, kappa, alpha, c)
+            ev[1].record(stream)
+            for src, dst in zip([Xn] + hist[:K], moved):
+                lsq.pattern_remap(gp, rLSp, g, rLS, B, src, dst)
+            ev[2].record(stream)
+            lsq.xl_initial_L(g, B, rLS, moved[0], rL, Xi, rL, L)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            prop_ms.append(ev[0].elapsed_time(ev[1]))
+            move_ms.append(ev[1].elapsed_time(ev[2]))
+            init_ms.append(ev[2].elapsed_time(ev[3]))
+            xl_ms.append(ev[0].elapsed_time(ev[3]))
+            hist = moved
+            Lprev = torch.zeros_like(L)
+            lsq.pattern_remap(gp, gp.range_id(R_L), g, rL, B, Lp_prev, Lprev)
+            Lon = torch.zeros_like(L)
+            ctx.init_L(Sd, Lon)
+            for name, Ls in (("previous_L", Lprev), ("onsite", Lon), ("xl", L)):
+                rep = ctx.minimise(Ls, Sd, Hd, MU, max_iter=300, tol_ha_per_atom=tol, precision=lsq.F32)
+                its[name].append(int(rep["iterations"]))
+            ctxp.close()
+            gp.close()
+        LS = torch.zeros((g.nnzb(rLS), B, B), dtype=f64, device="cuda")
+        lsq.block_matmul(g, B, L, rL, Sd, rS, LS, rLS)
+        if n == 0:
+            hist = [LS.clone() for _ in range(K + 1)]
+        prev = (g, ctx, hist, LS, L)
+    prev[1].close()
+    prev[0].close()
+    mean = lambda v: float(np.mean(v)) if v else None
+    return {"md_steps": n_md, "tol_ha_per_atom": tol, "cg_iterations_to_tol": its,
+            "xl_ms_per_md_step": mean(xl_ms), "propagate_ms": mean(prop_ms),
+            "move_history_ms": mean(move_ms), "initial_L_ms": mean(init_ms),
+            "dissipation": {"K": K, "kappa": kappa, "alpha": alpha, "c": list(c)},
+            "workload": ("4096-atom Si moving along a prescribed seeded trajectory (0.05 A "
+                         "oscillations, periods 20-40 steps, ~0.01 A per step); X on R_L + R_S, "
+                         "S^-1 from 12 float32 + 2 float64 Hotelling steps on R_L; mixed CG")}
+
+
 def run_ours(args):
     import torch
     import paper_2002_07704_gb300 as lsq
@@ -418,6 +501,9 @@ def run_ours(args):
              "ne_error_rel": abs(rc_["ne"] - n0) / n0, "lambda_ev": lam_,
              "workload": "mixed precision, N_e fixed at its value at the grand-canonical iterate"}
 
+    # --- extended-Lagrangian MD steps (Sec. 3.3) ---
+    xl = xl_md_section(lsq, torch, stream, args.md_steps) if args.md_steps > 0 else None
+
     # --- end to end through the public API, host buffers ---
     Lh = L0.cpu().pin_memory()
     Sh = Sd.cpu().pin_memory()
@@ -477,6 +563,7 @@ def run_ours(args):
             "hotelling": dict(hot, workload="X = S^-1 approximated on the 10 A range by "
                                              "X <- 2X - (X S) X from X0 = S / s^2, the LNV metric of Sec. 2.3.2"),
             "canonical": canon,
+            "xlbomd": xl,
             "metric_cg": dict(mcg, workload="mixed-precision CG from L0 until |dOmega|/N < tol; "
                                                "metric: X from 12 float32 + 2 float64 Hotelling steps "
                                                "on the 6.6 A range"),

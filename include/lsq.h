@@ -382,6 +382,59 @@ int lsq_lnv_minimise_batch(lsq_lnv ctx, double *L_dev, const double *S_dev, cons
                            const double *mu_host, const lsq_lnv_opts *opts, lsq_lnv_report *reps,
                            void *stream);
 
+/* ---- density matrix between MD steps (Sec. 3.3) ---------------------- */
+
+/*
+ * Moves a matrix to another pattern of the same atoms, typically the
+ * pattern of the same range after the atoms moved (Sec. 3.3: the matrices
+ * carried from one MD step to the next).  Block (i, j) of range_to's
+ * pattern in g_to receives block (i, j) of range_from's pattern in g_from
+ * where that pattern stores it, and zeros elsewhere: blocks of pairs that
+ * left the range are dropped, pairs that entered start at zero.  The
+ * copies are exact.
+ *
+ * g_from and g_to must hold the same atom count (LSQ_ERR_INVALID_ARG
+ * otherwise) and may be the same geometry.  X_from_dev: blocks on
+ * (g_from, range_from); X_to_dev: blocks on (g_to, range_to), written; both
+ * b x b row-major in the precision's value type (LSQ_F64 double, LSQ_F32
+ * float) and not aliased.  Enqueued on stream; no allocation, no
+ * synchronisation.
+ */
+int lsq_pattern_remap(lsq_geom g_from, int range_from, lsq_geom g_to, int range_to, int b,
+                      int precision, const void *X_from_dev, void *X_to_dev, void *stream);
+
+/*
+ * One step of the extended-Lagrangian propagation of X, the auxiliary
+ * matrix associated with L S (Sec. 3.3): the Verlet step in the harmonic
+ * potential centred on L(t) S(t), plus the dissipative sum,
+ *     X(t+dt) = 2 X(t) - X(t-dt) + kappa (LS - X(t)) + alpha sum_{m<n_c} c_m X(t - m dt),
+ * kappa = dt^2 w^2, evaluated in that order with every operation rounded
+ * once (no contraction).  alpha = 0 drops the sum (c may then be NULL).
+ *
+ * X_hist_host: host array of n_hist (2..10) device pointers, X(t), X(t-dt),
+ * ..., all float64 blocks on range_x (L S's range R_L + R_S) of g.
+ * LS_dev: L(t) S(t) on range_x.  c_host: n_c (1..n_hist) coefficients.
+ * X_next_dev: X(t+dt), written; it may be one of the history arrays
+ * (each value is read before it is written) but not LS_dev.  Enqueued on
+ * stream; no allocation, no synchronisation.
+ */
+int lsq_xl_propagate(lsq_geom g, int b, int range_x, int n_hist, const double *const *X_hist_host,
+                     const double *LS_dev, double kappa, double alpha, const double *c_host, int n_c,
+                     double *X_next_dev, void *stream);
+
+/*
+ * The initial L of an MD step from the propagated X (Sec. 3.3: X S^-1 is
+ * the initial guess for L): L_0 = ((X Sinv) + (X Sinv)^T) / 2 on range_l,
+ * the product truncated to range_l and its symmetric part formed in place
+ * (exactly symmetric).  X_dev: float64 blocks on range_x; Sinv_dev: an
+ * approximate inverse overlap on range_sinv (e.g. from
+ * lsq_hotelling_inverse); L_out_dev: float64 blocks on range_l, written,
+ * not aliasing the inputs.  The product's plan is built on the first call
+ * for these ranges (allocates, synchronises) as for lsq_block_matmul.
+ */
+int lsq_xl_initial_L(lsq_geom g, int b, int range_x, const double *X_dev, int range_sinv,
+                     const double *Sinv_dev, int range_l, double *L_out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,9 @@ def load():
         "lsq_lnv_set_metric": (I, [P, I, P, I, P]),
         "lsq_lnv_init_purify": (I, [P, P, P, D, I, P, I, I, I, P, P, P]),
         "lsq_lnv_minimise_canonical": (I, [P, P, P, P, D, P, P, P, P]),
+        "lsq_pattern_remap": (I, [P, I, P, I, I, I, P, P, P]),
+        "lsq_xl_propagate": (I, [P, I, I, I, P, P, D, D, P, I, P, P]),
+        "lsq_xl_initial_L": (I, [P, I, I, P, I, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -106,7 +109,7 @@ def exported_symbols():
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
             "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
-            "lsq_lnv_minimise_canonical"]
+            "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L"]
 
 
 def launch_count():
@@ -240,6 +243,42 @@ def block_matmul(geom, b, A, range_a, B, range_b, C, range_c, precision=F64, tra
                                        range_b, int(trans_b), _dev(B, dt), range_c, _dev(C, dt),
                                        float(alpha), float(beta), ctypes.byref(nt), _stream(stream)))
     return nt.value
+
+
+# A dissipation set (kappa, alpha, c_0..c_5) for lsq_xl_propagate: the K = 5 entry of the
+# table of Niklasson et al., J. Chem. Phys. 130, 214109 (2009), the scheme the paper cites
+# for its dissipative term (sum c_m = sum m c_m = 0).
+XL_DISSIPATION_K5 = (1.82, 0.018, (-6.0, 14.0, -8.0, -3.0, 4.0, -1.0))
+
+
+def pattern_remap(geom_from, range_from, geom_to, range_to, b, X_from, X_to, precision=F64, stream=None):
+    """X_to (on geom_to's range_to) = X_from (on geom_from's range_from) matched by atom pair."""
+    import torch
+    dt = torch.float64 if precision == F64 else torch.float32
+    _check(load().lsq_pattern_remap(geom_from.handle, range_from, geom_to.handle, range_to, b, precision,
+                                    _dev(X_from, dt), _dev(X_to, dt), _stream(stream)))
+
+
+def xl_propagate(geom, b, range_x, X_hist, LS, X_next, kappa, alpha=0.0, c=None, stream=None):
+    """X_next = 2 X(t) - X(t-dt) + kappa (LS - X(t)) + alpha sum_m c_m X(t - m dt).
+
+    X_hist: [X(t), X(t-dt), ...] (float64 tensors on range_x); X_next may be one of them.
+    """
+    import torch
+    ptrs = (ctypes.c_void_p * len(X_hist))(*[_dev(x, torch.float64) for x in X_hist])
+    nc = 0 if c is None else len(c)
+    carr = (ctypes.c_double * max(nc, 1))(*([float(v) for v in c] if c is not None else [0.0]))
+    _check(load().lsq_xl_propagate(geom.handle, b, range_x, len(X_hist), ptrs, _dev(LS, torch.float64),
+                                   float(kappa), float(alpha), carr if nc else None, nc,
+                                   _dev(X_next, torch.float64), _stream(stream)))
+
+
+def xl_initial_L(geom, b, range_x, X, range_sinv, Sinv, range_l, L_out, stream=None):
+    """L_out = symmetric part of (X Sinv) on range_l (the MD step's initial L)."""
+    import torch
+    _check(load().lsq_xl_initial_L(geom.handle, b, range_x, _dev(X, torch.float64), range_sinv,
+                                   _dev(Sinv, torch.float64), range_l, _dev(L_out, torch.float64),
+                                   _stream(stream)))
 
 
 def trace(geom, b, X, range_x, Y, range_y, precision=F64, stream=None):

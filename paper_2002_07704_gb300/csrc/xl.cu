@@ -1,0 +1,204 @@
+// Extended-Lagrangian propagation of the density matrix between MD steps (Sec. 3.3).
+//
+// An auxiliary sparse matrix X, associated with L S, follows a harmonic potential centred on
+// the ground state L(t) S(t).  Its Verlet step, with the dissipative sum the paper adds, is
+//
+//   X(t + dt) = 2 X(t) - X(t - dt) + kappa (L(t) S(t) - X(t)) + a sum_{m=0}^{M} c_m X(t - m dt),
+//
+// kappa = dt^2 w^2, and X S^-1 is the next step's initial L (here: its symmetric part on L's
+// range).  When the atoms move, the matrices carried from one step to the next move to the
+// new geometry's patterns block by block, matched by atom pair.
+//
+// Three entry points, each one or two kernels: the pattern move (index work, exact copies),
+// the fused propagation (HBM-bound: M + 3 reads and one write per value), and the initial L
+// (one truncated product and an in-place symmetric part).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "lsq_internal.h"
+
+namespace lsq {
+namespace {
+
+constexpr int kMaxHist = 10;
+
+// Block (i, j) of the target pattern takes block (i, j) of the source pattern where the
+// source stores it, else zero.  One warp per row: each lane finds one target block's source
+// by binary search in the (ascending) source row, then the warp copies the chunk's blocks
+// together, lanes over values.
+template <typename T>
+__global__ void k_remap_rows(int n, int bb, const int64_t *__restrict__ fp, const int32_t *__restrict__ fc,
+                             const T *__restrict__ Xf, const int64_t *__restrict__ tp,
+                             const int32_t *__restrict__ tc, T *__restrict__ Xt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw) {
+        const int64_t f0 = fp[i], f1 = fp[i + 1], t1 = tp[i + 1];
+        for (int64_t base = tp[i]; base < t1; base += 32) {
+            const int64_t e = base + lane;
+            int64_t src = -1;
+            if (e < t1) {
+                const int j = tc[e];
+                int64_t lo = f0, hi = f1;  // first position with column >= j
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (fc[mid] < j) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < f1 && fc[lo] == j) src = lo;
+            }
+            const int nb = (int)(t1 - base < 32 ? t1 - base : 32);
+            for (int t = 0; t < nb; ++t) {
+                const int64_t s = __shfl_sync(0xffffffffu, src, t);
+                T *dst = Xt + (base + t) * bb;
+                for (int v = lane; v < bb; v += 32) dst[v] = s >= 0 ? Xf[s * bb + v] : T(0);
+            }
+        }
+    }
+}
+
+struct XlArgs {
+    const double *X[kMaxHist];  // X(t), X(t - dt), ...
+    const double *LS;
+    double c[kMaxHist];
+    int nc;  // dissipation terms (0: none)
+    double kappa, alpha;
+    double *out;
+    int64_t m;
+};
+
+// The Verlet step with dissipation, every operation rounded once in the order written above
+// (no contraction), so that it is reproducible term by term.  out may be one of the history
+// arrays: each value is read before it is written, by the same thread.
+__global__ void k_xl_propagate(XlArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.m; e += stride) {
+        const double x0 = a.X[0][e];
+        double o = __dsub_rn(__dmul_rn(2.0, x0), a.X[1][e]);
+        o = __dadd_rn(o, __dmul_rn(a.kappa, __dsub_rn(a.LS[e], x0)));
+        if (a.nc > 0) {
+            double s = __dmul_rn(a.c[0], x0);
+            for (int k = 1; k < a.nc; ++k) s = __dadd_rn(s, __dmul_rn(a.c[k], a.X[k][e]));
+            o = __dadd_rn(o, __dmul_rn(a.alpha, s));
+        }
+        a.out[e] = o;
+    }
+}
+
+// X = (X + X^T) / 2 in place on a symmetric pattern: the thread of the entry with p <= tm[p]
+// reads both blocks of the pair and writes both, so the result is exactly symmetric.
+__global__ void k_sym_part_inplace(int64_t nnzb, int b, const int64_t *__restrict__ tm, double *X) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int bb = b * b;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnzb; p += stride) {
+        const int64_t q = tm[p];
+        if (q < p) continue;
+        double *P = X + p * bb, *Q = X + q * bb;
+        if (q == p) {
+            for (int r = 0; r < b; ++r)
+                for (int c = r + 1; c < b; ++c) {
+                    const double v = __dmul_rn(0.5, __dadd_rn(P[r * b + c], P[c * b + r]));
+                    P[r * b + c] = v;
+                    P[c * b + r] = v;
+                }
+        } else {
+            for (int r = 0; r < b; ++r)
+                for (int c = 0; c < b; ++c) {
+                    const double v = __dmul_rn(0.5, __dadd_rn(P[r * b + c], Q[c * b + r]));
+                    P[r * b + c] = v;
+                    Q[c * b + r] = v;
+                }
+        }
+    }
+}
+
+int grid_of(int64_t m, int threads = 256) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((m + threads - 1) / threads, 152 * 16));
+}
+
+}  // namespace
+}  // namespace lsq
+
+using namespace lsq;
+
+extern "C" int lsq_pattern_remap(lsq_geom g_from, int range_from, lsq_geom g_to, int range_to, int b,
+                                 int precision, const void *X_from, void *X_to, void *stream) {
+    clear_error();
+    LSQ_TRY(geom_check(g_from, range_from));
+    LSQ_TRY(geom_check(g_to, range_to));
+    if (g_from->n != g_to->n) return set_error(LSQ_ERR_INVALID_ARG, "the geometries hold different atom counts");
+    if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
+    if (precision != LSQ_F64 && precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    const Pattern &F = g_from->pats[range_from], &T = g_to->pats[range_to];
+    if (T.nnzb == 0 || g_to->n == 0) return LSQ_OK;
+    if (!X_to || (F.nnzb > 0 && !X_from)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
+    if (X_from == X_to) return set_error(LSQ_ERR_INVALID_ARG, "X_to must not alias X_from");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = grid_of((int64_t)g_to->n * 32);
+    note_launch();
+    if (precision == LSQ_F64)
+        k_remap_rows<double><<<grid, 256, 0, s>>>(g_to->n, b * b, F.row_ptr.p, F.col.p, (const double *)X_from,
+                                                  T.row_ptr.p, T.col.p, (double *)X_to);
+    else
+        k_remap_rows<float><<<grid, 256, 0, s>>>(g_to->n, b * b, F.row_ptr.p, F.col.p, (const float *)X_from,
+                                                 T.row_ptr.p, T.col.p, (float *)X_to);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
+extern "C" int lsq_xl_propagate(lsq_geom g, int b, int range_x, int n_hist, const double *const *X_hist,
+                                const double *LS, double kappa, double alpha, const double *c, int n_c,
+                                double *X_next, void *stream) {
+    clear_error();
+    LSQ_TRY(geom_check(g, range_x));
+    if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
+    if (n_hist < 2 || n_hist > kMaxHist)
+        return set_error(LSQ_ERR_INVALID_ARG, "n_hist must be in [2, " + std::to_string(kMaxHist) + "]");
+    if (!X_hist) return set_error(LSQ_ERR_INVALID_ARG, "null history array");
+    if (alpha != 0.0 && (!c || n_c < 1 || n_c > n_hist))
+        return set_error(LSQ_ERR_INVALID_ARG, "dissipation needs 1 <= n_c <= n_hist coefficients");
+    const int64_t m = g->pats[range_x].nnzb * (int64_t)(b * b);
+    if (m == 0) return LSQ_OK;
+    XlArgs a;
+    for (int k = 0; k < n_hist; ++k) {
+        if (!X_hist[k]) return set_error(LSQ_ERR_INVALID_ARG, "null history matrix");
+        a.X[k] = X_hist[k];
+    }
+    if (!LS || !X_next) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
+    a.nc = alpha != 0.0 ? n_c : 0;
+    for (int k = 0; k < a.nc; ++k) a.c[k] = c[k];
+    a.LS = LS;
+    a.kappa = kappa;
+    a.alpha = alpha;
+    a.out = X_next;
+    a.m = m;
+    note_launch();
+    k_xl_propagate<<<grid_of(m), 256, 0, (cudaStream_t)stream>>>(a);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
+extern "C" int lsq_xl_initial_L(lsq_geom g, int b, int range_x, const double *X, int range_sinv,
+                                const double *Sinv, int range_l, double *L_out, void *stream) {
+    clear_error();
+    LSQ_TRY(geom_check(g, range_x));
+    LSQ_TRY(geom_check(g, range_sinv));
+    LSQ_TRY(geom_check(g, range_l));
+    if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
+    if (g->n > 0 && (!X || !Sinv || !L_out)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
+    if ((const void *)L_out == (const void *)X || (const void *)L_out == (const void *)Sinv)
+        return set_error(LSQ_ERR_INVALID_ARG, "L_out must not alias X or Sinv");
+    if (g->n == 0) return LSQ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    LSQ_TRY(block_matmul(g, b, LSQ_F64, range_x, 0, X, range_sinv, 0, Sinv, range_l, L_out, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(ensure_tmap(g, range_l, s));
+    const int64_t nnzb = g->pats[range_l].nnzb;
+    note_launch();
+    k_sym_part_inplace<<<grid_of(nnzb), 256, 0, s>>>(nnzb, b, g->pats[range_l].tmap.p, L_out);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
