@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--cpu-sample-rows", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--md-steps", type=int, default=4,
+    p.add_argument("--md-steps", type=int, default=8,
                    help="extended-Lagrangian MD steps of the 4096-atom system (0: skip)")
     p.add_argument("--cells", default="4,6,8,10,12,16",
                    help="--workload sizes: diamond cells per edge of each system (8 n^3 atoms)")
@@ -237,7 +237,7 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
             gp, ctxp, hist, LSp, Lp_prev = prev
             rLSp = gp.range_id(R_L + R_S)
             lsq.xl_initial_L(g, B, rLS, torch.zeros((g.nnzb(rLS), B, B), dtype=f64, device="cuda"),
-                             rL, Xi, rL, L)                         # builds this geometry's plan
+                             rL, Xi, rL, L, precision=lsq.F32)      # builds this geometry's plan
             torch.cuda.synchronize()
             Xn = torch.empty_like(hist[0])
             moved = [torch.empty((g.nnzb(rLS), B, B), dtype=f64, device="cuda") for _ in range(K + 1)]
@@ -248,7 +248,7 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
             for src, dst in zip([Xn] + hist[:K], moved):
                 lsq.pattern_remap(gp, rLSp, g, rLS, B, src, dst)
             ev[2].record(stream)
-            lsq.xl_initial_L(g, B, rLS, moved[0], rL, Xi, rL, L)
+            lsq.xl_initial_L(g, B, rLS, moved[0], rL, Xi, rL, L, precision=lsq.F32)
             ev[3].record(stream)
             torch.cuda.synchronize()
             prop_ms.append(ev[0].elapsed_time(ev[1]))
@@ -270,16 +270,26 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
         if n == 0:
             hist = [LS.clone() for _ in range(K + 1)]
         prev = (g, ctx, hist, LS, L)
+    m_ls = prev[0].nnzb(prev[0].range_id(R_L + R_S)) * B * B
     prev[1].close()
     prev[0].close()
     mean = lambda v: float(np.mean(v)) if v else None
+    hbm_peak, hbm_kind = measured_peaks()
+    # algorithmic bytes: the propagation reads K + 1 history arrays and L S and writes X(t + dt);
+    # each move reads and writes one array of L S's range (float64)
+    prop_bytes = (K + 3) * m_ls * 8
+    move_bytes = (K + 1) * 2 * m_ls * 8
+    bw = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9 if ms else None
     return {"md_steps": n_md, "tol_ha_per_atom": tol, "cg_iterations_to_tol": its,
             "xl_ms_per_md_step": mean(xl_ms), "propagate_ms": mean(prop_ms),
             "move_history_ms": mean(move_ms), "initial_L_ms": mean(init_ms),
+            "propagate_gbs": bw(prop_bytes, mean(prop_ms)), "move_history_gbs": bw(move_bytes, mean(move_ms)),
+            "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind,
             "dissipation": {"K": K, "kappa": kappa, "alpha": alpha, "c": list(c)},
             "workload": ("4096-atom Si moving along a prescribed seeded trajectory (0.05 A "
                          "oscillations, periods 20-40 steps, ~0.01 A per step); X on R_L + R_S, "
-                         "S^-1 from 12 float32 + 2 float64 Hotelling steps on R_L; mixed CG")}
+                         "S^-1 from 12 float32 + 2 float64 Hotelling steps on R_L; L_0 = sym(X S^-1) with float32 "
+                         "products; mixed CG")}
 
 
 def run_ours(args):

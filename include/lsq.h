@@ -408,8 +408,10 @@ int lsq_pattern_remap(lsq_geom g_from, int range_from, lsq_geom g_to, int range_
  * matrix associated with L S (Sec. 3.3): the Verlet step in the harmonic
  * potential centred on L(t) S(t), plus the dissipative sum,
  *     X(t+dt) = 2 X(t) - X(t-dt) + kappa (LS - X(t)) + alpha sum_{m<n_c} c_m X(t - m dt),
- * kappa = dt^2 w^2, evaluated in that order with every operation rounded
- * once (no contraction).  alpha = 0 drops the sum (c may then be NULL).
+ * kappa = dt^2 w^2, evaluated with the terms grouped by history entry
+ * (weights 2 - kappa + alpha c_0, -1 + alpha c_1, alpha c_m, and kappa for
+ * LS; one FMA each), so it agrees with the formula as written to a few
+ * units in the last place.  alpha = 0 drops the sum (c may then be NULL).
  *
  * X_hist_host: host array of n_hist (2..10) device pointers, X(t), X(t-dt),
  * ..., all float64 blocks on range_x (L S's range R_L + R_S) of g.
@@ -429,10 +431,13 @@ int lsq_xl_propagate(lsq_geom g, int b, int range_x, int n_hist, const double *c
  * (exactly symmetric).  X_dev: float64 blocks on range_x; Sinv_dev: an
  * approximate inverse overlap on range_sinv (e.g. from
  * lsq_hotelling_inverse); L_out_dev: float64 blocks on range_l, written,
- * not aliasing the inputs.  The product's plan is built on the first call
+ * not aliasing the inputs.  precision LSQ_F64, or LSQ_F32: the operands
+ * are rounded to float32 and multiplied in float32 (a float32 workspace
+ * held by g, grown on demand), the product widened to float64 before its
+ * symmetric part is taken.  The product's plan is built on the first call
  * for these ranges (allocates, synchronises) as for lsq_block_matmul.
  */
-int lsq_xl_initial_L(lsq_geom g, int b, int range_x, const double *X_dev, int range_sinv,
+int lsq_xl_initial_L(lsq_geom g, int b, int precision, int range_x, const double *X_dev, int range_sinv,
                      const double *Sinv_dev, int range_l, double *L_out_dev, void *stream);
 
 #ifdef __cplusplus

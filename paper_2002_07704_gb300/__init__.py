@@ -90,7 +90,7 @@ def load():
         "lsq_lnv_minimise_canonical": (I, [P, P, P, P, D, P, P, P, P]),
         "lsq_pattern_remap": (I, [P, I, P, I, I, I, P, P, P]),
         "lsq_xl_propagate": (I, [P, I, I, I, P, P, D, D, P, I, P, P]),
-        "lsq_xl_initial_L": (I, [P, I, I, P, I, P, I, P, P]),
+        "lsq_xl_initial_L": (I, [P, I, I, I, P, I, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,10 +273,10 @@ def xl_propagate(geom, b, range_x, X_hist, LS, X_next, kappa, alpha=0.0, c=None,
                                    _dev(X_next, torch.float64), _stream(stream)))
 
 
-def xl_initial_L(geom, b, range_x, X, range_sinv, Sinv, range_l, L_out, stream=None):
+def xl_initial_L(geom, b, range_x, X, range_sinv, Sinv, range_l, L_out, precision=F64, stream=None):
     """L_out = symmetric part of (X Sinv) on range_l (the MD step's initial L)."""
     import torch
-    _check(load().lsq_xl_initial_L(geom.handle, b, range_x, _dev(X, torch.float64), range_sinv,
+    _check(load().lsq_xl_initial_L(geom.handle, b, precision, range_x, _dev(X, torch.float64), range_sinv,
                                    _dev(Sinv, torch.float64), range_l, _dev(L_out, torch.float64),
                                    _stream(stream)))
 

@@ -133,6 +133,8 @@ struct lsq_geom_s {
     std::map<std::tuple<int, int, int>, lsq::ProductPlan> pplans;
     // scratch for transposed operands of lsq_block_matmul (grown on demand)
     lsq::DevBuf<char> scratch_a, scratch_x;
+    // float32 operands and result of lsq_xl_initial_L (grown on demand)
+    lsq::DevBuf<char> xl_scratch;
     lsq::Reducer red;
 };
 

@@ -10,12 +10,13 @@
 // new geometry's patterns block by block, matched by atom pair.
 //
 // Three entry points, each one or two kernels: the pattern move (index work, exact copies),
-// the fused propagation (HBM-bound: M + 3 reads and one write per value), and the initial L
-// (one truncated product and an in-place symmetric part).
+// the fused propagation (M + 3 reads and one write per value, bound by the FP64 pipe), and
+// the initial L (one truncated product and an in-place symmetric part).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include "lsq_internal.h"
 
@@ -27,7 +28,8 @@ constexpr int kMaxHist = 10;
 // Block (i, j) of the target pattern takes block (i, j) of the source pattern where the
 // source stores it, else zero.  One warp per row: each lane finds one target block's source
 // by binary search in the (ascending) source row, then the warp copies the chunk's blocks
-// together, lanes over values.
+// together, lane l taking values l, l + 32, ... of the chunk (coalesced writes; the reads are
+// too wherever consecutive target blocks have consecutive sources).
 template <typename T>
 __global__ void k_remap_rows(int n, int bb, const int64_t *__restrict__ fp, const int32_t *__restrict__ fc,
                              const T *__restrict__ Xf, const int64_t *__restrict__ tp,
@@ -50,11 +52,14 @@ __global__ void k_remap_rows(int n, int bb, const int64_t *__restrict__ fp, cons
                 }
                 if (lo < f1 && fc[lo] == j) src = lo;
             }
-            const int nb = (int)(t1 - base < 32 ? t1 - base : 32);
-            for (int t = 0; t < nb; ++t) {
+            // the chunk's nb blocks are contiguous in the target: lanes take consecutive values
+            const int nv = (int)(t1 - base < 32 ? t1 - base : 32) * bb;
+            T *dst = Xt + base * bb;
+            for (int v0 = 0; v0 < nv; v0 += 32) {
+                const int v = v0 + lane;
+                const int t = (v < nv ? v : nv - 1) / bb;
                 const int64_t s = __shfl_sync(0xffffffffu, src, t);
-                T *dst = Xt + (base + t) * bb;
-                for (int v = lane; v < bb; v += 32) dst[v] = s >= 0 ? Xf[s * bb + v] : T(0);
+                if (v < nv) dst[v] = s >= 0 ? Xf[s * bb + (v - t * bb)] : T(0);
             }
         }
     }
@@ -63,29 +68,55 @@ __global__ void k_remap_rows(int n, int bb, const int64_t *__restrict__ fp, cons
 struct XlArgs {
     const double *X[kMaxHist];  // X(t), X(t - dt), ...
     const double *LS;
-    double c[kMaxHist];
-    int nc;  // dissipation terms (0: none)
-    double kappa, alpha;
+    double w[kMaxHist];  // weight of each history entry
+    int nh;              // history entries read (2 .. kMaxHist)
+    double kappa;        // weight of L S
     double *out;
     int64_t m;
 };
 
-// The Verlet step with dissipation, every operation rounded once in the order written above
-// (no contraction), so that it is reproducible term by term.  out may be one of the history
-// arrays: each value is read before it is written, by the same thread.
-__global__ void k_xl_propagate(XlArgs a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.m; e += stride) {
-        const double x0 = a.X[0][e];
-        double o = __dsub_rn(__dmul_rn(2.0, x0), a.X[1][e]);
-        o = __dadd_rn(o, __dmul_rn(a.kappa, __dsub_rn(a.LS[e], x0)));
-        if (a.nc > 0) {
-            double s = __dmul_rn(a.c[0], x0);
-            for (int k = 1; k < a.nc; ++k) s = __dadd_rn(s, __dmul_rn(a.c[k], a.X[k][e]));
-            o = __dadd_rn(o, __dmul_rn(a.alpha, s));
-        }
-        a.out[e] = o;
+// The Verlet step with dissipation, its terms grouped by history entry,
+//   X(t + dt) = kappa LS + (2 - kappa + a c_0) X(t) + (-1 + a c_1) X(t - dt) + sum_{m>=2} a c_m X(t - m dt),
+// one FMA per entry.  The FP64 pipe, not HBM, bounds this kernel on this GPU (eight FP64
+// instructions per 64 bytes moved against a ridge near 0.08 per byte), so the grouping (about
+// half the FP64 instructions of the formula evaluated term by term) sets its speed.  The
+// history loop is unrolled over the fixed maximum (predicated by nh), so the argument arrays
+// are indexed statically and all loads of a value issue together; V values per thread
+// (16-byte loads for V = 2).  out may be one of the history arrays: each value is read
+// before it is written, by the same thread.
+template <int V>
+__device__ __forceinline__ void xl_values(const XlArgs &a, int64_t e) {
+    using VT = typename std::conditional<V == 2, double2, double>::type;
+    auto ld = [&](const double *p) { return *reinterpret_cast<const VT *>(p + e); };
+    auto part = [](const VT &x, int j) -> double {
+        if constexpr (V == 2) return j == 0 ? x.x : x.y;
+        else return x;
+    };
+    VT xk[kMaxHist];
+    const VT ls = ld(a.LS);
+#pragma unroll
+    for (int k = 0; k < kMaxHist; ++k)
+        if (k < a.nh) xk[k] = ld(a.X[k]);
+    double o[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        double r = a.kappa * part(ls, j);
+#pragma unroll
+        for (int k = 0; k < kMaxHist; ++k)
+            if (k < a.nh) r = fma(a.w[k], part(xk[k], j), r);
+        o[j] = r;
     }
+    if constexpr (V == 2) *reinterpret_cast<double2 *>(a.out + e) = make_double2(o[0], o[1]);
+    else a.out[e] = o[0];
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_xl_propagate(XlArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
+    const int64_t mv = a.m / V * V;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; e < mv; e += stride) xl_values<V>(a, e);
+    // the odd tail value (V = 2, m odd)
+    if (V == 2 && blockIdx.x == 0 && threadIdx.x == 0 && mv < a.m) xl_values<1>(a, mv);
 }
 
 // X = (X + X^T) / 2 in place on a symmetric pattern: the thread of the entry with p <= tm[p]
@@ -113,6 +144,16 @@ __global__ void k_sym_part_inplace(int64_t nnzb, int b, const int64_t *__restric
                 }
         }
     }
+}
+
+__global__ void k_to_f32(int64_t m, const double *__restrict__ x, float *__restrict__ y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) y[e] = (float)x[e];
+}
+
+__global__ void k_to_f64(int64_t m, const float *__restrict__ x, double *__restrict__ y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) y[e] = (double)x[e];
 }
 
 int grid_of(int64_t m, int threads = 256) {
@@ -169,32 +210,72 @@ extern "C" int lsq_xl_propagate(lsq_geom g, int b, int range_x, int n_hist, cons
         a.X[k] = X_hist[k];
     }
     if (!LS || !X_next) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
-    a.nc = alpha != 0.0 ? n_c : 0;
-    for (int k = 0; k < a.nc; ++k) a.c[k] = c[k];
+    // weights of the history entries: 2 - kappa and -1 from the Verlet step, a c_m from the
+    // dissipation; entries beyond both are not read
+    const int nc = alpha != 0.0 ? n_c : 0;
+    a.nh = std::max(2, nc);
+    for (int k = 0; k < a.nh; ++k) {
+        double w = k == 0 ? 2.0 - kappa : (k == 1 ? -1.0 : 0.0);
+        if (k < nc) w += alpha * c[k];
+        a.w[k] = w;
+    }
     a.LS = LS;
     a.kappa = kappa;
-    a.alpha = alpha;
     a.out = X_next;
     a.m = m;
+    bool al16 = reinterpret_cast<uintptr_t>(LS) % 16 == 0 && reinterpret_cast<uintptr_t>(X_next) % 16 == 0;
+    for (int k = 0; k < a.nh; ++k) al16 = al16 && reinterpret_cast<uintptr_t>(X_hist[k]) % 16 == 0;
     note_launch();
-    k_xl_propagate<<<grid_of(m), 256, 0, (cudaStream_t)stream>>>(a);
+    if (al16)
+        k_xl_propagate<2><<<grid_of((m + 1) / 2), 256, 0, (cudaStream_t)stream>>>(a);
+    else
+        k_xl_propagate<1><<<grid_of(m), 256, 0, (cudaStream_t)stream>>>(a);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
 
-extern "C" int lsq_xl_initial_L(lsq_geom g, int b, int range_x, const double *X, int range_sinv,
+extern "C" int lsq_xl_initial_L(lsq_geom g, int b, int precision, int range_x, const double *X, int range_sinv,
                                 const double *Sinv, int range_l, double *L_out, void *stream) {
     clear_error();
     LSQ_TRY(geom_check(g, range_x));
     LSQ_TRY(geom_check(g, range_sinv));
     LSQ_TRY(geom_check(g, range_l));
     if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
+    if (precision != LSQ_F64 && precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
     if (g->n > 0 && (!X || !Sinv || !L_out)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
     if ((const void *)L_out == (const void *)X || (const void *)L_out == (const void *)Sinv)
         return set_error(LSQ_ERR_INVALID_ARG, "L_out must not alias X or Sinv");
     if (g->n == 0) return LSQ_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    LSQ_TRY(block_matmul(g, b, LSQ_F64, range_x, 0, X, range_sinv, 0, Sinv, range_l, L_out, 1.0, 0.0, nullptr, s));
+    const int64_t bb = (int64_t)b * b;
+    const int64_t mx = g->pats[range_x].nnzb * bb, ms = g->pats[range_sinv].nnzb * bb;
+    const int64_t ml = g->pats[range_l].nnzb * bb;
+    if (precision == LSQ_F64) {
+        LSQ_TRY(block_matmul(g, b, LSQ_F64, range_x, 0, X, range_sinv, 0, Sinv, range_l, L_out, 1.0, 0.0, nullptr,
+                             s));
+    } else {
+        // float32 copies of the operands, the product in float32, the result widened
+        auto up16 = [](int64_t m) { return (m * (int64_t)sizeof(float) + 255) / 256 * 256; };
+        const size_t need = (size_t)(up16(mx) + up16(ms) + up16(ml));
+        if (g->xl_scratch.n < need) {
+            LSQ_CUDA_TRY(cudaStreamSynchronize(s));  // the old buffer may still be read
+            LSQ_TRY(g->xl_scratch.alloc(need));
+        }
+        float *X32 = reinterpret_cast<float *>(g->xl_scratch.p);
+        float *S32 = reinterpret_cast<float *>(g->xl_scratch.p + up16(mx));
+        float *P32 = reinterpret_cast<float *>(g->xl_scratch.p + up16(mx) + up16(ms));
+        note_launch();
+        k_to_f32<<<grid_of(mx), 256, 0, s>>>(mx, X, X32);
+        note_launch();
+        k_to_f32<<<grid_of(ms), 256, 0, s>>>(ms, Sinv, S32);
+        LSQ_CHECK_LAUNCH();
+        LSQ_TRY(block_matmul(g, b, LSQ_F32, range_x, 0, X32, range_sinv, 0, S32, range_l, P32, 1.0, 0.0, nullptr,
+                             s));
+        note_launch();
+        k_to_f64<<<grid_of(ml), 256, 0, s>>>(ml, P32, L_out);
+        LSQ_CHECK_LAUNCH();
+    }
     LSQ_TRY(ensure_tmap(g, range_l, s));
     const int64_t nnzb = g->pats[range_l].nnzb;
     note_launch();

@@ -2,9 +2,9 @@
 
 lsq_pattern_remap bit for bit (float64 and float32, b = 4 and 13, between
 two geometries of a trajectory and between ranges of one geometry);
-lsq_xl_propagate bit for bit (every operation rounded once in the same
-order on both sides), with and without dissipation, in place; lsq_xl_initial_L
-within 1e-12 and exactly symmetric; and a short extended-Lagrangian MD run
+lsq_xl_propagate within a few units in the last place (the kernel groups
+the terms by history entry), with and without dissipation, in place; lsq_xl_initial_L
+within 1e-12 (float32 products: 1e-5 of max |X| |S^-1|) and exactly symmetric; and a short extended-Lagrangian MD run
 on 64 atoms (Hotelling S^-1, propagation, moves between geometries, initial
 L, 12 float64 CG steps per MD step) against the oracle's run.
 """
@@ -63,7 +63,7 @@ def test_remap_rejects_different_atom_counts():
 
 
 @pytest.mark.parametrize("dissipation", [False, True])
-def test_propagate_is_bit_exact(dissipation):
+def test_propagate_matches_oracle(dissipation):
     pos, cell = si(3, 0.05, config_seed(0) + 4)
     g = gpu_geometry(pos, cell, [11.6])
     p = gpu_pattern(g, 0)
@@ -72,16 +72,22 @@ def test_propagate_is_bit_exact(dissipation):
     LS = oracle.Bsr(p, 4, rng.standard_normal((p.nnzb, 4, 4)))
     alpha, c = (ALPHA, C5) if dissipation else (0.0, None)
     want = OX.propagate(hist, LS, KAPPA, alpha, c)
+    # the kernel groups the terms by history entry: rounding differs from the formula taken
+    # term by term by a few units in the last place of the largest term
+    scale = np.abs(np.stack([h.val for h in hist] + [LS.val])).max() * (2.0 + KAPPA + 2 * 14 * ALPHA)
+    tol = 8 * np.finfo(np.float64).eps * scale
     hg = [cuda(h.val) for h in hist]
     out = torch.zeros_like(hg[0])
     lsq.xl_propagate(g, 4, 0, hg, cuda(LS.val), out, KAPPA, alpha, c)
-    assert np.array_equal(out.cpu().numpy(), want.val)
-    # in place over the oldest history entry
+    got = out.cpu().numpy()
+    assert np.abs(got - want.val).max() <= tol
+    # in place over the oldest history entry: the same values
     lsq.xl_propagate(g, 4, 0, hg, cuda(LS.val), hg[5], KAPPA, alpha, c)
-    assert np.array_equal(hg[5].cpu().numpy(), want.val)
+    assert np.array_equal(hg[5].cpu().numpy(), got)
 
 
-def test_initial_L_matches_oracle():
+@pytest.mark.parametrize("prec", [lsq.F64, lsq.F32])
+def test_initial_L_matches_oracle(prec):
     pos, cell = si(3, 0.1, config_seed(0) + 5)
     R_L, R_X = 5.0, 4.0
     ranges = sorted({R_L, R_X, R_L + 6.6})
@@ -95,9 +101,13 @@ def test_initial_L_matches_oracle():
     want = OX.initial_L(m, X, Sinv, R_L)
     L = torch.full((want.pat.nnzb, 4, 4), np.nan, dtype=torch.float64, device="cuda")
     lsq.xl_initial_L(g, 4, g.range_id(R_L + 6.6), cuda(X.val), g.range_id(R_X), cuda(Sinv.val),
-                     g.range_id(R_L), L)
+                     g.range_id(R_L), L, precision=prec)
     got = L.cpu().numpy()
-    assert rel_err(got, want.val) <= 1e-12
+    if prec == lsq.F64:
+        assert rel_err(got, want.val) <= 1e-12
+    else:
+        bound, _ = oracle.matmul(oracle.Bsr(px, 4, np.abs(X.val)), oracle.Bsr(ps, 4, np.abs(Sinv.val)), want.pat)
+        assert np.abs(got - want.val).max() <= 1e-5 * bound.val.max()
     assert np.array_equal(got, oracle.transpose(oracle.Bsr(want.pat, 4, got), want.pat).val)
 
 
