@@ -203,11 +203,14 @@ def roofline_product(lsq, geom, SL, Q, out):
                             triangle=2)
 def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
     """Extended-Lagrangian MD steps of the headline system (Sec. 3.3) along a prescribed
-    trajectory: per MD step the geometry, H and S, S^-1 (Hotelling on R_L), the propagated X
-    moved to the new patterns, L_0 = sym(X S^-1), and mixed-precision CG to tol.  Reports the
-    CG iterations from that start against the previous step's L (moved to the new patterns)
-    and the on-site start, and the device time of the XL work (propagation, the moves of the
-    history, the initial L)."""
+    trajectory: per MD step the geometry (adopting the previous geometry's product
+    schedules), H and S, S^-1 (Hotelling on R_L), the propagated X moved to the new patterns,
+    L_0 = sym(X S^-1), and mixed-precision CG to tol.  Reports the CG iterations from that
+    start against the previous step's L (moved to the new patterns) and the on-site start, the
+    device time of the XL work (propagation, the moves of the history, the initial L), the
+    wall time of each MD step (all three CG runs included, the model's H and S excluded), and
+    the last step's S^-1 and CG on a fresh geometry with adopted schedules against its own
+    tuning run."""
     K = 5
     kappa, alpha, c = lsq.XL_DISSIPATION_K5
     pos0, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1))
@@ -218,12 +221,19 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
     its = {"xl": [], "previous_L": [], "onsite": []}
     xl_ms, prop_ms, move_ms, init_ms = [], [], [], []
     prev = None
+    wall = []
+    xl_start = None
     for n in range(n_md + 1):
+        t_step = time.perf_counter()
         g = lsq.Geometry(torch.from_numpy(traj[n]).cuda(), cell, ranges)
+        if prev is not None:
+            g.adopt_schedules(prev[0])          # same ranges: no tuning run for this geometry
         rS, rL, rLS = g.range_id(R_S), g.range_id(R_L), g.range_id(R_L + R_S)
         rp, col = g.pattern(1)
         rp, col = rp.cpu().numpy(), col.cpu().numpy()
+        t_hs = time.perf_counter()
         H, S = sk_blocks(traj[n], cell, np.repeat(np.arange(g.n_atoms), np.diff(rp)), col)
+        t_hs = time.perf_counter() - t_hs          # the model's H and S: input, not timed
         Hd, Sd = torch.from_numpy(H).cuda(), torch.from_numpy(S).cuda()
         ctx = lsq.Lnv(g, B, R_S, R_H, R_L)
         Xi = torch.zeros((g.nnzb(rL), B, B), dtype=f64, device="cuda")
@@ -260,6 +270,7 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
             lsq.pattern_remap(gp, gp.range_id(R_L), g, rL, B, Lp_prev, Lprev)
             Lon = torch.zeros_like(L)
             ctx.init_L(Sd, Lon)
+            xl_start = L.clone()
             for name, Ls in (("previous_L", Lprev), ("onsite", Lon), ("xl", L)):
                 rep = ctx.minimise(Ls, Sd, Hd, MU, max_iter=300, tol_ha_per_atom=tol, precision=lsq.F32)
                 its[name].append(int(rep["iterations"]))
@@ -270,6 +281,28 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
         if n == 0:
             hist = [LS.clone() for _ in range(K + 1)]
         prev = (g, ctx, hist, LS, L)
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t_step - t_hs)
+    # the last MD step's S^-1 and XL-started CG on a fresh geometry of the same positions, with
+    # the schedules adopted from the previous geometry and with its own tuning run
+    ab = {}
+    for adopt in (True, False):
+        g2 = lsq.Geometry(torch.from_numpy(traj[n_md]).cuda(), cell, ranges)
+        if adopt:
+            g2.adopt_schedules(prev[0])
+        ctx2 = lsq.Lnv(g2, B, R_S, R_H, R_L)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xi2 = torch.zeros((g2.nnzb(g2.range_id(R_L)), B, B), dtype=f64, device="cuda")
+        rs2, rl2, rls2 = g2.range_id(R_S), g2.range_id(R_L), g2.range_id(R_L + R_S)
+        lsq.hotelling_inverse(g2, B, Sd, rs2, Xi2, rl2, rls2, 12, precision=lsq.F32)
+        lsq.hotelling_inverse(g2, B, Sd, rs2, Xi2, rl2, rls2, 2, precision=lsq.F64, start=False)
+        L2 = xl_start.clone() if xl_start is not None else torch.zeros_like(prev[4])
+        ctx2.minimise(L2, Sd, Hd, MU, max_iter=300, tol_ha_per_atom=tol, precision=lsq.F32)
+        torch.cuda.synchronize()
+        ab["adopted_schedules_s" if adopt else "own_tuning_s"] = time.perf_counter() - t0
+        ctx2.close()
+        g2.close()
     m_ls = prev[0].nnzb(prev[0].range_id(R_L + R_S)) * B * B
     prev[1].close()
     prev[0].close()
@@ -284,6 +317,8 @@ def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
             "xl_ms_per_md_step": mean(xl_ms), "propagate_ms": mean(prop_ms),
             "move_history_ms": mean(move_ms), "initial_L_ms": mean(init_ms),
             "propagate_gbs": bw(prop_bytes, mean(prop_ms)), "move_history_gbs": bw(move_bytes, mean(move_ms)),
+            "md_step_wall_s": wall,
+            "last_step_sinv_and_cg_s": ab,
             "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind,
             "dissipation": {"K": K, "kappa": kappa, "alpha": alpha, "c": list(c)},
             "workload": ("4096-atom Si moving along a prescribed seeded trajectory (0.05 A "

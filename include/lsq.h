@@ -382,6 +382,20 @@ int lsq_lnv_minimise_batch(lsq_lnv ctx, double *L_dev, const double *S_dev, cons
                            const double *mu_host, const lsq_lnv_opts *opts, lsq_lnv_report *reps,
                            void *stream);
 
+/*
+ * Lets g_to use the kernel schedules the product autotuner chose in g_from
+ * (and those g_from adopted in turn), for the plans of the same (range_a,
+ * range_b, range_c, triangle): a plan of g_to that has not been tuned then
+ * runs the adopted schedule instead of timing every schedule on its first
+ * call.  Meant for a sequence of geometries of one system (MD steps), whose
+ * products have the same shape.  A schedule whose alignment or shared
+ * memory the operands do not allow falls back to the adopted 16-byte
+ * schedule, as a tuned one does.  Both geometries must hold the same range
+ * list (LSQ_ERR_INVALID_ARG otherwise); the atom counts may differ.  Host
+ * only, no device work; g_from may be destroyed afterwards.
+ */
+int lsq_geom_adopt_schedules(lsq_geom g_to, lsq_geom g_from);
+
 /* ---- density matrix between MD steps (Sec. 3.3) ---------------------- */
 
 /*

@@ -89,6 +89,7 @@ def load():
         "lsq_lnv_init_purify": (I, [P, P, P, D, I, P, I, I, I, P, P, P]),
         "lsq_lnv_minimise_canonical": (I, [P, P, P, P, D, P, P, P, P]),
         "lsq_pattern_remap": (I, [P, I, P, I, I, I, P, P, P]),
+        "lsq_geom_adopt_schedules": (I, [P, P]),
         "lsq_xl_propagate": (I, [P, I, I, I, P, P, D, D, P, I, P, P]),
         "lsq_xl_initial_L": (I, [P, I, I, I, P, I, P, I, P, P]),
     }
@@ -109,7 +110,8 @@ def exported_symbols():
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
             "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
-            "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L"]
+            "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L",
+            "lsq_geom_adopt_schedules"]
 
 
 def launch_count():
@@ -196,6 +198,10 @@ class Geometry:
         col = torch.empty(max(nnzb, 1), dtype=torch.int32, device="cuda")
         _check(_lib.lsq_pattern_copy(self.handle, r, _dev(rp), _dev(col), _stream(stream)))
         return rp, col[:nnzb]
+
+    def adopt_schedules(self, other):
+        """Use the product schedules tuned in another geometry of the same ranges."""
+        _check(load().lsq_geom_adopt_schedules(self.handle, other.handle))
 
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <atomic>
 #include <map>
 #include <string>
@@ -131,6 +132,9 @@ struct lsq_geom_s {
     std::map<std::tuple<int, int, int>, lsq::DevBuf<int64_t>> posmaps;
     // product plans keyed by (range_a, range_b, range_c)
     std::map<std::tuple<int, int, int>, lsq::ProductPlan> pplans;
+    // schedules adopted from another geometry (lsq_geom_adopt_schedules), same keys:
+    // {variant f64, variant f32, variant16 f64, variant16 f32}; used by a plan not yet tuned
+    std::map<std::tuple<int, int, int>, std::array<int, 4>> schedule_hints;
     // scratch for transposed operands of lsq_block_matmul (grown on demand)
     lsq::DevBuf<char> scratch_a, scratch_x;
     // float32 operands and result of lsq_xl_initial_L (grown on demand)

@@ -627,6 +627,16 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
                 LSQ_TRY(transpose_on(g, rb, b, dtype, B, g->scratch_x.p, s));
                 X = g->scratch_x.p;
             }
+            const int di = dtype == LSQ_F64 ? 0 : 1;
+            if (pp->variant[di] < 0 && !g->schedule_hints.empty()) {
+                // a schedule adopted from a geometry of the same ranges: no tuning run
+                const int upper = sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0);
+                auto h = g->schedule_hints.find(std::make_tuple(ra, rb, rc + 1000 * upper));
+                if (h != g->schedule_hints.end() && h->second[di] >= 0) {
+                    pp->variant[di] = h->second[di];
+                    pp->variant16[di] = h->second[2 + di];
+                }
+            }
             return plan_launch(g, dtype, *pp, ra, rb, rc, Aop, X, C, alpha, beta, s, sym == 1);
         }
         if (prc != LSQ_ERR_OOM && prc != LSQ_ERR_UNSUPPORTED) return prc;
@@ -897,5 +907,32 @@ extern "C" int lsq_transpose(lsq_geom g, int b, int precision, int range_x, cons
         k_transpose_into<float><<<tgrid(nnzb * b * b), 256, 0, s>>>(nnzb, b, pm, (float)alpha,
                                                                      (const float *)X, (float *)out);
     LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
+extern "C" int lsq_geom_adopt_schedules(lsq_geom g_to, lsq_geom g_from) {
+    using namespace lsq;
+    clear_error();
+    if (!g_to || !g_from) return set_error(LSQ_ERR_INVALID_ARG, "null geometry handle");
+    if (g_to == g_from) return LSQ_OK;
+    if (g_to->n_ranges != g_from->n_ranges)
+        return set_error(LSQ_ERR_INVALID_ARG, "the geometries hold different range lists");
+    for (int r = 0; r < g_to->n_ranges; ++r)
+        if (g_to->pats[r].R != g_from->pats[r].R)
+            return set_error(LSQ_ERR_INVALID_ARG, "the geometries hold different range lists");
+    // the source's own hints first, then its tuned plans (which take precedence)
+    for (const auto &kv : g_from->schedule_hints) g_to->schedule_hints[kv.first] = kv.second;
+    for (const auto &kv : g_from->pplans) {
+        const ProductPlan &p = kv.second;
+        std::array<int, 4> h = {p.variant[0], p.variant[1], p.variant16[0], p.variant16[1]};
+        auto it = g_to->schedule_hints.find(kv.first);
+        if (it != g_to->schedule_hints.end())
+            for (int k = 0; k < 2; ++k)
+                if (h[k] < 0) {
+                    h[k] = it->second[k];
+                    h[2 + k] = it->second[2 + k];
+                }
+        g_to->schedule_hints[kv.first] = h;
+    }
     return LSQ_OK;
 }

@@ -171,3 +171,42 @@ def test_xl_md_run_matches_oracle():
             hist_o = [LS_o] * (K + 1)
             hist_g = [LS_g.clone() for _ in range(K + 1)]
         prev = (g, m)
+
+
+def test_adopted_schedules_skip_tuning():
+    """lsq_geom_adopt_schedules: a geometry of the next MD step runs the schedules tuned in
+    the previous one (far fewer launches on its first product: no tuning run), with results
+    that still match the oracle."""
+    pos, cell = si(3, 0.05, config_seed(0) + 6)
+    traj = md_trajectory(pos, cell, 3, seed=29)
+    ranges = [6.6, 10.0, 16.6]
+    P1 = {R: oracle.neighbour_list(traj[3], cell, R) for R in ranges}
+    rng = np.random.default_rng(9)
+    A = oracle.Bsr(P1[10.0], 4, rng.standard_normal((P1[10.0].nnzb, 4, 4)))
+    Bm = oracle.Bsr(P1[6.6], 4, rng.standard_normal((P1[6.6].nnzb, 4, 4)))
+    ref, _ = oracle.matmul(A, Bm, P1[16.6])
+    bound, _ = oracle.matmul(oracle.Bsr(P1[10.0], 4, np.abs(A.val)), oracle.Bsr(P1[6.6], 4, np.abs(Bm.val)),
+                             P1[16.6])
+
+    def first_product(g):
+        C = torch.zeros((P1[16.6].nnzb, 4, 4), dtype=torch.float32, device="cuda")
+        n0 = lsq.launch_count()
+        lsq.block_matmul(g, 4, cuda(A.val, torch.float32), 1, cuda(Bm.val, torch.float32), 0, C, 2,
+                         precision=lsq.F32)
+        torch.cuda.synchronize()
+        got = C.double().cpu().numpy()
+        assert np.abs(got - ref.val).max() <= 1e-5 * bound.val.max()
+        return lsq.launch_count() - n0
+
+    g0 = gpu_geometry(traj[0], cell, ranges)
+    Cg = torch.zeros((g0.nnzb(2), 4, 4), dtype=torch.float32, device="cuda")
+    lsq.block_matmul(g0, 4, torch.ones((g0.nnzb(1), 4, 4), dtype=torch.float32, device="cuda"), 1,
+                     torch.ones((g0.nnzb(0), 4, 4), dtype=torch.float32, device="cuda"), 0, Cg, 2,
+                     precision=lsq.F32)                     # tunes g0's plan
+    tuned = first_product(gpu_geometry(traj[3], cell, ranges))
+    g1 = gpu_geometry(traj[3], cell, ranges)
+    g1.adopt_schedules(g0)
+    adopted = first_product(g1)
+    assert adopted + 20 < tuned, (adopted, tuned)
+    with pytest.raises(lsq.LsqError):
+        gpu_geometry(traj[3], cell, [6.6, 10.0]).adopt_schedules(g0)
