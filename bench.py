@@ -59,9 +59,10 @@ def parse():
     p.add_argument("--workload", default="si4096", choices=["si4096", "batch", "sizes"],
                    help="si4096: the 4096-atom headline (default); batch: the 48-system batched "
                         "workload (24 systems with 4x4 blocks, 24 with 13x13)")
-    p.add_argument("--only-product", nargs="?", const="sl_qt", choices=["sl_qt", "ls_l"],
-                   help="run only one product three times (for profilers): sl_qt, the roofline "
-                        "product (default), or ls_l, the bsgemm product")
+    p.add_argument("--only-product", nargs="?", const="sl_qt", choices=["sl_qt", "ls_l", "xl"],
+                   help="run only one kernel three times (for profilers): sl_qt, the roofline "
+                        "product (default), ls_l, the bsgemm product, or xl, the XL-BOMD "
+                        "propagation of X with dissipation (1728 atoms: 8 arrays of 210 MB)")
     return p.parse_args()
 
 
@@ -770,8 +771,30 @@ def run_sizes(args):
                       "sizes": out}))
 
 
+def run_only_xl():
+    """Three launches of lsq_xl_propagate (six history entries, the K = 5 dissipation) on L S's
+    range of 1728-atom Si (6x6x6 cells), random arrays; for profilers."""
+    import torch
+    import paper_2002_07704_gb300 as lsq
+    lsq.build()
+    lsq.load()
+    pos, cell = diamond_si_positions(6, SIGMA, config_seed(1))
+    g = lsq.Geometry(torch.from_numpy(pos).cuda(), cell, lsq.lnv_required_ranges(R_S, R_H, R_L))
+    r = g.range_id(R_L + R_S)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    A = [torch.randn((g.nnzb(r), B, B), dtype=torch.float64, device="cuda", generator=gen) for _ in range(8)]
+    kappa, alpha, c = lsq.XL_DISSIPATION_K5
+    for _ in range(3):
+        lsq.xl_propagate(g, B, r, A[:6], A[6], A[7], kappa, alpha, c)
+    torch.cuda.synchronize()
+    print("only-product xl done: %d values per array" % A[0].numel())
+
+
 def main():
     args = parse()
+    if args.only_product == "xl":
+        run_only_xl()
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
