@@ -78,9 +78,9 @@ struct XlArgs {
 // The Verlet step with dissipation, its terms grouped by history entry,
 //   X(t + dt) = kappa LS + (2 - kappa + a c_0) X(t) + (-1 + a c_1) X(t - dt) + sum_{m>=2} a c_m X(t - m dt),
 // one FMA per entry.  The FP64 pipe, not HBM, bounds this kernel on this GPU (with six
-// history entries, seven FP64 instructions per 64 bytes moved against a ridge near 0.08 per
-// byte), so the grouping (under half the FP64 instructions of the formula evaluated term by
-// term) sets its speed.  The
+// history entries, about eleven FP64 instructions per 64 bytes moved against a ridge near
+// 0.08 per byte; the pipe is 83 % busy while DRAM runs at 38 % of its peak), so the grouping
+// (about half the FP64 instructions of the formula evaluated term by term) sets its speed.  The
 // history loop is unrolled over the fixed maximum (predicated by nh), so the argument arrays
 // are indexed statically and all loads of a value issue together; V values per thread
 // (16-byte loads for V = 2).  out may be one of the history arrays: each value is read
