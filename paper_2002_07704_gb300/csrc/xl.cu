@@ -78,14 +78,13 @@ struct XlArgs {
 // The Verlet step with dissipation, its terms grouped by history entry,
 //   X(t + dt) = kappa LS + (2 - kappa + a c_0) X(t) + (-1 + a c_1) X(t - dt) + sum_{m>=2} a c_m X(t - m dt),
 // one FMA per entry.  The FP64 pipe, not HBM, bounds this kernel on this GPU (with six
-// history entries, about eleven FP64 instructions per 64 bytes moved against a ridge near
-// 0.08 per byte; the pipe is 83 % busy while DRAM runs at 38 % of its peak), so the grouping
-// (about half the FP64 instructions of the formula evaluated term by term) sets its speed.  The
-// history loop is unrolled over the fixed maximum (predicated by nh), so the argument arrays
-// are indexed statically and all loads of a value issue together; V values per thread
-// (16-byte loads for V = 2).  out may be one of the history arrays: each value is read
-// before it is written, by the same thread.
-template <int V>
+// history entries, seven FP64 instructions per 64 bytes moved against a ridge near 0.08 per
+// byte), so every FP64 instruction counts: the terms are grouped (about half the FP64
+// instructions of the formula evaluated term by term) and the history length NH is a template
+// argument (a loop unrolled to a fixed maximum and predicated still issues its idle FMAs).  All
+// loads of a value issue together; V values per thread (16-byte loads for V = 2).  out may be
+// one of the history arrays: each value is read before it is written, by the same thread.
+template <int V, int NH>
 __device__ __forceinline__ void xl_values(const XlArgs &a, int64_t e) {
     using VT = typename std::conditional<V == 2, double2, double>::type;
     auto ld = [&](const double *p) { return *reinterpret_cast<const VT *>(p + e); };
@@ -93,31 +92,45 @@ __device__ __forceinline__ void xl_values(const XlArgs &a, int64_t e) {
         if constexpr (V == 2) return j == 0 ? x.x : x.y;
         else return x;
     };
-    VT xk[kMaxHist];
+    VT xk[NH];
     const VT ls = ld(a.LS);
 #pragma unroll
-    for (int k = 0; k < kMaxHist; ++k)
-        if (k < a.nh) xk[k] = ld(a.X[k]);
+    for (int k = 0; k < NH; ++k) xk[k] = ld(a.X[k]);
     double o[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
         double r = a.kappa * part(ls, j);
 #pragma unroll
-        for (int k = 0; k < kMaxHist; ++k)
-            if (k < a.nh) r = fma(a.w[k], part(xk[k], j), r);
+        for (int k = 0; k < NH; ++k) r = fma(a.w[k], part(xk[k], j), r);
         o[j] = r;
     }
     if constexpr (V == 2) *reinterpret_cast<double2 *>(a.out + e) = make_double2(o[0], o[1]);
     else a.out[e] = o[0];
 }
 
-template <int V>
+template <int V, int NH>
 __global__ void __launch_bounds__(256) k_xl_propagate(XlArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * V;
     const int64_t mv = a.m / V * V;
-    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; e < mv; e += stride) xl_values<V>(a, e);
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V; e < mv; e += stride)
+        xl_values<V, NH>(a, e);
     // the odd tail value (V = 2, m odd)
-    if (V == 2 && blockIdx.x == 0 && threadIdx.x == 0 && mv < a.m) xl_values<1>(a, mv);
+    if (V == 2 && blockIdx.x == 0 && threadIdx.x == 0 && mv < a.m) xl_values<1, NH>(a, mv);
+}
+
+template <int V>
+void launch_propagate(const XlArgs &a, int grid, cudaStream_t s) {
+    switch (a.nh) {
+    case 2: k_xl_propagate<V, 2><<<grid, 256, 0, s>>>(a); break;
+    case 3: k_xl_propagate<V, 3><<<grid, 256, 0, s>>>(a); break;
+    case 4: k_xl_propagate<V, 4><<<grid, 256, 0, s>>>(a); break;
+    case 5: k_xl_propagate<V, 5><<<grid, 256, 0, s>>>(a); break;
+    case 6: k_xl_propagate<V, 6><<<grid, 256, 0, s>>>(a); break;
+    case 7: k_xl_propagate<V, 7><<<grid, 256, 0, s>>>(a); break;
+    case 8: k_xl_propagate<V, 8><<<grid, 256, 0, s>>>(a); break;
+    case 9: k_xl_propagate<V, 9><<<grid, 256, 0, s>>>(a); break;
+    default: k_xl_propagate<V, 10><<<grid, 256, 0, s>>>(a); break;
+    }
 }
 
 // X = (X + X^T) / 2 in place on a symmetric pattern: the thread of the entry with p <= tm[p]
@@ -228,9 +241,9 @@ extern "C" int lsq_xl_propagate(lsq_geom g, int b, int range_x, int n_hist, cons
     for (int k = 0; k < a.nh; ++k) al16 = al16 && reinterpret_cast<uintptr_t>(X_hist[k]) % 16 == 0;
     note_launch();
     if (al16)
-        k_xl_propagate<2><<<grid_of((m + 1) / 2), 256, 0, (cudaStream_t)stream>>>(a);
+        launch_propagate<2>(a, grid_of((m + 1) / 2), (cudaStream_t)stream);
     else
-        k_xl_propagate<1><<<grid_of(m), 256, 0, (cudaStream_t)stream>>>(a);
+        launch_propagate<1>(a, grid_of(m), (cudaStream_t)stream);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
