@@ -224,6 +224,7 @@ extern "C" int lsq_xl_propagate(lsq_geom g, int b, int range_x, int n_hist, cons
         a.X[k] = X_hist[k];
     }
     if (!LS || !X_next) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
+    if (X_next == LS) return set_error(LSQ_ERR_INVALID_ARG, "X_next must not alias LS");
     // weights of the history entries: 2 - kappa and -1 from the Verlet step, a c_m from the
     // dissipation; entries beyond both are not read
     const int nc = alpha != 0.0 ? n_c : 0;
