@@ -22,8 +22,10 @@ from synth import config_seed, md_trajectory, sk_blocks
 
 pytestmark = pytest.mark.gpu
 
-KAPPA, ALPHA = 1.82, 0.018
-C5 = [-6.0, 14.0, -8.0, -3.0, 4.0, -1.0]
+from test_oracle_xl import read_dissipation
+
+KAPPA, ALPHA, _C = read_dissipation()
+C5 = [float(v) for v in _C]
 
 
 @pytest.mark.parametrize("b,prec", [(4, lsq.F64), (4, lsq.F32), (13, lsq.F64)])

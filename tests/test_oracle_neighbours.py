@@ -1,5 +1,7 @@
 """Pins of the oracle's range patterns (Sec. 2.3.2: elements are zero when
 the inter-atomic distance exceeds the cutoff)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -40,17 +42,18 @@ def test_pattern_is_the_distance_set_sorted_symmetric():
         assert np.all(np.diff(c) > 0)
 
 
-# Coordination shells of the diamond lattice, radius in units of a:
-# sqrt(3)/4 (4 atoms), sqrt(2)/2 (12), sqrt(11)/4 (12), 1 (6), sqrt(19)/4 (12).
-SHELLS = [(np.sqrt(3) / 4, 4), (np.sqrt(2) / 2, 12), (np.sqrt(11) / 4, 12), (1.0, 6), (np.sqrt(19) / 4, 12)]
+# Coordination shells of the diamond lattice (tests/golden/diamond_shells.txt): radius in units
+# of a, atoms in the shell.
+_G = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "diamond_shells.txt"))
+SHELLS = [(np.sqrt(r2 / 16.0), int(c)) for r2, c in _G]
 
 
 @pytest.mark.parametrize("k", range(len(SHELLS)))
 def test_perfect_crystal_shell_counts(k):
     a = 5.431
-    pos, cell = diamond_si_positions(4, 0.0, 0)
+    pos, cell = diamond_si_positions(4, 0.0, 0)       # half the cell edge: 10.9 A
     r_lo = SHELLS[k][0] * a
-    r_hi = SHELLS[k + 1][0] * a if k + 1 < len(SHELLS) else 1.2 * a
+    r_hi = SHELLS[k + 1][0] * a if k + 1 < len(SHELLS) else 1.03 * r_lo
     R = 0.5 * (r_lo + r_hi)
     expect = 1 + sum(c for _, c in SHELLS[:k + 1])
     p = oracle.neighbour_list(pos, cell, R, "cell")

@@ -7,6 +7,8 @@ pair matching of a matrix moved between the patterns of two geometries, and
 dense algebra for the initial L (X S^-1 = L at the centre; masked dense
 product when truncated).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -15,9 +17,31 @@ from oracle import lnv as OL
 from oracle import xl as OX
 from synth import config_seed, diamond_si_positions, md_trajectory, sk_blocks
 
-# a dissipation set of the form the paper's cited scheme tabulates (sum c_m = sum m c_m = 0)
-KAPPA, ALPHA = 1.82, 0.018
-C5 = np.array([-6.0, 14.0, -8.0, -3.0, 4.0, -1.0])
+
+def read_dissipation():
+    """(kappa, alpha, c) from tests/golden/xl_dissipation_k5.txt (the cited table's K = 5 row)."""
+    vals = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "xl_dissipation_k5.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, *rest = line.split()
+            vals[key] = [float(x) for x in rest]
+    return vals["kappa"][0], vals["alpha"][0], np.array(vals["c"])
+
+
+KAPPA, ALPHA, C5 = read_dissipation()
+
+
+def test_dissipation_coefficients_annihilate_constant_and_linear_histories():
+    m = np.arange(len(C5), dtype=float)
+    assert np.sum(C5) == 0.0 and np.sum(m * C5) == 0.0
+    assert 0.0 < KAPPA < 4.0                      # the undamped Verlet recursion is stable
+
+
+def test_binding_default_is_the_golden_row():
+    import paper_2002_07704_gb300 as lsq
+    kappa, alpha, c = lsq.XL_DISSIPATION_K5
+    assert (kappa, alpha) == (KAPPA, ALPHA) and np.array_equal(np.array(c), C5)
 
 
 def _rand_bsr(pat, b, rng):
