@@ -47,10 +47,15 @@ extern "C" {
 #define LSQ_ERR_UNSTABLE       5   /* LNV: no local minimum along the line */
 #define LSQ_ERR_NOT_CONVERGED  6   /* LNV: iteration limit reached (L holds the last iterate) */
 #define LSQ_ERR_UNSUPPORTED    7   /* size beyond a documented kernel limit */
+#define LSQ_ERR_TIMEOUT        8   /* a bounded wait inside a kernel expired (see lsq_device_status) */
 
 /* ---- precisions of block products ----------------------------------- */
 #define LSQ_F64    0   /* float64 storage, FP64 FMA */
 #define LSQ_F32    1   /* float32 storage, FP32 FMA */
+#define LSQ_TF32X3 2   /* float32 storage; 4 x 4 blocks multiplied on the tensor cores with
+                          split operands: v = hi + lo, hi = tf32(v), lo = tf32(v - hi) (22
+                          bits of v), the products hi.hi + hi.lo + lo.hi (and lo.lo)
+                          accumulated in FP32; other block sizes as LSQ_F32 */
 
 typedef struct lsq_geom_s *lsq_geom;
 typedef struct lsq_lnv_s *lsq_lnv;
@@ -169,6 +174,25 @@ int lsq_block_matmul_tri(lsq_geom g, int b, int precision,
                          int range_b, int trans_b, const void *B_dev,
                          int range_c, void *C_dev, double alpha, double beta, int triangle,
                          int64_t *n_triples_host, void *stream);
+
+/*
+ * With precision LSQ_TF32X3 and b = 4, lsq_block_matmul(_tri) runs the tensor-core product:
+ * atoms i in groups of 8 and the atoms j of their rows of C in tiles of 16; per tile the
+ * blocks of op(B)^T and op(A) over the union of the group's rows of op(A) are gathered into
+ * shared memory by bulk asynchronous copies and contracted by tcgen05.mma (kind::tf32) into
+ * a float32 accumulator in tensor memory.  op(A) and op(B)^T are first copied in split form
+ * (a 128-byte hi/lo unit per block) into buffers held by g and grown on demand; the plan of
+ * the first call for a (range_a, range_b, range_c, triangle) allocates and synchronises.
+ * Arrays need only float alignment.  Limits: rows of at most 65534 blocks and at most
+ * 2^31 - 1 blocks in C (LSQ_ERR_UNSUPPORTED).  The kernel bounds every wait on its
+ * pipeline barriers (1 s); if one expires it records an error in g and returns early, and
+ * lsq_device_status reports it.  Calls on different streams race on the split buffers.
+ */
+
+/* Synchronises stream and reports the device error word of g: LSQ_OK, or LSQ_ERR_TIMEOUT
+ * when a kernel with bounded waits (the LSQ_TF32X3 product) gave up since the last check
+ * (the word is then cleared; the results of that launch are not valid). */
+int lsq_device_status(lsq_geom g, void *stream);
 
 /* out = alpha X^T on pattern range_out: out_ij = alpha (X_ji)^T where (j, i)
  * is stored in X's pattern, zero elsewhere (the adjoint of a trace and of a

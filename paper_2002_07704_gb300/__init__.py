@@ -16,10 +16,11 @@ from ._build import LIB, build  # noqa: F401
 
 F64 = 0
 F32 = 1
+TF32X3 = 2   # float32 storage, 4 x 4 blocks on the tensor cores in split TF32
 HARTREE_EV = 27.211386245988
 
 ERRORS = {1: "INVALID_ARG", 2: "PATTERN", 3: "OOM", 4: "CUDA", 5: "UNSTABLE",
-          6: "NOT_CONVERGED", 7: "UNSUPPORTED"}
+          6: "NOT_CONVERGED", 7: "UNSUPPORTED", 8: "TIMEOUT"}
 
 _lib = None
 
@@ -92,6 +93,7 @@ def load():
         "lsq_geom_adopt_schedules": (I, [P, P]),
         "lsq_xl_propagate": (I, [P, I, I, I, P, P, D, D, P, I, P, P]),
         "lsq_xl_initial_L": (I, [P, I, I, I, P, I, P, I, P, P]),
+        "lsq_device_status": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -111,7 +113,7 @@ def exported_symbols():
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
             "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
             "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L",
-            "lsq_geom_adopt_schedules"]
+            "lsq_geom_adopt_schedules", "lsq_device_status"]
 
 
 def launch_count():
@@ -198,6 +200,10 @@ class Geometry:
         col = torch.empty(max(nnzb, 1), dtype=torch.int32, device="cuda")
         _check(_lib.lsq_pattern_copy(self.handle, r, _dev(rp), _dev(col), _stream(stream)))
         return rp, col[:nnzb]
+
+    def device_status(self, stream=None):
+        """Raises LsqError(TIMEOUT) if a kernel with bounded waits gave up since the last check."""
+        _check(load().lsq_device_status(self.handle, _stream(stream)))
 
     def adopt_schedules(self, other):
         """Use the product schedules tuned in another geometry of the same ranges."""

@@ -104,6 +104,28 @@ struct ProductPlan {
     ProductPlan(ProductPlan &&) = default;
 };
 
+// Tensor-core plan of a truncated 4 x 4 product (see tc.cu): atoms i in groups of 8, the
+// atoms j of each group's rows of C in tiles of 16, and per tile a list of atoms k (the
+// union of the group's rows of op(A), restricted to atoms in the tile's rows of op(B)^T).
+// Tile t runs on CTA t % grid; the block indices each CTA gathers form one stream of stage
+// records (24 rows x 16 blocks, -1 for a block its row does not hold).
+struct TcPlan {
+    int ngroups = 0;
+    int ntiles = 0;
+    int grid = 0;                // CTAs the plan was laid out for
+    int upper = 0;
+    int64_t triples = 0;         // exact block triples of the computed blocks of C
+    int64_t units = 0;           // operand blocks gathered per launch (incl. zero fills)
+    int64_t dense_triples = 0;   // block triples the MMAs execute (incl. zero blocks)
+    DevBuf<int32_t> tile_nk;     // [ntiles] k-list length (a multiple of 16)
+    DevBuf<int64_t> tile_posoff; // [ntiles] first stage record of the tile
+    DevBuf<int32_t> cta_stages;  // [grid] stages of each CTA
+    DevBuf<int32_t> pos;         // stage records: block indices in op(A) or op(B)^T, or -1
+    DevBuf<int32_t> cpos;        // [128 ntiles]: block (i, j) of C, -1 if not computed
+    TcPlan() = default;
+    TcPlan(TcPlan &&) = default;
+};
+
 struct Reducer {
     DevBuf<double> partial;   // per-block partial sums
     DevBuf<double> scalars;   // result slots
@@ -137,6 +159,12 @@ struct lsq_geom_s {
     std::map<std::tuple<int, int, int>, std::array<int, 4>> schedule_hints;
     // scratch for transposed operands of lsq_block_matmul (grown on demand)
     lsq::DevBuf<char> scratch_a, scratch_x;
+    // tensor-core plans keyed by (range_a, range_b, range_c + 1000 * triangle), the split
+    // (hi, lo) operand copies they read (grown on demand), and the device error word of the
+    // kernels with bounded waits (0: none)
+    std::map<std::tuple<int, int, int>, lsq::TcPlan> tcplans;
+    lsq::DevBuf<char> tc_a, tc_x;
+    lsq::DevBuf<int> dev_err;
     // float32 operands and result of lsq_xl_initial_L (grown on demand)
     lsq::DevBuf<char> xl_scratch;
     lsq::Reducer red;
@@ -186,6 +214,17 @@ int sum_into(lsq_geom g, const double *x, int64_t m, int slot, cudaStream_t s);
 int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s);
 
 inline size_t dtype_size(int dtype) { return dtype == LSQ_F64 ? 8 : 4; }
+
+// Exact block triples of a product restricted to a triangle (upper: 0 all, 1 j >= i, 2 j <= i).
+int plan_count_triples(lsq_geom g, int ra, int rb, int rc, int upper, int64_t *out, cudaStream_t s);
+// Lower blocks of a symmetric 4 x 4 result from the upper ones (pattern rc).
+int mirror_lower4(lsq_geom g, int rc, int dtype, void *C, cudaStream_t s);
+// Device error word of g (allocated and cleared on first use).
+int dev_err_ptr(lsq_geom g, int **out);
+// Tensor-core truncated 4 x 4 product in split TF32 (see tc.cu); float32 operands and result.
+int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, const float *B, int rc,
+                    float *C, double alpha, double beta, int upper, bool mirror, int64_t *triples,
+                    cudaStream_t s);
 
 #ifdef __CUDACC__
 // Error-free float32 sum (Knuth's TwoSum): s = fl(a + b) and s + e = a + b exactly.

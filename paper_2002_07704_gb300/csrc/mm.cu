@@ -580,10 +580,20 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     LSQ_TRY(geom_check(g, rb));
     LSQ_TRY(geom_check(g, rc));
     if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
-    if (dtype != LSQ_F64 && dtype != LSQ_F32)
-        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    if (dtype != LSQ_F64 && dtype != LSQ_F32 && dtype != LSQ_TF32X3)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64, LSQ_F32 or LSQ_TF32X3");
     if (g->n > 0 && (!A || !B || !C)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
     if (C == A || C == B) return set_error(LSQ_ERR_INVALID_ARG, "C must not alias A or B");
+    if (dtype == LSQ_TF32X3) {
+        // float32 storage; 4 x 4 blocks contract on the tensor cores in split TF32, other block
+        // sizes on the float32 FMA kernels
+        if (b == 4) {
+            const int upper = sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0);
+            return tc_block_matmul(g, ra, ta, static_cast<const float *>(A), rb, tb, static_cast<const float *>(B),
+                                   rc, static_cast<float *>(C), alpha, beta, upper, sym == 1, triples, s);
+        }
+        dtype = LSQ_F32;
+    }
     // transposed operands and MODE_INNER read through transpose maps
     LSQ_TRY(ensure_tmap(g, ra, s));
     LSQ_TRY(ensure_tmap(g, rb, s));

@@ -791,6 +791,64 @@ int mirror_lower_gen(lsq_geom g, int rc, int b, int dtype, void *C, cudaStream_t
     return LSQ_OK;
 }
 
+__global__ void k_sum_cnt(int64_t m, const int32_t *__restrict__ cnt, unsigned long long *__restrict__ out) {
+    unsigned long long s = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        s += (unsigned long long)cnt[e];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+int plan_count_triples(lsq_geom g, int ra, int rb, int rc, int upper, int64_t *out, cudaStream_t s) {
+    const Pattern &PA = g->pats[ra], &PB = g->pats[rb], &PC = g->pats[rc];
+    const int n = g->n;
+    *out = 0;
+    if (n == 0 || PC.nnzb == 0) return LSQ_OK;
+    auto it = g->pplans.find(std::make_tuple(ra, rb, rc + 1000 * upper));
+    if (it != g->pplans.end()) {
+        *out = it->second.triples;
+        return LSQ_OK;
+    }
+    if ((size_t)n * sizeof(int) + 1024 > g->smem_optin)
+        return set_error(LSQ_ERR_UNSUPPORTED, "too many atoms for the shared-memory atom map");
+    DevBuf<int32_t> cnt;
+    DevBuf<unsigned long long> tot;
+    LSQ_TRY(cnt.alloc(PC.nnzb));
+    LSQ_TRY(tot.alloc(1));
+    const size_t smem_map = (size_t)n * sizeof(int);
+    LSQ_CUDA_TRY(cudaFuncSetAttribute(k_plan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_map));
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_count, 512, smem_map);
+    const int grid_rows = std::max(1, std::min(n, g->num_sms * std::max(per_sm, 1)));
+    LSQ_CUDA_TRY(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long), s));
+    note_launch();
+    k_plan_count<<<grid_rows, 512, smem_map, s>>>(n, PA.row_ptr.p, PA.col.p, PB.row_ptr.p, PB.col.p,
+                                                  PC.row_ptr.p, PC.col.p, upper, cnt.p);
+    note_launch();
+    k_sum_cnt<<<(int)std::min<int64_t>((PC.nnzb + 255) / 256, (int64_t)g->num_sms * 8), 256, 0, s>>>(
+        PC.nnzb, cnt.p, tot.p);
+    LSQ_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    LSQ_CUDA_TRY(cudaMemcpyAsync(&h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = (int64_t)h;
+    return LSQ_OK;
+}
+
+int mirror_lower4(lsq_geom g, int rc, int dtype, void *C, cudaStream_t s) {
+    LSQ_TRY(ensure_tmap(g, rc, s));
+    const int64_t m = g->pats[rc].nnzb * 16;
+    if (m == 0) return LSQ_OK;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16));
+    note_launch();
+    if (dtype == LSQ_F64)
+        k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (double *)C);
+    else
+        k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (float *)C);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
+
 __global__ void k_rows_of(int n, const int64_t *__restrict__ c_ptr, int64_t *__restrict__ c_row) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
