@@ -49,16 +49,20 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=10)
+    p.add_argument("--tol", type=float, default=1e-6,
+                   help="|dOmega|/N (Ha/atom) at which the to-tolerance runs stop")
+    p.add_argument("--no-tol", action="store_true", help="skip the runs to tolerance")
     p.add_argument("--cpu-sample-rows", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--md-steps", type=int, default=8,
                    help="extended-Lagrangian MD steps of the 4096-atom system (0: skip)")
     p.add_argument("--cells", default="4,6,8,10,12,16",
                    help="--workload sizes: diamond cells per edge of each system (8 n^3 atoms)")
-    p.add_argument("--workload", default="si4096", choices=["si4096", "batch", "sizes"],
+    p.add_argument("--workload", default="si4096", choices=["si4096", "batch", "sizes", "oracle"],
                    help="si4096: the 4096-atom headline (default); batch: the 48-system batched "
-                        "workload (24 systems with 4x4 blocks, 24 with 13x13)")
+                        "workload (24 systems with 4x4 blocks, 24 with 13x13); oracle: the CPU "
+                        "oracle timed on the host cores (1 thread and all), no GPU")
     p.add_argument("--only-product", nargs="?", const="sl_qt", choices=["sl_qt", "ls_l", "xl"],
                    help="run only one kernel three times (for profilers): sl_qt, the roofline "
                         "product (default), ls_l, the bsgemm product, or xl, the XL-BOMD "
@@ -93,14 +97,36 @@ def oracle_step_seconds(pos, cell, rows_per_step, seed):
     return mm * n / rows_per_step + (total - mm), total
 
 
+def host_cpu():
+    """(cores, model name) of this host."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model", "hardware")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count(), model
+
+
 def run_reference(args):
+    """The oracle on this host's cores, on the 4096-atom workload: each step is one oracle CG
+    step (energy, gradient, cubic) whose block products are restricted to a random sample of
+    rows and scaled by 4096 / rows (the products are row-separable), other work in full."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     pos, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1))
     import oracle
     oracle.build()
-    rows = max(1, args.cpu_sample_rows // 4)
+    oracle.build(openmp=True)
+    threads = oracle.use_threads(0)
+    ncpu, model = host_cpu()
+    rows = max(16, args.cpu_sample_rows)
     for w in range(args.warmup):
         oracle_step_seconds(pos, cell, rows, 1000 + w)
     est, wall = [], 0.0
@@ -110,15 +136,19 @@ def run_reference(args):
         wall += t
     sec = float(np.mean(est))
     v = 1.0 / sec
-    sample = ("oracle CG step with each block product restricted to %d of 4096 rows "
-              "(scaled by 4096/%d), other work in full; %d steps" % (rows, rows, args.steps))
+    sample = ("oracle CG step with each block product restricted to %d random rows of 4096 and "
+              "scaled by 4096/%d (an extrapolation, not a timed full step), other work in full; "
+              "%d steps, %.1f s of wall time in all" % (rows, rows, args.steps, wall))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "float64 oracle (CPU)"},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "extrapolated": {"rows_sampled": rows, "scale": 4096.0 / rows, "wall_s": wall,
+                             "note": "ms_per_step is the projected time of a full-size step, not "
+                                     "a measured one"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": threads, "kind": "oracle",
+                             "cpu_model": model, "host_cpus": ncpu, "sample": sample},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -197,11 +227,21 @@ class Clocks:
 ROOFLINE_PRODUCT = "sl_qt_upper_rl"
 
 
-def roofline_product(lsq, geom, SL, Q, out):
+def roofline_product(lsq, geom, SL, Q, out, precision=None):
     """The step's dominant product kernel: SL.Q^T on the upper triangle of L's range (the
     gradient terms and the line search's Z are products of this shape, three per step)."""
-    return lsq.block_matmul(geom, B, SL, 3, Q, 5, out, 2, precision=lsq.F32, trans_b=True,
-                            triangle=2)
+    return lsq.block_matmul(geom, B, SL, 3, Q, 5, out, 2, precision=lsq.F32 if precision is None else precision,
+                            trans_b=True, triangle=2)
+
+
+def tensor_peaks():
+    """(bf16, tf32) dense tensor TFLOP/s: the pool's measured cuBLAS bf16 burst, and tf32 at the
+    nominal tf32/bf16 ratio of GB300's dense tensor rates (1.1 / 2.25 PFLOP/s)."""
+    try:
+        bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        bf16 = 1900.0
+    return bf16, bf16 * 1.1 / 2.25
 def xl_md_section(lsq, torch, stream, n_md, tol=1e-6):
     """Extended-Lagrangian MD steps of the headline system (Sec. 3.3) along a prescribed
     trajectory: per MD step the geometry (adopting the previous geometry's product
@@ -349,6 +389,10 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # --- measured FMA rates of this GPU (roofline denominators of the FMA kernels) ---
+    ffma = lsq.measure_peak(lsq.F32)
+    dfma = lsq.measure_peak(lsq.F64)
+
     # --- workload (one replica per rank) ---
     pos, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1) + 1000 * rank)
     ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
@@ -426,6 +470,51 @@ def run_ours(args):
     om_d, _ = ctx.energy_gradient(L64, Sd, Hd, MU)
     acc = abs(om_m - om_d) / lsq.HARTREE_EV / geom.n_atoms
 
+    # --- mixed precision with LSQ_TF32X3: per product the faster of the FP32 FMA schedules and
+    # the split-TF32 tensor-core kernel (the first steps time both) ---
+    Lt = L0.clone()
+    steps(Lt, max(args.warmup, 2), lsq.TF32X3)
+    Lt = L0.clone()
+    barrier()
+    e0.record(stream)
+    rep_tc = steps(Lt, args.steps, lsq.TF32X3)
+    e1.record(stream)
+    barrier()
+    ms_tc = e0.elapsed_time(e1) / max(int(rep_tc["iterations"]), 1)
+    # the step's products (range ids: 0 R_S = R_H, 2 R_L, 3 R_L + R_S, 5 R_H + R_L + R_S) and the
+    # kernel the timing chose for each
+    STEP_PRODUCTS = [("L.S", 2, 0, 3, 0), ("SL.(Q+Q^T)^T lower", 3, 5, 2, 3), ("SL.Q^T upper", 3, 5, 2, 2),
+                     ("P = D.S", 2, 0, 3, 0), ("QD = H'.P", 0, 3, 5, 0), ("F = P.D", 3, 2, 5, 1),
+                     ("Z = P^T.QD^T", 3, 5, 2, 1)]
+    choices = {}
+    for name, ra_, rb_, rc_, tri in STEP_PRODUCTS:
+        try:
+            info = geom.product_plan_info(ra_, rb_, rc_, tri)
+            choices[name] = {-1: "untimed", 0: "fp32 fma", 1: "tensor cores"}[info["auto_choice"]]
+        except lsq.LsqError:
+            choices[name] = "fp32 fma (no tensor-core plan)"
+
+    # --- to the tolerance of the metric: CG until |dOmega|/N < tol, the mixed paths followed by
+    # their float64 refinement steps and a float64 final Omega; time to solution included ---
+    to_tol = None
+    if not args.no_tol:
+        to_tol = {"tol_ha_per_atom": args.tol}
+        for name, prec in (("fp64", lsq.F64), ("mixed_f32", lsq.F32), ("mixed_tf32x3", lsq.TF32X3)):
+            Lr = L0.clone()
+            barrier()
+            e0.record(stream)
+            r = ctx.minimise(Lr, Sd, Hd, MU, max_iter=300, tol_ha_per_atom=args.tol, precision=prec,
+                             refine_iter=2, final_eval=True)
+            e1.record(stream)
+            barrier()
+            to_tol[name] = {"iterations": int(r["iterations"]), "iterations_fp64": int(r["iterations_fp64"]),
+                            "status": int(r["status"]), "omega_ev": r["omega_ev"],
+                            "omega_ha_per_atom": r["omega_ha_per_atom"], "ne": r["ne"],
+                            "seconds": e0.elapsed_time(e1) / 1e3}
+        for name in ("mixed_f32", "mixed_tf32x3"):
+            to_tol[name]["vs_fp64_ha_per_atom"] = abs(to_tol[name]["omega_ev"] - to_tol["fp64"]["omega_ev"]) \
+                / lsq.HARTREE_EV / geom.n_atoms
+
     # --- dominant kernel: LS.L (row form) timed alone on the same stream ---
     dt = torch.float32
     Lc = L.to(dt)
@@ -445,7 +534,8 @@ def run_ours(args):
     flops = 2.0 * B ** 3 * trip
     hbm_peak, hbm_kind = measured_peaks()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+    fp32_nominal = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+    fp32_peak = ffma                                       # measured (lsq_measure_peak)
 
     # --- the step's dominant kernel, on the plan the step tuned ---
     Gx = torch.zeros((geom.nnzb(2), B, B), dtype=dt, device="cuda")
@@ -458,6 +548,30 @@ def run_ours(args):
     barrier()
     rms = e0.elapsed_time(e1) / reps
     rflops = 2.0 * B ** 3 * rtrip
+    # the same product on the tensor cores (LSQ_TF32X3), split conversions of both operands included
+    roofline_product(lsq, geom, LS, LSL, Gx, precision=lsq.TF32X3)
+    barrier()
+    e0.record(stream)
+    for _ in range(reps):
+        roofline_product(lsq, geom, LS, LSL, Gx, precision=lsq.TF32X3)
+    e1.record(stream)
+    barrier()
+    tms = e0.elapsed_time(e1) / reps
+    geom.device_status()
+    tinfo = geom.product_plan_info(3, 5, 2, 2)
+    bf16_peak, tf32_peak = tensor_peaks()
+    # the float64 path: algorithmic flops of one CG step (the step's products, Q formed afresh
+    # every tenth step) over the measured DFMA rate
+    step_trip = 0.0
+    for name, ra_, rb_, rc_, tri in STEP_PRODUCTS + [("Q = H'.LS", 0, 3, 5, 0)]:
+        Aa = torch.zeros((geom.nnzb(ra_), B, B), dtype=torch.float32, device="cuda")
+        Bb = torch.zeros((geom.nnzb(rb_), B, B), dtype=torch.float32, device="cuda")
+        Cc = torch.zeros((geom.nnzb(rc_), B, B), dtype=torch.float32, device="cuda")
+        t_ = lsq.block_matmul(geom, B, Aa, ra_, Bb, rb_, Cc, rc_, precision=lsq.F32, trans_b=True,
+                              triangle=tri)
+        step_trip += t_ / 10.0 if name.startswith("Q =") else t_
+        del Aa, Bb, Cc
+    fp64_step_flops = 2.0 * B ** 3 * step_trip
     # algorithmic bytes: A and B read once, the upper half of C written (float32)
     abytes = (geom.nnzb(3) + geom.nnzb(5) + geom.nnzb(2) / 2.0) * B * B * 4
     traffic = None
@@ -576,12 +690,22 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        sec, wall = oracle_step_seconds(pos, cell, args.cpu_sample_rows, 7)
-        cpu = {"value": 1.0 / sec, "unit": "steps/s", "cores": 1, "kind": "oracle",
+        oracle.build(openmp=True)
+        ncpu, model = host_cpu()
+        oracle.use_threads(1)
+        sec1, wall1 = oracle_step_seconds(pos, cell, args.cpu_sample_rows, 7)
+        nthr = oracle.use_threads(0)
+        rows_n = max(args.cpu_sample_rows, 4 * nthr)
+        secn, walln = oracle_step_seconds(pos, cell, rows_n, 7)
+        oracle.use_threads(1)
+        cpu = {"value": 1.0 / secn, "unit": "steps/s", "cores": nthr, "kind": "oracle", "cpu_model": model,
+               "host_cpus": ncpu,
                "sample": ("one oracle CG step (energy, gradient, cubic) with every block product "
-                          "restricted to %d random rows of 4096 and scaled by 4096/%d, other "
-                          "work timed in full; %.1f s of CPU" % (args.cpu_sample_rows,
-                                                                 args.cpu_sample_rows, wall))}
+                          "restricted to %d random rows of 4096 (on %d threads) and scaled by 4096/%d, "
+                          "other work timed in full; %.1f s wall" % (rows_n, nthr, rows_n, walln)),
+               "single_core": {"value": 1.0 / sec1, "cores": 1,
+                               "sample": "the same with %d rows on 1 thread; %.1f s wall"
+                                         % (args.cpu_sample_rows, wall1)}}
 
     if rank == 0:
         line = {
@@ -592,8 +716,16 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "precision": "float32 products, float64 traces/CG",
                        "l2": "inputs larger than L2 (LSL alone is 885 MB in float32)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "fp64": {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64, "steps": args.fp64_steps},
+            "fp64": {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64, "steps": args.fp64_steps,
+                     "roofline": {"bound": "fp64", "achieved": fp64_step_flops / ms64 / 1e9, "peak": dfma,
+                                  "unit": "TFLOP/s", "frac": fp64_step_flops / ms64 / 1e9 / dfma,
+                                  "flops_per_step": fp64_step_flops,
+                                  "peak_note": "measured DFMA loop (lsq_measure_peak)"}},
+            "mixed_tf32x3": {"steps_per_s": 1000.0 / ms_tc, "ms_per_step": ms_tc,
+                             "steps": int(rep_tc["iterations"]), "product_kernels": choices},
             "mixed_vs_fp64_omega_ha_per_atom": acc,
+            "mixed_vs_fp64_same_steps": {"steps": args.fp64_steps, "ha_per_atom": acc},
+            "mixed_vs_fp64_at_tol": to_tol,
             "bsgemm": {"product": "LS.L truncated to 23.2 A (P2 of the product schedule, every block)",
                        "triples": trip,
                        "gflops": flops / kms / 1e6, "ms": kms, "frac_fp32_peak": flops / kms / 1e9 / fp32_peak},
@@ -605,7 +737,22 @@ def run_ours(args):
                          "triples": rtrip, "ms": rms,
                          "kernel": "k_mm_plan_b4_rb<float, ...> (schedule picked by the autotuner)",
                          "hbm_frac": abytes / rms / 1e6 / hbm_peak, "hbm_peak_kind": hbm_kind,
-                         "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"},
+                         "peak_note": "measured FFMA loop (lsq_measure_peak); nominal below",
+                         "peak_nominal": fp32_nominal, "frac_nominal": rflops / rms / 1e9 / fp32_nominal},
+            "roofline_tensor": {"bound": "tensor", "kernel": "k_tc_product (LSQ_TF32X3)",
+                                "product": "the same SL.Q^T, upper triangle of 10 A",
+                                "ms": tms, "achieved": rflops / tms / 1e9, "unit": "TFLOP/s",
+                                "achieved_note": "algorithmic flops (2 b^3 per block triple) per launch, split "
+                                                 "conversions of both operands included in the time",
+                                "executed": 512.0 * tinfo["dense_triples"] / tms / 1e9,
+                                "executed_note": "tensor flops the MMAs execute: 4 x 128 per dense block "
+                                                 "triple (hi/lo x hi/lo, zero blocks of the tiles included)",
+                                "peak": tf32_peak, "frac": 512.0 * tinfo["dense_triples"] / tms / 1e9 / tf32_peak,
+                                "peak_note": "dense tf32 = measured cuBLAS bf16 burst (%.0f) x 1.1 / 2.25" % bf16_peak,
+                                "useful_fraction": tinfo["triples"] / max(tinfo["dense_triples"], 1),
+                                "gathered_gbs": 128.0 * tinfo["blocks_gathered"] / tms / 1e6,
+                                "gathered_bytes": 128 * tinfo["blocks_gathered"],
+                                "vs_fma": rms / tms},
             "hotelling": dict(hot, workload="X = S^-1 approximated on the 10 A range by "
                                              "X <- 2X - (X S) X from X0 = S / s^2, the LNV metric of Sec. 2.3.2"),
             "canonical": canon,
@@ -617,7 +764,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "last_report": {"mixed": rep, "fp64": rep64, "e2e": rep_e2e},
+            "last_report": {"mixed": rep, "fp64": rep64, "mixed_tf32x3": rep_tc, "e2e": rep_e2e},
         }
         print(json.dumps(line))
     if dist is not None:
@@ -790,6 +937,62 @@ def run_only_xl():
     print("only-product xl done: %d values per array" % A[0].numel())
 
 
+def run_oracle(args):
+    """The CPU oracle on this host's cores, single-threaded and on all cores (its OpenMP build):
+    the 64-atom configuration in full (20 CG steps), the three single products of the 4096-atom
+    configuration on sampled rows (scaled by 4096 / rows; inputs are random blocks on the
+    products' patterns, the time does not depend on the values), and CG steps of the 512-atom
+    sub-cell of the 32768-atom configuration.  No GPU is used."""
+    import oracle
+    from oracle import lnv as OL
+    oracle.build()
+    oracle.build(openmp=True)
+    ncpu, model = host_cpu()
+    out = {"metric": "oracle (CPU) timings", "cpu_model": model, "host_cpus": ncpu}
+
+    def lnv_case(ncell, sigma, seed, R_L):
+        pos, cell = diamond_si_positions(ncell, sigma, seed)
+        m = OL.System(pos, cell)
+        pH = m.pattern(R_H)
+        H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
+        Hb, Sb = oracle.Bsr(pH, B, H), oracle.Bsr(pH, B, S)
+        lnv = OL.Lnv(m, Sb, Hb, R_L, MU)
+        return lnv, OL.onsite_inverse_half(Sb, lnv.pat_L)
+
+    for threads in (1, 0):
+        nthr = oracle.use_threads(threads)
+        key = "threads_%d" % nthr
+        res = {}
+        lnv, L0 = lnv_case(2, SIGMA, config_seed(0), 8.0)
+        t0 = time.perf_counter()
+        OL.minimise(lnv, L0, 20)
+        res["cfg0_64_atoms_20_cg_steps_s"] = time.perf_counter() - t0
+        lnv, L0 = lnv_case(4, 0.1, config_seed(4), R_L)
+        OL.minimise(lnv, L0, 1)
+        t0 = time.perf_counter()
+        OL.minimise(lnv, L0, 2)
+        res["cfg4_512_atom_subcell_s_per_cg_step"] = (time.perf_counter() - t0) / 2
+        pos, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1))
+        P = {R: oracle.neighbour_list(pos, cell, R) for R in (R_S, R_L, R_L + R_S, R_H + R_L + R_S)}
+        rng = np.random.default_rng(11)
+        rnd = lambda R: oracle.Bsr(P[R], B, rng.standard_normal((P[R].nnzb, B, B)))
+        rows = np.sort(rng.choice(4096, size=max(64, 4 * nthr), replace=False))
+        prods = {}
+        for name, ra, rb, rc in (("L.S", R_L, R_S, R_L + R_S), ("LS.L", R_L + R_S, R_L, R_H + R_L + R_S),
+                                 ("LSL.SL|R_H", R_H + R_L + R_S, R_L + R_S, R_H)):
+            A_, B_ = rnd(ra), rnd(rb)
+            t0 = time.perf_counter()
+            _, trip = oracle.matmul(A_, B_, P[rc], rows=rows)
+            dt = time.perf_counter() - t0
+            prods[name] = {"rows": int(rows.size), "s_sampled": dt, "s_full_estimate": dt * 4096 / rows.size,
+                           "gflops": 2.0 * B ** 3 * trip / dt / 1e9}
+        res["cfg1_products"] = prods
+        out[key] = res
+        print(json.dumps({key: res}), file=sys.stderr, flush=True)
+    oracle.use_threads(1)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.only_product == "xl":
@@ -797,6 +1000,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "oracle":
+        run_oracle(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "sizes":

@@ -189,6 +189,22 @@ int lsq_block_matmul_tri(lsq_geom g, int b, int precision,
  * lsq_device_status reports it.  Calls on different streams race on the split buffers.
  */
 
+/* Measured FMA rate of this GPU in TFLOP/s (2 flop per fused multiply-add): a loop of
+ * independent FMAs in float64 (LSQ_F64) or float32 (LSQ_F32) on every SM, the best of three
+ * timed launches.  The roofline denominator of the FMA product kernels; no counterpart in the
+ * paper.  Synchronises stream; takes a few milliseconds. */
+int lsq_measure_peak(int precision, double *tflops_host, void *stream);
+
+/* Statistics of the LSQ_TF32X3 plan of a product already run on g (triangle as for
+ * lsq_block_matmul_tri), into info_host[5]: the block triples of the computed blocks; the
+ * block triples the MMAs execute (16 j x 8 i x k-list per tile, zero blocks included; each
+ * costs 4 x 128 tensor flops with the split operands); the blocks gathered per launch (128
+ * bytes each); the tiles; and, for products the LNV path ran with LSQ_TF32X3, which kernel
+ * the timing chose (-1 not timed, 0 FP32 FMA, 1 tensor cores).  Host only.  No counterpart
+ * in the paper. */
+int lsq_product_plan_info(lsq_geom g, int range_a, int range_b, int range_c, int triangle,
+                          int64_t *info_host);
+
 /* Synchronises stream and reports the device error word of g: LSQ_OK, or LSQ_ERR_TIMEOUT
  * when a kernel with bounded waits (the LSQ_TF32X3 product) gave up since the last check
  * (the word is then cleared; the results of that launch are not valid). */
@@ -218,10 +234,12 @@ int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
  * Scratch: one float64 partial sum per atom row in a fixed file-scope
  * device array of 262144 entries (2 MiB), which every GPU that loads the
  * library holds until the process exits.  Geometries with more than
- * 262144 atoms are rejected with LSQ_ERR_UNSUPPORTED.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.
- * All calls share the array: calls whose kernels overlap on the GPU
+ * 262144 atoms are rejected with LSQ_ERR_UNSUPPORTED.  The array is loaded
+ * on a device by the creation of a geometry there (lsq_build_neighbour_lists,
+ * which allocates in any case); each call then looks up its device address
+ * (cudaGetSymbolAddress, with g's device current), which neither allocates
+ * nor synchronises once the array is loaded, and stays valid after a device
+ * reset.  All calls share the array: calls whose kernels overlap on the GPU
  * (different streams without ordering) race and give wrong results.
  *
  * X_dev, Y_dev: blocks on patterns range_x and range_y (dtype = precision).
@@ -248,8 +266,10 @@ int lsq_trace_static(lsq_geom g, int b, int precision, int range_x, const void *
  * from the X given (which must be symmetric).  n_iter steps are taken; if
  * dx_host is not NULL, dx_host[n] receives |X_{n+1} - X_n|_F.
  * precision: LSQ_F64, or LSQ_F32 for float32 products (X is updated in
- * float64).  Allocates its workspace per call and synchronises stream
- * before returning.
+ * float64).  The workspace (X S, (X S) X, float32 copies, reductions) is held
+ * by g and grown on demand: the first call for given ranges allocates (as do
+ * the product plans it builds), later calls of the same or smaller sizes
+ * allocate nothing.  Synchronises stream before returning.
  */
 int lsq_hotelling_inverse(lsq_geom g, int b, int precision, int range_s, const double *S_dev,
                           int range_x, int range_xs, double *X_dev, int start, int n_iter,

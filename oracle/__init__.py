@@ -21,22 +21,42 @@ _LIB_PATH = os.path.join(_HERE, "_oracle.so")
 _lib = None
 
 
-def build(force=False):
-    """Compile oracle.c with gcc into an in-tree shared library."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+_OMP_PATH = os.path.join(_HERE, "_oracle_omp.so")
+
+
+def build(force=False, openmp=False):
+    """Compile oracle.c with gcc into an in-tree shared library (openmp=True: the OpenMP build
+    that times the CPU baseline on all host cores; the tests use the single-threaded one)."""
+    path = _OMP_PATH if openmp else _LIB_PATH
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    tmp = path + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared"] + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, path)
+    return path
+
+
+_want_omp = False
+
+
+def use_threads(n):
+    """Products on n host threads (the OpenMP build; n = 1: the plain single-threaded build).
+    Returns the number of threads the products then use.  For the CPU-baseline timing only."""
+    global _lib, _want_omp
+    _want_omp = n != 1
+    _lib = None
+    lib = _load()
+    return int(lib.orc_set_threads(int(n))) if _want_omp else 1
 
 
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    lib = ctypes.CDLL(build(openmp=_want_omp))
+    lib.orc_set_threads.restype = ctypes.c_int
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
     P = ctypes.c_void_p
     i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.orc_neigh_count.restype = i64

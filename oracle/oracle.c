@@ -1,5 +1,7 @@
 /*
- * oracle.c -- plain, slow, single-threaded CPU FP64 oracle.
+ * oracle.c -- plain, slow CPU FP64 oracle (single-threaded; an OpenMP build of
+ * the same source, used only to time the CPU baseline on all host cores, shares
+ * the rows of a product among threads without changing any row's arithmetic).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
  * benchmark's CPU-baseline leg may load this library.  It shares no code,
@@ -28,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static double orc_dist2(const double *pi, const double *pj, const double *cell)
 {
@@ -206,47 +211,83 @@ static int64_t orc_find(const int64_t *ptr, const int32_t *col, int i, int j)
  * b-term sum runs in ascending inner index.  Returns the number of block
  * triples (i, k, j) that contributed.
  */
+/* One row i of the truncated product (the body of orc_bsr_matmul); slot[] is a scratch
+ * map of n entries, all -1 on entry and on return.  Returns the row's block triples. */
+static int64_t bsr_matmul_row(int b, int i,
+                              const int64_t *a_ptr, const int32_t *a_col, const double *a_val,
+                              const int64_t *b_ptr, const int32_t *b_col, const double *b_val,
+                              const int64_t *c_ptr, const int32_t *c_col, double *c_val, int64_t *slot)
+{
+    int64_t bb = (int64_t)b * b;
+    int64_t triples = 0;
+    for (int64_t p = c_ptr[i]; p < c_ptr[i + 1]; ++p) {
+        slot[c_col[p]] = p;
+        memset(c_val + p * bb, 0, sizeof(double) * (size_t)bb);
+    }
+    for (int64_t pa = a_ptr[i]; pa < a_ptr[i + 1]; ++pa) {
+        int k = a_col[pa];
+        const double *ablk = a_val + pa * bb;
+        for (int64_t pb = b_ptr[k]; pb < b_ptr[k + 1]; ++pb) {
+            int64_t pc = slot[b_col[pb]];
+            if (pc < 0) continue;
+            const double *bblk = b_val + pb * bb;
+            double *cblk = c_val + pc * bb;
+            for (int x = 0; x < b; ++x)
+                for (int y = 0; y < b; ++y) {
+                    double acc = cblk[x * b + y];
+                    for (int t = 0; t < b; ++t) {
+                        double prod = ablk[x * b + t] * bblk[t * b + y];
+                        acc = acc + prod;
+                    }
+                    cblk[x * b + y] = acc;
+                }
+            ++triples;
+        }
+    }
+    for (int64_t p = c_ptr[i]; p < c_ptr[i + 1]; ++p) slot[c_col[p]] = -1;
+    return triples;
+}
+
 int64_t orc_bsr_matmul(int b, int n,
                        const int64_t *a_ptr, const int32_t *a_col, const double *a_val,
                        const int64_t *b_ptr, const int32_t *b_col, const double *b_val,
                        const int64_t *c_ptr, const int32_t *c_col, double *c_val,
                        int nrows, const int32_t *rows)
 {
-    int64_t bb = (int64_t)b * b;
-    int64_t *slot = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-    for (int j = 0; j < n; ++j) slot[j] = -1;
     int64_t triples = 0;
     int nr = rows ? nrows : n;
-    for (int r = 0; r < nr; ++r) {
-        int i = rows ? rows[r] : r;
-        for (int64_t p = c_ptr[i]; p < c_ptr[i + 1]; ++p) {
-            slot[c_col[p]] = p;
-            memset(c_val + p * bb, 0, sizeof(double) * (size_t)bb);
+    /* Rows are independent.  Built with OpenMP (only for the timed CPU baseline) the rows are
+     * shared among threads, each with its own scratch map; every row is computed exactly as
+     * in the single-threaded build. */
+#ifdef _OPENMP
+#pragma omp parallel reduction(+ : triples)
+#endif
+    {
+        int64_t *slot = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        for (int j = 0; j < n; ++j) slot[j] = -1;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+        for (int r = 0; r < nr; ++r) {
+            int i = rows ? rows[r] : r;
+            triples += bsr_matmul_row(b, i, a_ptr, a_col, a_val, b_ptr, b_col, b_val, c_ptr, c_col, c_val, slot);
         }
-        for (int64_t pa = a_ptr[i]; pa < a_ptr[i + 1]; ++pa) {
-            int k = a_col[pa];
-            const double *ablk = a_val + pa * bb;
-            for (int64_t pb = b_ptr[k]; pb < b_ptr[k + 1]; ++pb) {
-                int64_t pc = slot[b_col[pb]];
-                if (pc < 0) continue;
-                const double *bblk = b_val + pb * bb;
-                double *cblk = c_val + pc * bb;
-                for (int x = 0; x < b; ++x)
-                    for (int y = 0; y < b; ++y) {
-                        double acc = cblk[x * b + y];
-                        for (int t = 0; t < b; ++t) {
-                            double prod = ablk[x * b + t] * bblk[t * b + y];
-                            acc = acc + prod;
-                        }
-                        cblk[x * b + y] = acc;
-                    }
-                ++triples;
-            }
-        }
-        for (int64_t p = c_ptr[i]; p < c_ptr[i + 1]; ++p) slot[c_col[p]] = -1;
+        free(slot);
     }
-    free(slot);
     return triples;
+}
+
+/* Threads the products use: the OpenMP build sets and returns n (n <= 0: the default); the
+ * plain build returns 1. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Tr[X Y] = sum over stored (i, j) of X with (j, i) stored in Y of sum_rc X_ij[r][c] Y_ji[c][r]. */

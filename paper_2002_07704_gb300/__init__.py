@@ -94,6 +94,8 @@ def load():
         "lsq_xl_propagate": (I, [P, I, I, I, P, P, D, D, P, I, P, P]),
         "lsq_xl_initial_L": (I, [P, I, I, I, P, I, P, I, P, P]),
         "lsq_device_status": (I, [P, P]),
+        "lsq_measure_peak": (I, [I, P, P]),
+        "lsq_product_plan_info": (I, [P, I, I, I, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -113,7 +115,14 @@ def exported_symbols():
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
             "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
             "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L",
-            "lsq_geom_adopt_schedules", "lsq_device_status"]
+            "lsq_geom_adopt_schedules", "lsq_device_status", "lsq_measure_peak", "lsq_product_plan_info"]
+
+
+def measure_peak(precision=F32, stream=None):
+    """Measured FMA rate of the current GPU in TFLOP/s (lsq_measure_peak)."""
+    t = ctypes.c_double()
+    _check(load().lsq_measure_peak(int(precision), ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def launch_count():
@@ -144,6 +153,17 @@ def _dev(t, dtype=None):
     if dtype is not None and t.dtype != dtype:
         raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, geom, r, b, name):
+    """Raises LsqError(INVALID_ARG) unless t holds the nnzb(r) b x b blocks of range r of geom
+    (a short array would be written or read out of bounds on the device)."""
+    if t is None:
+        return
+    n = geom.nnzb(r) * b * b
+    if t.numel() != n:
+        raise LsqError(1, "%s has %d values; range %d of the geometry holds %d blocks of %d x %d (%d values)"
+                       % (name, t.numel(), r, geom.nnzb(r), b, b, n))
 
 
 def _darr(vals):
@@ -205,6 +225,13 @@ class Geometry:
         """Raises LsqError(TIMEOUT) if a kernel with bounded waits gave up since the last check."""
         _check(load().lsq_device_status(self.handle, _stream(stream)))
 
+    def product_plan_info(self, range_a, range_b, range_c, triangle=0):
+        """Statistics of the tensor-core plan of a product already run (lsq_product_plan_info)."""
+        out = (ctypes.c_int64 * 5)()
+        _check(load().lsq_product_plan_info(self.handle, range_a, range_b, range_c, triangle, out))
+        return {"triples": out[0], "dense_triples": out[1], "blocks_gathered": out[2], "tiles": out[3],
+                "auto_choice": out[4]}
+
     def adopt_schedules(self, other):
         """Use the product schedules tuned in another geometry of the same ranges."""
         _check(load().lsq_geom_adopt_schedules(self.handle, other.handle))
@@ -244,6 +271,9 @@ def block_matmul(geom, b, A, range_a, B, range_b, C, range_c, precision=F64, tra
     """
     import torch
     dt = torch.float64 if precision == F64 else torch.float32
+    _need(A, geom, range_a, b, "A")
+    _need(B, geom, range_b, b, "B")
+    _need(C, geom, range_c, b, "C")
     nt = ctypes.c_int64()
     if triangle:
         _check(load().lsq_block_matmul_tri(geom.handle, b, precision, range_a, int(trans_a),
@@ -267,6 +297,8 @@ def pattern_remap(geom_from, range_from, geom_to, range_to, b, X_from, X_to, pre
     """X_to (on geom_to's range_to) = X_from (on geom_from's range_from) matched by atom pair."""
     import torch
     dt = torch.float64 if precision == F64 else torch.float32
+    _need(X_from, geom_from, range_from, b, "X_from")
+    _need(X_to, geom_to, range_to, b, "X_to")
     _check(load().lsq_pattern_remap(geom_from.handle, range_from, geom_to.handle, range_to, b, precision,
                                     _dev(X_from, dt), _dev(X_to, dt), _stream(stream)))
 
@@ -277,6 +309,10 @@ def xl_propagate(geom, b, range_x, X_hist, LS, X_next, kappa, alpha=0.0, c=None,
     X_hist: [X(t), X(t-dt), ...] (float64 tensors on range_x); X_next may be one of them.
     """
     import torch
+    for k, x in enumerate(X_hist):
+        _need(x, geom, range_x, b, "X_hist[%d]" % k)
+    _need(LS, geom, range_x, b, "LS")
+    _need(X_next, geom, range_x, b, "X_next")
     ptrs = (ctypes.c_void_p * len(X_hist))(*[_dev(x, torch.float64) for x in X_hist])
     nc = 0 if c is None else len(c)
     carr = (ctypes.c_double * max(nc, 1))(*([float(v) for v in c] if c is not None else [0.0]))
@@ -288,6 +324,9 @@ def xl_propagate(geom, b, range_x, X_hist, LS, X_next, kappa, alpha=0.0, c=None,
 def xl_initial_L(geom, b, range_x, X, range_sinv, Sinv, range_l, L_out, precision=F64, stream=None):
     """L_out = symmetric part of (X Sinv) on range_l (the MD step's initial L)."""
     import torch
+    _need(X, geom, range_x, b, "X")
+    _need(Sinv, geom, range_sinv, b, "Sinv")
+    _need(L_out, geom, range_l, b, "L_out")
     _check(load().lsq_xl_initial_L(geom.handle, b, precision, range_x, _dev(X, torch.float64), range_sinv,
                                    _dev(Sinv, torch.float64), range_l, _dev(L_out, torch.float64),
                                    _stream(stream)))
@@ -296,6 +335,8 @@ def xl_initial_L(geom, b, range_x, X, range_sinv, Sinv, range_l, L_out, precisio
 def trace(geom, b, X, range_x, Y, range_y, precision=F64, stream=None):
     import torch
     dt = torch.float64 if precision == F64 else torch.float32
+    _need(X, geom, range_x, b, "X")
+    _need(Y, geom, range_y, b, "Y")
     out = ctypes.c_double()
     _check(load().lsq_trace(geom.handle, b, precision, range_x, _dev(X, dt), range_y, _dev(Y, dt),
                             ctypes.byref(out), _stream(stream)))
@@ -306,6 +347,8 @@ def transpose(geom, b, X, range_x, out, range_out, alpha=1.0, precision=F64, str
     """out = alpha X^T on pattern range_out (zero where X has no (j, i) block)."""
     import torch
     dt = torch.float64 if precision == F64 else torch.float32
+    _need(X, geom, range_x, b, "X")
+    _need(out, geom, range_out, b, "out")
     _check(load().lsq_transpose(geom.handle, b, precision, range_x, _dev(X, dt), range_out,
                                 _dev(out, dt), float(alpha), _stream(stream)))
 
@@ -320,6 +363,10 @@ def trace_static(geom, b, X, range_x, Y, range_y, out, precision=F64, stream=Non
     """
     import torch
     dt = torch.float64 if precision == F64 else torch.float32
+    _need(X, geom, range_x, b, "X")
+    _need(Y, geom, range_y, b, "Y")
+    if out is None or out.numel() != 1:
+        raise LsqError(1, "out must be a one-element float64 tensor")
     _check(load().lsq_trace_static(geom.handle, b, precision, range_x, _dev(X, dt), range_y,
                                    _dev(Y, dt), _dev(out, torch.float64), _stream(stream)))
 
@@ -331,6 +378,8 @@ def hotelling_inverse(geom, b, S, range_s, X, range_x, range_xs, n_iter, precisi
     Returns the list of |X_{n+1} - X_n|_F (one per step).  See lsq_hotelling_inverse.
     """
     import torch
+    _need(S, geom, range_s, b, "S")
+    _need(X, geom, range_x, b, "X")
     dx = (ctypes.c_double * max(int(n_iter), 1))()
     _check(load().lsq_hotelling_inverse(geom.handle, b, precision, range_s, _dev(S, torch.float64),
                                         range_x, range_xs, _dev(X, torch.float64), int(bool(start)),
@@ -354,15 +403,22 @@ class Lnv:
         self.handle = h
         self.geom = geom
         self.b = b
+        self.rS, self.rH, self.rL = geom.range_id(R_S), geom.range_id(R_H), geom.range_id(R_L)
+
+    def _need_lsh(self, L=None, S=None, H=None, G=None):
+        for t, r, name in ((L, self.rL, "L"), (S, self.rS, "S"), (H, self.rH, "H"), (G, self.rL, "G")):
+            _need(t, self.geom, r, self.b, name)
 
     def init_L(self, S, L, stream=None):
         import torch
+        self._need_lsh(L=L, S=S)
         _check(_lib.lsq_lnv_init_L(self.handle, _dev(S, torch.float64), _dev(L, torch.float64),
                                    _stream(stream)))
 
     def energy_gradient(self, L, S, H, mu, spin=2.0, precision=F64, G=None, stream=None):
         import torch
         om, ne = ctypes.c_double(), ctypes.c_double()
+        self._need_lsh(L=L, S=S, H=H, G=G)
         f = torch.float64
         _check(_lib.lsq_lnv_energy_gradient(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),
                                             float(mu), float(spin), precision, ctypes.byref(om),
@@ -375,6 +431,7 @@ class Lnv:
         import torch
         o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
                     int(bool(final_eval)), int(bool(verbose)), 1)
+        self._need_lsh(L=L, S=S, H=H)
         rep = LnvReport()
         f = torch.float64
         rc = _lib.lsq_lnv_minimise(self.handle, _dev(L, f), _dev(S, f), _dev(H, f), float(mu),
@@ -388,6 +445,7 @@ class Lnv:
         """Minimises E_band at fixed N_e (in place in L).  Returns (report dict, lambda = mu)."""
         import torch
         o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, 0, spin, 0, int(bool(verbose)), 0)
+        self._need_lsh(L=L, S=S, H=H)
         rep = LnvReport()
         lam = ctypes.c_double()
         f = torch.float64
@@ -405,6 +463,8 @@ class Lnv:
         """
         import torch
         dk = (ctypes.c_double * max(int(n_iter), 1))()
+        self._need_lsh(L=L, S=S, H=H)
+        _need(X, self.geom, int(range_x), self.b, "X")
         f = torch.float64
         _check(_lib.lsq_lnv_init_purify(self.handle, _dev(S, f), _dev(H, f), float(mu), int(range_x),
                                         _dev(X, f), int(range_xh), int(n_iter), int(precision),
@@ -414,6 +474,7 @@ class Lnv:
     def set_metric(self, X, range_x, range_xg, stream=None):
         """CG metric X ~ S^-1 (float64 blocks on range_x; None removes it)."""
         import torch
+        _need(X, self.geom, int(range_x), self.b, "X")
         ptr = None if X is None else _dev(X, torch.float64)
         _check(_lib.lsq_lnv_set_metric(self.handle, int(range_x), ptr, int(range_xg), _stream(stream)))
 
@@ -426,6 +487,7 @@ class Lnv:
         o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
                     int(bool(final_eval)), 0, int(bool(graph)))
         reps = (LnvReport * len(mu))()
+        self._need_lsh(L=L, S=S, H=H)
         f = torch.float64
         rc = _lib.lsq_lnv_minimise_batch(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),
                                          _darr(mu), ctypes.byref(o), reps, _stream(stream))

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblsq.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["geom.cu", "mm.cu", "plan.cu", "lnv.cu", "hotelling.cu", "noalloc.cu", "xl.cu", "tc.cu"]
+SOURCES = ["geom.cu", "mm.cu", "plan.cu", "lnv.cu", "hotelling.cu", "noalloc.cu", "xl.cu", "tc.cu", "peak.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-diag-suppress", "128", "-I", INCLUDE]

@@ -62,16 +62,19 @@ class TraceFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
+        # dX = g (Y^T)|pat(X): the masked transpose runs with alpha = 1 and the scaling by the
+        # incoming gradient stays on the device (no host synchronisation)
         X, Y = ctx.saved_tensors
         geom, b, rx, ry, prec = ctx.meta
-        gv = float(g.item())
         dX = dY = None
         if ctx.needs_input_grad[0]:
             dX = torch.empty_like(X)
-            transpose(geom, b, Y.contiguous(), ry, dX, rx, alpha=gv, precision=prec)
+            transpose(geom, b, Y.contiguous(), ry, dX, rx, precision=prec)
+            dX.mul_(g.to(dX.dtype))
         if ctx.needs_input_grad[1]:
             dY = torch.empty_like(Y)
-            transpose(geom, b, X.contiguous(), rx, dY, ry, alpha=gv, precision=prec)
+            transpose(geom, b, X.contiguous(), rx, dY, ry, precision=prec)
+            dY.mul_(g.to(dY.dtype))
         return dX, dY, None, None, None, None
 
 

@@ -373,6 +373,12 @@ extern "C" int lsq_build_neighbour_lists(const double *pos_dev, int n, const dou
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
     g->smem_optin = (size_t)optin;
     g->pats.resize(nr);
+    // load lsq_trace_static's fixed scratch array on this device now (geometry creation
+    // allocates anyway), so that the allocation-free call never triggers the module load
+    {
+        const int prc = noalloc_prime();
+        if (prc != LSQ_OK) return fail(prc);
+    }
 
     CellGrid cg;
     int ncell = 1;

@@ -130,66 +130,70 @@ extern "C" int lsq_hotelling_inverse(lsq_geom g, int b, int precision, int range
     const int bb = b * b;
     const int64_t mx = PX.nnzb * bb, ms = PS.nnzb * bb, mxs = PXS.nnzb * bb;
     const size_t es = dtype_size(precision);
-    DevBuf<double> red;  // [kHotBlocks] partial sums, then scalars
-    LSQ_TRY(red.alloc(kHotBlocks + 2));
+    // workspace held by g, grown on demand (a later call of the same or smaller sizes allocates
+    // nothing): partial sums and scalars, row sums of |S|, X S, (X S) X and float32 copies
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o_red = 0, o_row = up(sizeof(double) * (kHotBlocks + 2));
+    const size_t o_T = o_row + up(sizeof(double) * (size_t)g->n * b);
+    const size_t o_U = o_T + up(es * (size_t)mxs);
+    const size_t o_Xc = o_U + up(es * (size_t)mx);
+    const size_t o_Sc = o_Xc + (precision == LSQ_F32 ? up(es * (size_t)mx) : 0);
+    const size_t need = o_Sc + (precision == LSQ_F32 ? up(es * (size_t)ms) : 0);
+    if (g->hot_ws.n < need) LSQ_TRY(g->hot_ws.alloc(need));
+    char *ws = g->hot_ws.p;
+    double *red = reinterpret_cast<double *>(ws + o_red);  // [kHotBlocks] partial sums, then scalars
+    void *T = ws + o_T, *U = ws + o_U;
+    float *Xc = reinterpret_cast<float *>(ws + o_Xc), *Sc = reinterpret_cast<float *>(ws + o_Sc);
     if (start) {
-        DevBuf<double> rowabs;
-        LSQ_TRY(rowabs.alloc((size_t)g->n * b));
+        double *rowabs = reinterpret_cast<double *>(ws + o_row);
         const int64_t *pos = nullptr;
         LSQ_TRY(get_posmap(g, range_x, range_s, 0, &pos, s));
         note_launch();
-        k_row_abs<<<(int)(((int64_t)g->n * b + 255) / 256), 256, 0, s>>>(g->n, b, PS.row_ptr.p, S, rowabs.p);
+        k_row_abs<<<(int)(((int64_t)g->n * b + 255) / 256), 256, 0, s>>>(g->n, b, PS.row_ptr.p, S, rowabs);
         note_launch();
-        k_max<<<1, 1024, 0, s>>>((int64_t)g->n * b, rowabs.p, red.p + kHotBlocks);
+        k_max<<<1, 1024, 0, s>>>((int64_t)g->n * b, rowabs, red + kHotBlocks);
         note_launch();
-        k_scaled_start<<<grid_of(mx), 256, 0, s>>>(PX.nnzb, bb, pos, S, red.p + kHotBlocks, X);
+        k_scaled_start<<<grid_of(mx), 256, 0, s>>>(PX.nnzb, bb, pos, S, red + kHotBlocks, X);
         LSQ_CHECK_LAUNCH();
-        LSQ_CUDA_TRY(cudaStreamSynchronize(s));  // rowabs is released on return
     }
-    DevBuf<char> T, U, Xc, Sc;
-    LSQ_TRY(T.alloc(es * (size_t)mxs));
-    LSQ_TRY(U.alloc(es * (size_t)mx));
     const void *Sop = S;
     if (precision == LSQ_F32) {
-        LSQ_TRY(Xc.alloc(es * (size_t)mx));
-        LSQ_TRY(Sc.alloc(es * (size_t)ms));
         note_launch();
-        k_f64_to_f32<<<grid_of(ms), 256, 0, s>>>(ms, S, (float *)Sc.p);
+        k_f64_to_f32<<<grid_of(ms), 256, 0, s>>>(ms, S, Sc);
         LSQ_CHECK_LAUNCH();
-        Sop = Sc.p;
+        Sop = Sc;
     }
     for (int it = 0; it < n_iter; ++it) {
         const void *Xop = X;
         if (precision == LSQ_F32) {
             note_launch();
-            k_f64_to_f32<<<grid_of(mx), 256, 0, s>>>(mx, X, (float *)Xc.p);
+            k_f64_to_f32<<<grid_of(mx), 256, 0, s>>>(mx, X, Xc);
             LSQ_CHECK_LAUNCH();
-            Xop = Xc.p;
+            Xop = Xc;
         }
         // T = X S (S symmetric: op(B) = S^T = S, read as rows), U = (T X)|R_X on the upper
         // triangle, mirrored (X symmetric)
-        LSQ_TRY(block_matmul(g, b, precision, range_x, 0, Xop, range_s, 1, Sop, range_xs, T.p, 1.0, 0.0,
+        LSQ_TRY(block_matmul(g, b, precision, range_x, 0, Xop, range_s, 1, Sop, range_xs, T, 1.0, 0.0,
                              nullptr, s));
-        LSQ_TRY(block_matmul(g, b, precision, range_xs, 0, T.p, range_x, 1, Xop, range_x, U.p, 1.0, 0.0,
+        LSQ_TRY(block_matmul(g, b, precision, range_xs, 0, T, range_x, 1, Xop, range_x, U, 1.0, 0.0,
                              nullptr, s, 1));
         // U exactly symmetric keeps X exactly symmetric.  (The second product reads X as X^T;
         // an antisymmetric part of X would double at every step.)
-        LSQ_TRY(sym_diag_on(g, range_x, b, precision, U.p, s));
+        LSQ_TRY(sym_diag_on(g, range_x, b, precision, U, s));
         note_launch();
         if (precision == LSQ_F64)
-            k_hot_update<double><<<kHotBlocks, kHotThreads, 0, s>>>(mx, (const double *)U.p, X, red.p);
+            k_hot_update<double><<<kHotBlocks, kHotThreads, 0, s>>>(mx, (const double *)U, X, red);
         else
-            k_hot_update<float><<<kHotBlocks, kHotThreads, 0, s>>>(mx, (const float *)U.p, X, red.p);
+            k_hot_update<float><<<kHotBlocks, kHotThreads, 0, s>>>(mx, (const float *)U, X, red);
         note_launch();
-        k_sum_sqrt<<<1, kHotBlocks, 0, s>>>(kHotBlocks, red.p, red.p + kHotBlocks + 1);
+        k_sum_sqrt<<<1, kHotBlocks, 0, s>>>(kHotBlocks, red, red + kHotBlocks + 1);
         LSQ_CHECK_LAUNCH();
         if (dx_host) {
-            LSQ_CUDA_TRY(cudaMemcpyAsync(dx_host + it, red.p + kHotBlocks + 1, sizeof(double),
+            LSQ_CUDA_TRY(cudaMemcpyAsync(dx_host + it, red + kHotBlocks + 1, sizeof(double),
                                          cudaMemcpyDeviceToHost, s));
             LSQ_CUDA_TRY(cudaStreamSynchronize(s));
         }
     }
-    // the workspace is released on return: let the enqueued work finish first
     LSQ_CUDA_TRY(cudaStreamSynchronize(s));
     return LSQ_OK;
 }

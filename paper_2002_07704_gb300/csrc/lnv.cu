@@ -413,6 +413,9 @@ using namespace lsq;
 struct lsq_lnv_s {
     lsq_geom g = nullptr;
     int b = 4;
+    // product precision of the float32 path: LSQ_F32 (FMA kernels), or kMixedAuto when the
+    // caller asked for LSQ_TF32X3 (per product the faster of those and the tensor-core kernel)
+    int mm32 = LSQ_F32;
     int rS = -1, rH = -1, rL = -1, r1 = -1, r2 = -1, r3 = -1;
     // float64 working set
     DevBuf<double> Hp, Sh, G, Gp, D;
@@ -432,6 +435,20 @@ struct lsq_lnv_s {
 };
 
 static int64_t nvals(lsq_lnv c, int r) { return c->g->pats[r].nnzb * c->b * c->b; }
+
+// Precision handed to the products: the float32 path runs them as c->mm32.
+static int mmp(lsq_lnv c, int prec) { return prec == LSQ_F32 ? c->mm32 : prec; }
+
+// Accepts LSQ_F64, LSQ_F32 and LSQ_TF32X3; the latter runs the float32 path (float32 storage,
+// float64 traces and CG) with the products chosen per product between the FP32 FMA schedules
+// and the split-TF32 tensor-core kernel.  *prec becomes LSQ_F64 or LSQ_F32.
+static int take_precision(lsq_lnv c, int *prec) {
+    if (*prec != LSQ_F64 && *prec != LSQ_F32 && *prec != LSQ_TF32X3)
+        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64, LSQ_F32 or LSQ_TF32X3");
+    c->mm32 = *prec == LSQ_TF32X3 ? kMixedAuto : LSQ_F32;
+    if (*prec == LSQ_TF32X3) *prec = LSQ_F32;
+    return LSQ_OK;
+}
 
 // Steps between fresh products Q = H'LS in the single-system CG (Q is updated along the line
 // search in between).
@@ -642,9 +659,9 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     // With the gradient, slots 0 and 1 come from <L, Q> and <L, M> / 3 (see the header) and LSL
     // is formed only for N_e.
     const bool need_lsl = !G || ne || want_ne;
-    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, o.L, c->rS, 1, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rL, 0, o.L, c->rS, 1, o.S, c->r1, c->LS.p, 1.0, 0.0, nullptr, s));
     if (need_lsl)
-        LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, c->LS.p, c->rL, 1, o.L, c->r3, c->LSL.p, 1.0, 0.0, nullptr, s, 1));
     // 4 x 4 blocks: transposed operands are materialised so the plan kernel reads rows; the
     // kernel for other block sizes reads transposes through the transpose map
     const bool mat = c->b == 4;
@@ -652,7 +669,7 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     const int tLS = mat ? 1 : 0;
     if (mat) LSQ_TRY(transpose_on(g, c->r1, b, prec, c->LS.p, c->SL.p, s));
     if (!reuse_q)
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, tLS, LSop, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rH, 0, o.Hp, c->r1, tLS, LSop, c->r3, c->Q.p, 1.0, 0.0, nullptr, s));
     auto tr = [&](int rx, const void *X, int ry, const void *Y, int slot) {
         return seg ? seg_trace(c, prec, rx, X, ry, Y, slot, s) : trace_into(g, b, prec, rx, X, ry, Y, slot, s);
     };
@@ -665,7 +682,7 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
     }
     if (ne || want_ne) {
         void *SLS = c->QD.p;
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Sh, c->r1, tLS, LSop, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rH, 0, o.Sh, c->r1, tLS, LSop, c->r3, SLS, 1.0, 0.0, nullptr, s, 1));
         LSQ_TRY(tr(c->rH, o.Sh, c->r3, c->LSL.p, 2));
         LSQ_TRY(dt(c->r3, c->LSL.p, SLS, 3));
     }
@@ -680,14 +697,14 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         void *Qs = c->QD.p;
         LSQ_TRY(sym_sum_on(g, c->r3, b, prec, c->Q.p, Qs, s));
         if (mat)
-            LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->SL.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
+            LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, c->SL.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
         else
-            LSQ_TRY(block_matmul(g, b, prec, c->r1, 1, c->LS.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
+            LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 1, c->LS.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
         // T2 = SL.Q^T: op(B) = Q^T, read as rows of Q; op(A) = SL (materialised for 4 x 4 blocks)
         if (mat)
-            LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, c->SL.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
+            LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, c->SL.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
         else
-            LSQ_TRY(block_matmul(g, b, prec, c->r1, 1, c->LS.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
+            LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 1, c->LS.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
         const int64_t *pq = nullptr, *pqt = nullptr;
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 0, &pq, s));
         LSQ_TRY(get_posmap(g, c->rL, c->r3, 1, &pqt, s));
@@ -749,21 +766,21 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     }
     void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
     const bool mat = c->b == 4;  // see energy_gradient
-    LSQ_TRY(block_matmul(g, b, prec, c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
     if (mat) {
         LSQ_TRY(transpose_on(g, c->r1, b, prec, P, PT, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 1, PT, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rH, 0, o.Hp, c->r1, 1, PT, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
     } else {
-        LSQ_TRY(block_matmul(g, b, prec, c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
     }
-    LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
+    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
     // Z = QD^T.P is symmetric, so it is formed as P^T.QD: the operand whose rows the kernel
     // walks (and stages in shared memory) is then P^T on L+S's range, not QD^T on R3
     if (mat) {
         LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
-        LSQ_TRY(block_matmul(g, b, prec, c->r1, 0, PT, c->r3, 1, QDT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, PT, c->r3, 1, QDT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
     } else {
-        LSQ_TRY(block_matmul(g, b, prec, c->r1, 1, P, c->r3, 0, c->QD.p, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 1, P, c->r3, 0, c->QD.p, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
     }
     if (seg) {
         LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->D.p, 4, s));
@@ -812,8 +829,7 @@ extern "C" int lsq_lnv_energy_gradient(lsq_lnv c, const double *L, const double 
                                        double *G, void *stream) {
     clear_error();
     if (!c || !L || !S || !H) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
-    if (prec != LSQ_F64 && prec != LSQ_F32)
-        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    LSQ_TRY(take_precision(c, &prec));
     cudaStream_t s = (cudaStream_t)stream;
     LSQ_TRY(prepare_hs(c, S, H, mu, prec, s));
     double om = 0, n_e = 0;
@@ -968,8 +984,7 @@ extern "C" int lsq_lnv_init_purify(lsq_lnv c, const double *S, const double *H, 
     lsq_geom g = c->g;
     LSQ_TRY(geom_check(g, range_x));
     LSQ_TRY(geom_check(g, range_xh));
-    if (precision != LSQ_F64 && precision != LSQ_F32)
-        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    LSQ_TRY(take_precision(c, &precision));
     if (n_iter < 0) return set_error(LSQ_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (g->pats[range_xh].R < g->pats[range_x].R + g->pats[c->rH].R - 1e-9)
         return set_error(LSQ_ERR_INVALID_ARG, "range_xh must cover the natural range R_X + R_H of X H");
@@ -1023,12 +1038,12 @@ extern "C" int lsq_lnv_init_purify(lsq_lnv c, const double *S, const double *H, 
             k_to_f32<<<grid_for(nl), 256, 0, s>>>(nl, L, (float *)c->Lc.p);
             LSQ_CHECK_LAUNCH();
         }
-        LSQ_TRY(block_matmul(g, b, precision, c->rL, 0, Kop, c->rS, 1, Sop, c->r1, KS, 1.0, 0.0, nullptr, s));
-        LSQ_TRY(block_matmul(g, b, precision, c->r1, 0, KS, c->rL, 1, Kop, c->rL, Bm, 1.0, 0.0, nullptr, s, 1));
+        LSQ_TRY(block_matmul(g, b, mmp(c, precision), c->rL, 0, Kop, c->rS, 1, Sop, c->r1, KS, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, mmp(c, precision), c->r1, 0, KS, c->rL, 1, Kop, c->rL, Bm, 1.0, 0.0, nullptr, s, 1));
         LSQ_TRY(sym_diag_on(g, c->rL, b, precision, Bm, s));
         // (K S)(K S K) on every block (truncated K S K makes it unsymmetric); the second factor
         // read as rows of its transpose, which it equals
-        LSQ_TRY(block_matmul(g, b, precision, c->r1, 0, KS, c->rL, 1, Bm, c->rL, Cm, 1.0, 0.0, nullptr, s));
+        LSQ_TRY(block_matmul(g, b, mmp(c, precision), c->r1, 0, KS, c->rL, 1, Bm, c->rL, Cm, 1.0, 0.0, nullptr, s));
         const int64_t *tmL = g->pats[c->rL].tmap.p;
         note_launch();
         if (precision == LSQ_F64)
@@ -1064,8 +1079,8 @@ int metric_apply(lsq_lnv c, int prec, const double *G, cudaStream_t s) {
         Gop = c->Dc.p;
         Xop = c->Xmc.p;
     }
-    LSQ_TRY(block_matmul(g, b, prec, c->rX, 0, Xop, c->rL, 1, Gop, c->rXG, c->XG.p, 1.0, 0.0, nullptr, s));
-    LSQ_TRY(block_matmul(g, b, prec, c->rXG, 0, c->XG.p, c->rX, 1, Xop, c->rL, c->Pc.p, 1.0, 0.0, nullptr, s, 1));
+    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rX, 0, Xop, c->rL, 1, Gop, c->rXG, c->XG.p, 1.0, 0.0, nullptr, s));
+    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rXG, 0, c->XG.p, c->rX, 1, Xop, c->rL, c->Pc.p, 1.0, 0.0, nullptr, s, 1));
     LSQ_TRY(sym_diag_on(g, c->rL, b, prec, c->Pc.p, s));
     if (prec == LSQ_F64) {
         LSQ_CUDA_TRY(cudaMemcpyAsync(c->Pm.p, c->Pc.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
@@ -1086,8 +1101,7 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
     lsq_lnv_opts o;
     lsq_lnv_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != LSQ_F64 && o.precision != LSQ_F32)
-        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    LSQ_TRY(take_precision(c, &o.precision));
     if (o.max_iter < 0 || o.cg_reset < 1 || o.refine_iter < 0)
         return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1217,8 +1231,7 @@ extern "C" int lsq_lnv_minimise_canonical(lsq_lnv c, double *L, const double *S,
     lsq_lnv_opts o;
     lsq_lnv_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != LSQ_F64 && o.precision != LSQ_F32)
-        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    LSQ_TRY(take_precision(c, &o.precision));
     if (o.max_iter < 0 || o.cg_reset < 1) return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
     if (!(n_electrons > 0.0)) return set_error(LSQ_ERR_INVALID_ARG, "n_electrons must be positive");
     if (c->rX >= 0) return set_error(LSQ_ERR_UNSUPPORTED, "the canonical minimiser has no metric; clear it");
@@ -1450,8 +1463,7 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
     lsq_lnv_opts o;
     lsq_lnv_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != LSQ_F64 && o.precision != LSQ_F32)
-        return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64 or LSQ_F32");
+    LSQ_TRY(take_precision(c, &o.precision));
     if (o.max_iter < 0 || o.cg_reset < 1 || o.refine_iter < 0)
         return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
     cudaStream_t us = (cudaStream_t)stream;

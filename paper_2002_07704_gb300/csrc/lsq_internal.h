@@ -122,6 +122,10 @@ struct TcPlan {
     DevBuf<int32_t> cta_stages;  // [grid] stages of each CTA
     DevBuf<int32_t> pos;         // stage records: block indices in op(A) or op(B)^T, or -1
     DevBuf<int32_t> cpos;        // [128 ntiles]: block (i, j) of C, -1 if not computed
+    // kMixedAuto products: -1 not yet timed, 0 the FP32 FMA schedule won, 1 this kernel won;
+    // and the two times (ms) of that comparison
+    int auto_choice = -1;
+    float auto_ms[2] = {0.f, 0.f};
     TcPlan() = default;
     TcPlan(TcPlan &&) = default;
 };
@@ -165,6 +169,8 @@ struct lsq_geom_s {
     std::map<std::tuple<int, int, int>, lsq::TcPlan> tcplans;
     lsq::DevBuf<char> tc_a, tc_x;
     lsq::DevBuf<int> dev_err;
+    // workspace of lsq_hotelling_inverse (grown on demand)
+    lsq::DevBuf<char> hot_ws;
     // float32 operands and result of lsq_xl_initial_L (grown on demand)
     lsq::DevBuf<char> xl_scratch;
     lsq::Reducer red;
@@ -215,10 +221,20 @@ int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s);
 
 inline size_t dtype_size(int dtype) { return dtype == LSQ_F64 ? 8 : 4; }
 
+// Internal product precision (not part of the ABI): float32 storage, and per product the
+// faster of the FP32 FMA schedules and the LSQ_TF32X3 tensor-core kernel, timed on the
+// product's first call (with beta = 0).  The LNV path uses it when asked for LSQ_TF32X3.
+constexpr int kMixedAuto = 100;
+
+// The TF32X3 tensor-core plan of a product (built on first use; see tc.cu).
+int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cudaStream_t s);
+
 // Exact block triples of a product restricted to a triangle (upper: 0 all, 1 j >= i, 2 j <= i).
 int plan_count_triples(lsq_geom g, int ra, int rb, int rc, int upper, int64_t *out, cudaStream_t s);
 // Lower blocks of a symmetric 4 x 4 result from the upper ones (pattern rc).
 int mirror_lower4(lsq_geom g, int rc, int dtype, void *C, cudaStream_t s);
+// Loads the fixed scratch array of lsq_trace_static on the current device (noalloc.cu).
+int noalloc_prime();
 // Device error word of g (allocated and cleared on first use).
 int dev_err_ptr(lsq_geom g, int **out);
 // Tensor-core truncated 4 x 4 product in split TF32 (see tc.cu); float32 operands and result.

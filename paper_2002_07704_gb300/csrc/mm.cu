@@ -26,6 +26,9 @@
 // algorithmic flop count.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include <algorithm>
 #include <cstdint>
 #include <string>
@@ -580,8 +583,67 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     LSQ_TRY(geom_check(g, rb));
     LSQ_TRY(geom_check(g, rc));
     if (b < 1 || b > 16) return set_error(LSQ_ERR_INVALID_ARG, "block size must be in [1, 16]");
-    if (dtype != LSQ_F64 && dtype != LSQ_F32 && dtype != LSQ_TF32X3)
+    if (dtype != LSQ_F64 && dtype != LSQ_F32 && dtype != LSQ_TF32X3 && dtype != kMixedAuto)
         return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64, LSQ_F32 or LSQ_TF32X3");
+    if (dtype == kMixedAuto) {
+        // the faster of the FP32 FMA schedules and the tensor-core kernel for this product
+        if (b != 4 || g->n == 0) {
+            dtype = LSQ_F32;
+        } else {
+            const int upper = sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0);
+            TcPlan *tp = nullptr;
+            int prc = tc_plan_get(g, ra, rb, rc, upper, &tp, s);
+            if (prc == LSQ_ERR_OOM || prc == LSQ_ERR_UNSUPPORTED) {
+                (void)cudaGetLastError();
+                clear_error();
+                dtype = LSQ_F32;
+            } else if (prc != LSQ_OK) {
+                return prc;
+            } else if (tp->auto_choice < 0 && beta != 0.0) {
+                dtype = LSQ_F32;  // no timing run on an accumulating call: FMA until timed
+            } else {
+                if (tp->auto_choice < 0) {
+                    // time each once more after its own first call (plan, tuning) has run
+                    cudaEvent_t e0, e1;
+                    LSQ_CUDA_TRY(cudaEventCreate(&e0));
+                    LSQ_CUDA_TRY(cudaEventCreate(&e1));
+                    float ms[2] = {0.f, 0.f};
+                    for (int k = 0; k < 2; ++k) {
+                        const int pk = k == 0 ? LSQ_F32 : LSQ_TF32X3;
+                        LSQ_TRY(block_matmul(g, b, pk, ra, ta, A, rb, tb, B, rc, C, alpha, beta, nullptr, s, sym));
+                        LSQ_CUDA_TRY(cudaEventRecord(e0, s));
+                        LSQ_TRY(block_matmul(g, b, pk, ra, ta, A, rb, tb, B, rc, C, alpha, beta, nullptr, s, sym));
+                        LSQ_CUDA_TRY(cudaEventRecord(e1, s));
+                        LSQ_CUDA_TRY(cudaEventSynchronize(e1));
+                        LSQ_CUDA_TRY(cudaEventElapsedTime(&ms[k], e0, e1));
+                    }
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    tp->auto_choice = ms[1] < ms[0] ? 1 : 0;
+                    tp->auto_ms[0] = ms[0];
+                    tp->auto_ms[1] = ms[1];
+                    if (std::getenv("LSQ_TUNE_LOG"))
+                        std::fprintf(stderr, "lsq autotune: ranges (%g, %g, %g) tri %d: FP32 FMA %.3f ms, TF32X3 %.3f ms -> %s\n",
+                                     g->pats[ra].R, g->pats[rb].R, g->pats[rc].R, upper, ms[0], ms[1],
+                                     tp->auto_choice ? "tensor cores" : "FMA");
+                    if (tp->auto_choice == 1) {
+                        // the FMA plan of this product is not needed any more
+                        g->pplans.erase(std::make_tuple(ra, rb, rc + 1000 * upper));
+                    } else {
+                        // nor the tensor-core plan's records (the choice itself is kept)
+                        tp->pos.release();
+                        tp->cpos.release();
+                        tp->tile_nk.release();
+                        tp->tile_posoff.release();
+                        tp->cta_stages.release();
+                    }
+                    if (triples) *triples = tp->triples;
+                    return LSQ_OK;  // C holds the product (both runs wrote the same result)
+                }
+                dtype = tp->auto_choice == 1 ? LSQ_TF32X3 : LSQ_F32;
+            }
+        }
+    }
     if (g->n > 0 && (!A || !B || !C)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
     if (C == A || C == B) return set_error(LSQ_ERR_INVALID_ARG, "C must not alias A or B");
     if (dtype == LSQ_TF32X3) {

@@ -11,7 +11,6 @@
 // file-scope device array.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "lsq_internal.h"
@@ -21,11 +20,6 @@ namespace lsq {
 // One float64 partial sum per atom row; 2 MiB, held by every device that loads the library.
 constexpr int kStaticTraceRows = 262144;
 static __device__ __align__(256) double g_trace_rows[kStaticTraceRows];
-
-// Device address of g_trace_rows for each device, looked up once with that device current.
-constexpr int kMaxDevices = 64;
-static double *g_rows_addr[kMaxDevices] = {nullptr};
-static std::mutex g_rows_mutex;
 
 __device__ __forceinline__ int64_t find_col(const int64_t *__restrict__ ptr,
                                             const int32_t *__restrict__ col, int row, int key) {
@@ -75,18 +69,21 @@ __global__ void k_trace_rows_sum(int n, const double *__restrict__ rows, double 
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Device address of g_trace_rows on the current device.  Looked up on every call: once the
+// array's module is loaded on the device (by the geometry's creation, see noalloc_prime) the
+// lookup neither allocates nor synchronises, and a reset device gets its new address.
 static int static_rows_address(double **out) {
-    int dev = 0;
-    LSQ_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(LSQ_ERR_UNSUPPORTED, "device index too large");
-    std::lock_guard<std::mutex> lock(g_rows_mutex);
-    if (!g_rows_addr[dev]) {
-        void *p = nullptr;
-        LSQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_trace_rows));
-        g_rows_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_rows_addr[dev];
+    void *p = nullptr;
+    LSQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_trace_rows));
+    *out = static_cast<double *>(p);
     return LSQ_OK;
+}
+
+// Loads the array on the current device (the first symbol lookup does, allocating its 2 MiB),
+// so that lsq_trace_static itself never does.  Called by lsq_build_neighbour_lists.
+int noalloc_prime() {
+    double *p = nullptr;
+    return static_rows_address(&p);
 }
 
 }  // namespace lsq

@@ -615,6 +615,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
 
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 256;
 
+}  // namespace
+
 int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cudaStream_t s) {
     auto key = std::make_tuple(ra, rb, rc + 1000 * upper);
     auto f = g->tcplans.find(key);
@@ -738,6 +740,8 @@ int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cud
     return LSQ_OK;
 }
 
+namespace {
+
 int split_operand(lsq_geom g, int r, bool trans, const float *X, DevBuf<char> &buf, cudaStream_t s) {
     const int64_t nnzb = g->pats[r].nnzb;
     const size_t need = (size_t)kUnit * (size_t)std::max<int64_t>(nnzb, 1);
@@ -802,6 +806,26 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
 }  // namespace lsq
 
 using namespace lsq;
+
+extern "C" int lsq_product_plan_info(lsq_geom g, int range_a, int range_b, int range_c, int triangle,
+                                     int64_t *info_host) {
+    clear_error();
+    LSQ_TRY(geom_check(g, range_a));
+    LSQ_TRY(geom_check(g, range_b));
+    LSQ_TRY(geom_check(g, range_c));
+    if (!info_host) return set_error(LSQ_ERR_INVALID_ARG, "info_host is null");
+    if (triangle < 0 || triangle > 3) return set_error(LSQ_ERR_INVALID_ARG, "triangle must be 0..3");
+    const int upper = triangle == 3 ? 2 : (triangle >= 1 ? 1 : 0);
+    auto f = g->tcplans.find(std::make_tuple(range_a, range_b, range_c + 1000 * upper));
+    if (f == g->tcplans.end()) return set_error(LSQ_ERR_INVALID_ARG, "no tensor-core plan for these ranges yet");
+    const TcPlan &p = f->second;
+    info_host[0] = p.triples;
+    info_host[1] = p.dense_triples;
+    info_host[2] = p.units;
+    info_host[3] = p.ntiles;
+    info_host[4] = p.auto_choice;
+    return LSQ_OK;
+}
 
 extern "C" int lsq_device_status(lsq_geom g, void *stream) {
     clear_error();

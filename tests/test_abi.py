@@ -66,3 +66,27 @@ def test_invalid_arguments_are_rejected_without_gpu(lib):
     buf = ctypes.create_string_buffer(256)
     assert L.lsq_last_error(buf, 256) == 1 and b"positive" in buf.value
     assert L.lsq_block_matmul(None, 4, 0, 0, 0, None, 0, 0, None, 0, None, 1.0, 0.0, None, None) == 1
+
+
+def test_binding_rejects_wrong_sizes_without_gpu():
+    """Every matrix argument must hold exactly nnzb(range) b x b values; a short (or long)
+    tensor raises LsqError(INVALID_ARG) on the host, before any device call."""
+    import torch
+
+    class FakeGeom:
+        handle = None
+
+        def nnzb(self, r):
+            return {0: 10, 1: 7}[r]
+
+    A = torch.zeros(10 * 16)
+    short = torch.zeros(7 * 16 - 1)
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.block_matmul(FakeGeom(), 4, A, 0, A, 0, short, 1)
+    assert e.value.code == 1 and "C has 111 values" in str(e.value)
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.trace(FakeGeom(), 4, A, 0, torch.zeros(8 * 16), 1)
+    assert e.value.code == 1
+    with pytest.raises(lsq.LsqError) as e:
+        lsq.transpose(FakeGeom(), 13, torch.zeros(10 * 169), 0, torch.zeros(7 * 16), 1)
+    assert e.value.code == 1

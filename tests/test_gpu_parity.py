@@ -3,7 +3,8 @@
 Tolerances: range patterns bit-exact; float64 products within 1e-12 of
 the oracle (max-norm, relative to the largest reference element); float32
 products within 1e-5 of max |A|.|B| (inputs rounded to 24 bits and sums
-of up to ~10^4 terms); LNV energies in float64 within 1e-11 relative.
+of up to ~10^4 terms); LNV energy, electron number and gradient in float64
+within 1e-12 relative.
 """
 import numpy as np
 import pytest
@@ -202,6 +203,45 @@ def test_block_matmul_full_size_sampled_rows():
     assert t > 0
 
 
+@pytest.mark.parametrize("shape", ["sl_qt_upper", "p_d_upper", "l_s"])
+def test_block_matmul_full_size_float32_sampled_rows(shape):
+    """4096-atom Si, float32, the three product shapes whose schedules the autotuner picks for
+    the benchmark's mixed step, in the same launch configuration (same geometry, ranges and
+    triangle, first call tuned): 32 sampled rows of C against the oracle, within 1e-5 of
+    max |A|.|B| over those rows.  At this size rows of C hold ~200 (10 A) to ~2600 (23.2 A)
+    blocks and item lists ~900 entries, so the 16-bit offsets and the split lists take their
+    full-size paths.
+      sl_qt_upper: SL (16.6 A) . Q^T (Q on 23.2 A), upper triangle of 10 A (trans_b);
+      p_d_upper:   P (16.6 A) . D^T (D on 10 A), upper triangle of 23.2 A;
+      l_s:         L (10 A) . S^T (S on 6.6 A), every block of 16.6 A."""
+    ra, rb, rc, tri = {"sl_qt_upper": (16.6, 23.2, 10.0, 2), "p_d_upper": (16.6, 10.0, 23.2, 2),
+                       "l_s": (10.0, 6.6, 16.6, 0)}[shape]
+    pos, cell = si(8, 0.05, config_seed(1))
+    ranges = [6.6, 10.0, 16.6, 23.2]
+    g = gpu_geometry(pos, cell, ranges)
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in ranges}
+    rng = np.random.default_rng(17)
+    A = oracle.Bsr(P[ra], 4, _rand(P[ra], 4, rng).astype(np.float32).astype(np.float64))
+    B = oracle.Bsr(P[rb], 4, _rand(P[rb], 4, rng).astype(np.float32).astype(np.float64))
+    Cg = torch.zeros((P[rc].nnzb, 4, 4), dtype=torch.float32, device="cuda")
+    args = (g, 4, cuda(A.val, torch.float32), g.range_id(ra), cuda(B.val, torch.float32), g.range_id(rb),
+            Cg, g.range_id(rc))
+    lsq.block_matmul(*args, precision=lsq.F32, trans_b=True, triangle=tri)   # tunes the schedule
+    Cg.zero_()
+    lsq.block_matmul(*args, precision=lsq.F32, trans_b=True, triangle=tri)
+    torch.cuda.synchronize()
+    rows = np.sort(rng.choice(4096, size=32, replace=False))
+    Bt = oracle.transpose(B, P[rb])
+    ref, _ = oracle.matmul(A, Bt, P[rc], rows=rows)
+    bnd, _ = oracle.matmul(oracle.Bsr(P[ra], 4, np.abs(A.val)), oracle.Bsr(P[rb], 4, np.abs(Bt.val)),
+                           P[rc], rows=rows)
+    pc = P[rc]
+    prow = np.repeat(np.arange(pc.n), np.diff(pc.ptr))
+    sel = np.isin(prow, rows) & ((pc.col >= prow) if tri == 2 else True)
+    got = Cg.double().cpu().numpy()
+    assert np.abs(got[sel] - ref.val[sel]).max() <= 1e-5 * bnd.val[sel].max()
+
+
 def test_trace_matches_oracle():
     pos, cell = si(2, 0.1, 5)
     g = gpu_geometry(pos, cell, [6.6, 10.0])
@@ -244,11 +284,11 @@ def test_lnv_init_energy_gradient_float64():
     G = torch.zeros_like(Lg)
     om, ne = ctx.energy_gradient(cuda(L1.val), cuda(Sb.val), cuda(Hb.val), MU, G=G)
     om_ref, ne_ref = ref.energy(L1)
-    assert abs(om - om_ref) <= 1e-11 * abs(om_ref)
-    assert abs(ne - ne_ref) <= 1e-11 * abs(ne_ref)
+    assert abs(om - om_ref) <= 1e-12 * abs(om_ref)
+    assert abs(ne - ne_ref) <= 1e-12 * abs(ne_ref)
     Gr = ref.gradient(L1)
     Gr = 0.5 * (Gr + oracle.transpose(Gr, Gr.pat))
-    assert rel_err(G.cpu().numpy(), Gr.val) <= 1e-11
+    assert rel_err(G.cpu().numpy(), Gr.val) <= 1e-12
     Gh = G.cpu().numpy()
     assert np.array_equal(Gh, oracle.transpose(oracle.Bsr(ref.pat_L, 4, Gh), ref.pat_L).val)
 
@@ -293,6 +333,32 @@ def test_lnv_mixed_precision_reaches_float64_minimum():
     # the returned Omega is a float64 evaluation of the returned L
     om_chk, _ = ref.energy(oracle.Bsr(ref.pat_L, 4, Lg.cpu().numpy()))
     assert abs(rep["omega_ev"] - om_chk) <= 1e-10 * abs(om_chk)
+
+
+def test_lnv_tf32x3_energy_gradient_and_minimum():
+    """The mixed path with LSQ_TF32X3 (per product the faster of the FP32 FMA schedules and the
+    split-TF32 tensor-core kernel, timed on first use): Omega within 1e-6 Ha/atom and G within
+    1e-5 of max |G| of the oracle at an intermediate L, and the minimum (float64 refinement and
+    final Omega) within 1e-6 Ha/atom of the oracle's."""
+    g, ctx, ref, Hb, Sb = _lnv_setup(3, 0.05, config_seed(0), 8.0)
+    n = g.n_atoms
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    L1, _ = OL.minimise(ref, L0, 3)
+    G = torch.zeros((ref.pat_L.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+    for _ in range(2):   # the first call times both kernels for every product
+        om, _ = ctx.energy_gradient(cuda(L1.val), cuda(Sb.val), cuda(Hb.val), MU, G=G, precision=lsq.TF32X3)
+    g.device_status()
+    om_ref, _ = ref.energy(L1)
+    assert abs(om - om_ref) / lsq.HARTREE_EV / n < 1e-6
+    Gr = ref.gradient(L1)
+    assert rel_err(G.cpu().numpy(), 0.5 * (Gr.val + oracle.transpose(Gr, Gr.pat).val)) < 1e-5
+    Lr, _ = OL.minimise(ref, L0, 200, tol_ha_per_atom=1e-10)
+    om_min = ref.energy(Lr)[0]
+    Lg = cuda(L0.val)
+    rep = ctx.minimise(Lg, cuda(Sb.val), cuda(Hb.val), MU, max_iter=200, tol_ha_per_atom=1e-9,
+                       precision=lsq.TF32X3, refine_iter=3)
+    g.device_status()
+    assert abs(rep["omega_ev"] - om_min) / lsq.HARTREE_EV / n < 1e-6
 
 
 def test_lnv_metric_cg_matches_oracle_trajectory():

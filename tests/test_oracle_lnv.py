@@ -209,3 +209,35 @@ def test_metric_cg_reaches_the_exact_minimum_in_fewer_steps(full_range):
     assert abs(lnv.energy(Lm)[0] - om_exact) <= 1e-8 * abs(om_exact)
     assert all(b["omega"] <= a["omega"] + 1e-9 for a, b in zip(hm, hm[1:]))
     assert len(hm) < n_plain
+
+
+def test_onsite_inverse_half_pin():
+    """L0 = 1/2 (S_ii)^-1 on the diagonal blocks (the configuration's start), zero elsewhere.
+    Three atoms on a line, so that the diagonal block sits at the start, middle and end of
+    its row.  Symmetric on-site blocks: L0_ii S_ii = I / 2 exactly (to rounding).
+    Non-symmetric ones: 2 L0_ii is symmetric and differs from S_ii^-1 (a library solve) by
+    an antisymmetric matrix, i.e. it is the symmetric part of S_ii^-1."""
+    pos = np.array([[1.0, 5.0, 5.0], [3.0, 5.0, 5.0], [5.0, 5.0, 5.0]])
+    cell = [20.0, 20.0, 20.0]
+    pat = oracle.neighbour_list(pos, cell, 2.5)
+    rows = np.repeat(np.arange(3), np.diff(pat.ptr))
+    assert [list(pat.col[pat.ptr[i]:pat.ptr[i + 1]]) for i in range(3)] == [[0, 1], [0, 1, 2], [1, 2]]
+    rng = np.random.default_rng(8)
+    for symmetric in (True, False):
+        val = 0.1 * rng.standard_normal((pat.nnzb, 4, 4))
+        for p in np.nonzero(rows == pat.col)[0]:
+            m = rng.standard_normal((4, 4))
+            val[p] = (m @ m.T + 4 * np.eye(4)) if symmetric else (m + 5 * np.eye(4))
+        S = oracle.Bsr(pat, 4, val)
+        L0 = OL.onsite_inverse_half(S, pat)
+        for p in range(pat.nnzb):
+            if rows[p] != pat.col[p]:
+                assert not L0.val[p].any()
+                continue
+            Lii, Sii = L0.val[p], S.val[p]
+            assert np.array_equal(Lii, Lii.T)
+            if symmetric:
+                assert np.abs(Lii @ Sii - 0.5 * np.eye(4)).max() < 1e-14
+            else:
+                D = 2.0 * Lii - np.linalg.solve(Sii, np.eye(4))
+                assert np.abs(D + D.T).max() < 1e-14 and np.abs(D).max() > 1e-3
