@@ -645,7 +645,7 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
         }
     }
     if (g->n > 0 && (!A || !B || !C)) return set_error(LSQ_ERR_INVALID_ARG, "null matrix pointer");
-    if (C == A || C == B) return set_error(LSQ_ERR_INVALID_ARG, "C must not alias A or B");
+    if (g->n > 0 && (C == A || C == B)) return set_error(LSQ_ERR_INVALID_ARG, "C must not alias A or B");
     if (dtype == LSQ_TF32X3) {
         // float32 storage; 4 x 4 blocks contract on the tensor cores in split TF32, other block
         // sizes on the float32 FMA kernels

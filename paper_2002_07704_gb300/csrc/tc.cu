@@ -27,8 +27,9 @@
 //    rate, not the bytes, bounded the kernel.)
 //  * Roles.  Six warps issue the copies through a ring of stages, one thread issues the
 //    MMAs, four warps read the accumulator (tcgen05.ld) and write the blocks of C the plan
-//    keeps.  Two accumulators in tensor memory let the epilogue of a tile overlap the MMAs
-//    of the next.  Every wait on an mbarrier is bounded: past the limit the kernel records
+//    keeps.  The tensor core's float32 additions truncate, which biases long sums, so each
+//    stage (8 MMAs) accumulates into a fresh accumulator of a ring of four in tensor memory
+//    and the epilogue adds the stages in float32 with rounding to nearest.  Every wait on an mbarrier is bounded: past the limit the kernel records
 //    an error code in a device word, stops issuing work, waits (bounded) for its copies and
 //    MMAs in flight, frees its tensor memory and returns.
 //
@@ -57,7 +58,8 @@ constexpr int kRows = kJT + kG;               // gathered rows per stage
 constexpr int kPanelX = kJT * kKS * kUnit;    // X rows of a stage (M side), 32 KB
 constexpr int kStageBytes = kRows * kKS * kUnit;  // 48 KB
 constexpr int kN = 8 * kG;                    // accumulator columns of a tile
-constexpr int kTmemCols = 2 * kN;             // two accumulators
+constexpr int kPartials = 4;                  // ring of per-stage accumulators in tensor memory
+constexpr int kTmemCols = kPartials * kN;
 constexpr int kCopyWarps = 6;                 // warps 0-5 copy (4 rows of a stage each)
 constexpr int kMmaWarp = 6;                   // one thread of warp 6 issues the MMAs
 constexpr int kThreads = 352;                 // warps 7-10 read the accumulator
@@ -436,16 +438,16 @@ struct TcArgs {
 __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
-    // bars: full[kStages], empty[kStages], tfull[2], tempty[2], drain[1]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 5);
+    // bars: full[kStages], empty[kStages], tfull[kPartials], tempty[kPartials], drain[1]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 2 * kPartials + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = smem_u32(bars);
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
     auto tfull = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
-    auto tempty = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
-    const uint32_t drain = bar0 + 8u * (2 * kStages + 4);
+    auto tempty = [&](int b) { return bar0 + 8u * (2 * kStages + kPartials + b); };
+    const uint32_t drain = bar0 + 8u * (2 * kStages + 2 * kPartials);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
             mbar_init(full(s), 32 * kCopyWarps);
             mbar_init(empty(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kPartials; ++b) {
             mbar_init(tfull(b), 1);
             mbar_init(tempty(b), 4);
         }
@@ -511,21 +513,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
-            // ---- MMAs: per stage 8 of M = 128, N = 64, K = 8 (two atoms k)
+            // ---- MMAs: per stage 8 of M = 128, N = 64, K = 8 (two atoms k), into a fresh
+            // accumulator of the ring (the tensor core's float32 additions truncate, so sums
+            // are kept to one stage there and the stages are added by the epilogue)
             constexpr uint32_t idesc = idesc_tf32(128, kN);
-            int it = 0, tt = 0;
+            int it = 0;
             bool ok = true;
-            int t = blockIdx.x;
-            int nk = t < p.ntiles ? p.tile_nk[t] : 0;
-            for (; t < p.ntiles && ok; t += gridDim.x, ++tt) {
-                const int tn = t + (int)gridDim.x;
-                const int nk_next = tn < p.ntiles ? p.tile_nk[tn] : 0;
-                const int buf = tt & 1;
-                ok = mbar_wait(tempty(buf), ((uint32_t)(tt >> 1) & 1u) ^ 1u, abort_flag, p.err, 3);
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * kN);
+            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                const int nk = p.tile_nk[t];
                 for (int k0 = 0; k0 < nk; k0 += kKS, ++it) {
+                    const int buf = it % kPartials;
+                    ok = mbar_wait(tempty(buf), ((uint32_t)(it / kPartials) & 1u) ^ 1u, abort_flag, p.err, 3);
+                    if (!ok) break;
                     const int slot = it % kStages;
                     ok = mbar_wait(full(slot), (uint32_t)(it / kStages) & 1u, abort_flag, p.err, 2);
                     if (!ok) break;
@@ -533,18 +532,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                     // through the async proxy
                     fence_proxy_async();
                     tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(buf * kN);
                     const uint32_t sa = sbase + (uint32_t)slot * kStageBytes, sb = sa + kPanelX;
 #pragma unroll
                     for (int kk = 0; kk < kKS; kk += 2) {
                         const uint64_t ad = sdesc(sa + kk * kUnit, kUnit, kKS * kUnit);
                         const uint64_t bd = sdesc(sb + kk * kUnit, kUnit, kKS * kUnit);
-                        mma_tf32(d, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
                     mma_commit(empty(slot));
+                    mma_commit(tfull(buf));
                 }
-                if (!ok) break;
-                mma_commit(tfull(buf));
-                nk = nk_next;
             }
             // every MMA issued has completed before tensor memory is released
             mma_commit(drain);
@@ -556,37 +554,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                 }
         }
     } else {
-        // ---- epilogue: thread row m = 8 jj + 4 h + c of the accumulator
+        // ---- epilogue: thread row m = 8 jj + 4 h + c of the accumulator.  The stages' partial
+        // accumulators of a tile are added here in float32 (rounded to nearest), then the
+        // {hi, lo} cross terms are combined and the blocks of C written.
         const int sub = warp & 3;
         const int m = 32 * sub + lane;
         const int jj = m >> 3, h = (m >> 2) & 1, c = m & 3;
-        int tt = 0;
-        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++tt) {
-            const int buf = tt & 1;
+        const uint32_t tlane = tmem + ((uint32_t)(32 * sub) << 16);
+        int it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+            const int nst = p.tile_nk[t] / kKS;
             int32_t cp[kG];
 #pragma unroll
             for (int ii = 0; ii < kG; ++ii) cp[ii] = p.cpos[(int64_t)128 * t + kJT * ii + jj];
-            bool ok = mbar_wait(tfull(buf), (uint32_t)(tt >> 1) & 1u, abort_flag, p.err, 4);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            tc_fence_after();
-            float s[kG][4];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(buf * kN);
+            float acc[kN];
 #pragma unroll
-            for (int q = 0; q < kN / 16; ++q) {
-                uint32_t v[16];
-                tmem_ld16(taddr + 16 * q, v);
-                tmem_wait_ld();
-                // columns 16 q .. 16 q + 15: atoms i = 2q and 2q + 1, each hi rows 0-3 then lo rows 0-3
+            for (int e = 0; e < kN; ++e) acc[e] = 0.f;
+            for (int st = 0; st < nst; ++st, ++it) {
+                const int buf = it % kPartials;
+                ok = mbar_wait(tfull(buf), (uint32_t)(it / kPartials) & 1u, abort_flag, p.err, 4);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
 #pragma unroll
-                for (int u = 0; u < 2; ++u)
+                for (int q = 0; q < kN / 16; ++q) {
+                    uint32_t v[16];
+                    tmem_ld16(tlane + (uint32_t)(buf * kN + 16 * q), v);
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        s[2 * q + u][r] = __uint_as_float(v[8 * u + r]) + __uint_as_float(v[8 * u + 4 + r]);
+                    for (int e = 0; e < 16; ++e) acc[16 * q + e] += __uint_as_float(v[e]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty(buf));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty(buf));
+            if (!ok) break;
+            // columns 8 ii + 4 h' + r: atom i = ii, hi (h' = 0) or lo (h' = 1) rows r of A_ik
+            float s[kG][4];
+#pragma unroll
+            for (int ii = 0; ii < kG; ++ii)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) s[ii][r] = acc[8 * ii + r] + acc[8 * ii + 4 + r];
             // rows hi and lo of the same (j, c) are lanes l and l + 4
 #pragma unroll
             for (int ii = 0; ii < kG; ++ii)

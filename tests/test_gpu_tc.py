@@ -135,7 +135,7 @@ def test_tf32x3_ragged_group_and_split_precision():
 def test_tf32x3_empty_and_other_block_sizes():
     """No atoms: nothing to do.  b = 13 with TF32X3 runs the float32 FMA kernels."""
     g0 = gpu_geometry(np.zeros((0, 3)), [10.0, 10.0, 10.0], [3.0])
-    z = torch.zeros((1, 4, 4), dtype=torch.float32, device="cuda")
+    z = torch.zeros((0, 4, 4), dtype=torch.float32, device="cuda")
     assert lsq.block_matmul(g0, 4, z, 0, z.clone(), 0, z.clone(), 0, precision=lsq.TF32X3) == 0
     pos, cell = si(1, 0.1, config_seed(0) + 3)
     ranges = [3.0, 4.0]
