@@ -2,17 +2,22 @@
 """Benchmark of the LNV hot path on 4096-atom Si (8x8x8 diamond cells).
 
 One "step" is one conjugate-gradient step of the LNV minimisation: the
-energy and gradient (six truncated block products, traces, the gradient
-combine), the exact cubic line search (four more products and traces)
-and the update of L.  The headline value is mixed-precision (float32
-products, float64 traces and CG) steps per second; the float64 path, the
-dominant product kernel's roofline, an end-to-end number through the
-public API with host buffers, and the CPU oracle timed on a row sample
-of the same workload are reported beside it.
+energy and gradient (truncated block products, traces, the gradient
+combine), the exact cubic line search (more products and traces) and the
+update of L.  The headline value is mixed-precision steps per second: the
+configuration's mixed mode, split-TF32 block products on the tensor cores
+with FP32 accumulation (per product the faster of those and the FP32 FMA
+schedules, timed by the first steps), float32 storage, float64 traces and
+CG.  Beside it: FP32-FMA-only mixed steps, the float64 path, the runs to
+|dOmega|/N < 1e-6 Ha/atom with their time to solution, the dominant
+product's tensor-core and FMA rooflines against measured peaks, an
+end-to-end number through the public API with host buffers, and the CPU
+oracle timed on a row sample of the same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch     # 48 independent systems, 4x4 and 13x13 blocks
   python bench.py --workload sizes     # ms/step against atoms, 512 ... 32768 (O(N))
+  python bench.py --workload oracle    # the CPU oracle on this host's cores (no GPU)
 
 With N > 1 (torchrun) every rank runs an independent replica of the
 workload on its own GPU (the path has no exchange step).
@@ -63,10 +68,14 @@ def parse():
                    help="si4096: the 4096-atom headline (default); batch: the 48-system batched "
                         "workload (24 systems with 4x4 blocks, 24 with 13x13); oracle: the CPU "
                         "oracle timed on the host cores (1 thread and all), no GPU")
-    p.add_argument("--only-product", nargs="?", const="sl_qt", choices=["sl_qt", "ls_l", "xl"],
+    p.add_argument("--only-product", nargs="?", const="sl_qt", choices=["sl_qt", "ls_l", "xl", "tc_sl_qt"],
                    help="run only one kernel three times (for profilers): sl_qt, the roofline "
-                        "product (default), ls_l, the bsgemm product, or xl, the XL-BOMD "
-                        "propagation of X with dissipation (1728 atoms: 8 arrays of 210 MB)")
+                        "product (default), ls_l, the bsgemm product, tc_sl_qt, the roofline product "
+                        "on the tensor cores (LSQ_TF32X3), or xl, the XL-BOMD propagation of X with "
+                        "dissipation (1728 atoms: 8 arrays of 210 MB)")
+    p.add_argument("--product-cells", type=int, default=N_CELLS,
+                   help="--only-product: diamond cells per edge of the system (8: the 4096-atom "
+                        "workload; 6: 1728 atoms, a small case for multi-pass profiler captures)")
     return p.parse_args()
 
 
@@ -234,6 +243,22 @@ def roofline_product(lsq, geom, SL, Q, out, precision=None):
                             trans_b=True, triangle=2)
 
 
+def traffic_of(fname, src, product_id):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a product kernel
+    from a committed ncu summary under profiles/, or None when the summary is of another product
+    or the kernel's source has changed since the capture (sha256 recorded in the summary)."""
+    try:
+        import hashlib
+        tj = json.load(open(os.path.join(ROOT, "profiles", fname)))
+        code = open(os.path.join(ROOT, "paper_2002_07704_gb300", "csrc", src), "rb").read()
+        if tj.get("product_id") == product_id and tj.get(src.replace(".", "_") + "_sha256") == \
+                hashlib.sha256(code).hexdigest():
+            return tj.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def tensor_peaks():
     """(bf16, tf32) dense tensor TFLOP/s: the pool's measured cuBLAS bf16 burst, and tf32 at the
     nominal tf32/bf16 ratio of GB300's dense tensor rates (1.1 / 2.25 PFLOP/s)."""
@@ -394,7 +419,8 @@ def run_ours(args):
     dfma = lsq.measure_peak(lsq.F64)
 
     # --- workload (one replica per rank) ---
-    pos, cell = diamond_si_positions(N_CELLS, SIGMA, config_seed(1) + 1000 * rank)
+    ncells = args.product_cells if args.only_product else N_CELLS
+    pos, cell = diamond_si_positions(ncells, SIGMA, config_seed(1) + 1000 * rank)
     ranges = lsq.lnv_required_ranges(R_S, R_H, R_L)
     geom = lsq.Geometry(torch.from_numpy(pos).cuda(), cell, ranges)
     rp, col = geom.pattern(1)
@@ -420,19 +446,25 @@ def run_ours(args):
             for _ in range(3):
                 lsq.block_matmul(geom, B, LS, 3, Lc, 2, LSL, 5, precision=lsq.F32, trans_b=True)
         else:
+            prec = lsq.TF32X3 if args.only_product == "tc_sl_qt" else lsq.F32
             for _ in range(3):
-                roofline_product(lsq, geom, LS, Qx, Gx)
+                roofline_product(lsq, geom, LS, Qx, Gx, precision=prec)
+            if prec == lsq.TF32X3:
+                geom.device_status()
+                print("tensor-core plan:", json.dumps(geom.product_plan_info(3, 5, 2, 2)))
         torch.cuda.synchronize()
-        print("only-product done")
+        print("only-product done: %d atoms" % geom.n_atoms)
         return
 
     def steps(L, k, prec):
         return ctx.minimise(L, Sd, Hd, MU, max_iter=k, precision=prec, refine_iter=0,
                             final_eval=False)
 
-    # --- mixed precision: warm-up, then the timed steps ---
+    # --- mixed precision (the configuration's mode: split-TF32 tensor-core products with FP32
+    # accumulation, float64 traces and CG; per product the faster of those and the FP32 FMA
+    # schedules, timed by the first steps): warm-up, then the timed steps ---
     L = L0.clone()
-    steps(L, args.warmup, lsq.F32)
+    steps(L, max(args.warmup, 2), lsq.TF32X3)
     L = L0.clone()
     clk = Clocks(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,7 +472,7 @@ def run_ours(args):
     n0 = lsq.launch_count()
     clk.start()
     e0.record(stream)
-    rep = steps(L, args.steps, lsq.F32)
+    rep = steps(L, args.steps, lsq.TF32X3)
     e1.record(stream)
     barrier()
     clocks = clk.stop()
@@ -465,22 +497,21 @@ def run_ours(args):
     ms64 = e0.elapsed_time(e1) / max(int(rep64["iterations"]), 1)
     # accuracy of the mixed path: float64 Omega of both iterates after the same number of steps
     Lm = L0.clone()
-    steps(Lm, args.fp64_steps, lsq.F32)
+    steps(Lm, args.fp64_steps, lsq.TF32X3)
     om_m, _ = ctx.energy_gradient(Lm, Sd, Hd, MU)
     om_d, _ = ctx.energy_gradient(L64, Sd, Hd, MU)
     acc = abs(om_m - om_d) / lsq.HARTREE_EV / geom.n_atoms
 
-    # --- mixed precision with LSQ_TF32X3: per product the faster of the FP32 FMA schedules and
-    # the split-TF32 tensor-core kernel (the first steps time both) ---
+    # --- mixed precision with FP32 FMA products only (LSQ_F32) ---
     Lt = L0.clone()
-    steps(Lt, max(args.warmup, 2), lsq.TF32X3)
+    steps(Lt, args.warmup, lsq.F32)
     Lt = L0.clone()
     barrier()
     e0.record(stream)
-    rep_tc = steps(Lt, args.steps, lsq.TF32X3)
+    rep_f32 = steps(Lt, args.steps, lsq.F32)
     e1.record(stream)
     barrier()
-    ms_tc = e0.elapsed_time(e1) / max(int(rep_tc["iterations"]), 1)
+    ms_f32 = e0.elapsed_time(e1) / max(int(rep_f32["iterations"]), 1)
     # the step's products (range ids: 0 R_S = R_H, 2 R_L, 3 R_L + R_S, 5 R_H + R_L + R_S) and the
     # kernel the timing chose for each
     STEP_PRODUCTS = [("L.S", 2, 0, 3, 0), ("SL.(Q+Q^T)^T lower", 3, 5, 2, 3), ("SL.Q^T upper", 3, 5, 2, 2),
@@ -563,6 +594,7 @@ def run_ours(args):
     tms = e0.elapsed_time(e1) / reps
     geom.device_status()
     tinfo = geom.product_plan_info(3, 5, 2, 2)
+    traffic_tc = traffic_of("traffic_tc.json", "tc.cu", "tc_" + ROOFLINE_PRODUCT)
     bf16_peak, tf32_peak = tensor_peaks()
     # the float64 path: algorithmic flops of one CG step (the step's products, Q formed afresh
     # every tenth step) over the measured DFMA rate
@@ -578,18 +610,7 @@ def run_ours(args):
     fp64_step_flops = 2.0 * B ** 3 * step_trip
     # algorithmic bytes: A and B read once, the upper half of C written (float32)
     abytes = (geom.nnzb(3) + geom.nnzb(5) + geom.nnzb(2) / 2.0) * B * B * 4
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            import hashlib
-            src = open(os.path.join(ROOT, "paper_2002_07704_gb300", "csrc", "plan.cu"), "rb").read()
-            if (tj.get("plan_cu_sha256") == hashlib.sha256(src).hexdigest()
-                    and tj.get("product_id") == ROOFLINE_PRODUCT):
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = traffic_of("traffic.json", "plan.cu", ROOFLINE_PRODUCT)
 
     # --- the sparse inverse overlap (Hotelling) on L's range, the LNV metric ---
     # float32 products from the scaled start, then float64 steps continuing from that X
@@ -678,7 +699,7 @@ def run_ours(args):
     Ldev = Lh.to("cuda", non_blocking=True)
     Sdev = Sh.to("cuda", non_blocking=True)
     Hdev = Hh.to("cuda", non_blocking=True)
-    rep_e2e = ctx.minimise(Ldev, Sdev, Hdev, MU, max_iter=args.steps, precision=lsq.F32,
+    rep_e2e = ctx.minimise(Ldev, Sdev, Hdev, MU, max_iter=args.steps, precision=lsq.TF32X3,
                            refine_iter=0, final_eval=True)
     Lout.copy_(Ldev, non_blocking=True)
     torch.cuda.synchronize()
@@ -715,48 +736,58 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "float32 products, float64 traces/CG",
+            "config": {"workload": WORKLOAD,
+                       "precision": "mixed: split-TF32 (hi + lo) block products on the tensor cores with "
+                                    "FP32 accumulation where the per-product timing picks them, FP32 FMA "
+                                    "elsewhere; float32 storage, float64 traces and CG",
                        "l2": "inputs larger than L2 (LSL alone is 885 MB in float32)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "product_kernels": choices},
             "fp64": {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64, "steps": args.fp64_steps,
                      "roofline": {"bound": "fp64", "achieved": fp64_step_flops / ms64 / 1e9, "peak": dfma,
                                   "unit": "TFLOP/s", "frac": fp64_step_flops / ms64 / 1e9 / dfma,
                                   "flops_per_step": fp64_step_flops,
                                   "peak_note": "measured DFMA loop (lsq_measure_peak)"}},
-            "mixed_tf32x3": {"steps_per_s": 1000.0 / ms_tc, "ms_per_step": ms_tc,
-                             "steps": int(rep_tc["iterations"]), "product_kernels": choices},
+            "mixed_f32": {"steps_per_s": 1000.0 / ms_f32, "ms_per_step": ms_f32,
+                          "steps": int(rep_f32["iterations"]),
+                          "precision": "FP32 FMA products only (LSQ_F32), float64 traces and CG"},
             "mixed_vs_fp64_omega_ha_per_atom": acc,
             "mixed_vs_fp64_same_steps": {"steps": args.fp64_steps, "ha_per_atom": acc},
             "mixed_vs_fp64_at_tol": to_tol,
             "bsgemm": {"product": "LS.L truncated to 23.2 A (P2 of the product schedule, every block)",
                        "triples": trip,
                        "gflops": flops / kms / 1e6, "ms": kms, "frac_fp32_peak": flops / kms / 1e9 / fp32_peak},
-            "roofline": {"bound": "alu", "achieved": rflops / rms / 1e9, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": rflops / rms / 1e9 / fp32_peak,
-                         "traffic": traffic,
+            "roofline": {"bound": "tensor", "kernel": "k_tc_product (LSQ_TF32X3)",
                          "product": "SL.Q^T on the upper triangle of the 10 A range (A 16.6 A, B 23.2 A): "
-                                    "the shape of three of the step's products",
-                         "triples": rtrip, "ms": rms,
-                         "kernel": "k_mm_plan_b4_rb<float, ...> (schedule picked by the autotuner)",
-                         "hbm_frac": abytes / rms / 1e6 / hbm_peak, "hbm_peak_kind": hbm_kind,
-                         "peak_note": "measured FFMA loop (lsq_measure_peak); nominal below",
-                         "peak_nominal": fp32_nominal, "frac_nominal": rflops / rms / 1e9 / fp32_nominal},
-            "roofline_tensor": {"bound": "tensor", "kernel": "k_tc_product (LSQ_TF32X3)",
-                                "product": "the same SL.Q^T, upper triangle of 10 A",
-                                "ms": tms, "achieved": rflops / tms / 1e9, "unit": "TFLOP/s",
-                                "achieved_note": "algorithmic flops (2 b^3 per block triple) per launch, split "
-                                                 "conversions of both operands included in the time",
-                                "executed": 512.0 * tinfo["dense_triples"] / tms / 1e9,
-                                "executed_note": "tensor flops the MMAs execute: 4 x 128 per dense block "
-                                                 "triple (hi/lo x hi/lo, zero blocks of the tiles included)",
-                                "peak": tf32_peak, "frac": 512.0 * tinfo["dense_triples"] / tms / 1e9 / tf32_peak,
-                                "peak_note": "dense tf32 = measured cuBLAS bf16 burst (%.0f) x 1.1 / 2.25" % bf16_peak,
-                                "useful_fraction": tinfo["triples"] / max(tinfo["dense_triples"], 1),
-                                "gathered_gbs": 128.0 * tinfo["blocks_gathered"] / tms / 1e6,
-                                "gathered_bytes": 128 * tinfo["blocks_gathered"],
-                                "vs_fma": rms / tms},
+                                    "the shape of three of the step's products, which the mixed step runs "
+                                    "on the tensor cores",
+                         "triples": rtrip, "ms": tms,
+                         "achieved": 512.0 * tinfo["dense_triples"] / tms / 1e9, "unit": "TFLOP/s",
+                         "achieved_note": "tensor flops the MMAs execute per launch (4 x 128 per dense block "
+                                          "triple: hi/lo x hi/lo, zero blocks of the tiles included) over the "
+                                          "launch time, split conversions of both operands included",
+                         "peak": tf32_peak, "frac": 512.0 * tinfo["dense_triples"] / tms / 1e9 / tf32_peak,
+                         "peak_note": "dense tf32 of measured: cuBLAS bf16 burst (%.0f) x 1.1 / 2.25 (the "
+                                      "nominal tf32 / bf16 ratio)" % bf16_peak,
+                         "traffic": traffic_tc,
+                         "algorithmic_tflops": rflops / tms / 1e9,
+                         "useful_fraction": tinfo["triples"] / max(tinfo["dense_triples"], 1),
+                         "gathered_gbs": 128.0 * tinfo["blocks_gathered"] / tms / 1e6,
+                         "gathered_bytes": 128 * tinfo["blocks_gathered"],
+                         "bound_note": "gathering the operand blocks (scattered 128-byte lines through L2) "
+                                       "bounds this kernel, not the tensor pipe",
+                         "vs_fma": rms / tms},
+            "roofline_fma": {"bound": "alu", "achieved": rflops / rms / 1e9, "peak": fp32_peak,
+                             "unit": "TFLOP/s", "frac": rflops / rms / 1e9 / fp32_peak,
+                             "traffic": traffic,
+                             "product": "the same SL.Q^T with FP32 FMA (LSQ_F32)",
+                             "triples": rtrip, "ms": rms,
+                             "kernel": "k_mm_plan_b4_rb<float, ...> (schedule picked by the autotuner)",
+                             "hbm_frac": abytes / rms / 1e6 / hbm_peak, "hbm_peak_kind": hbm_kind,
+                             "peak_note": "measured FFMA loop (lsq_measure_peak); nominal below",
+                             "peak_nominal": fp32_nominal, "frac_nominal": rflops / rms / 1e9 / fp32_nominal},
             "hotelling": dict(hot, workload="X = S^-1 approximated on the 10 A range by "
                                              "X <- 2X - (X S) X from X0 = S / s^2, the LNV metric of Sec. 2.3.2"),
             "canonical": canon,
@@ -768,7 +799,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "last_report": {"mixed": rep, "fp64": rep64, "mixed_tf32x3": rep_tc, "e2e": rep_e2e},
+            "last_report": {"mixed": rep, "fp64": rep64, "mixed_f32": rep_f32, "e2e": rep_e2e},
         }
         print(json.dumps(line))
     if dist is not None:

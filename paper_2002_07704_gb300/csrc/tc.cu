@@ -29,9 +29,10 @@
 //    MMAs, four warps read the accumulator (tcgen05.ld) and write the blocks of C the plan
 //    keeps.  The tensor core's float32 additions truncate, which biases long sums, so each
 //    stage (8 MMAs) accumulates into a fresh accumulator of a ring of four in tensor memory
-//    and the epilogue adds the stages in float32 with rounding to nearest.  Every wait on an mbarrier is bounded: past the limit the kernel records
-//    an error code in a device word, stops issuing work, waits (bounded) for its copies and
-//    MMAs in flight, frees its tensor memory and returns.
+//    and the epilogue adds the stages in float32 with rounding to nearest.  Every wait on an
+//    mbarrier is bounded: past the limit the kernel records an error code in a device word,
+//    stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its tensor
+//    memory and returns.
 //
 // The plan (which blocks to gather, where to write) is built on the GPU once per geometry
 // and product, like the FMA path's plan.
