@@ -199,9 +199,10 @@ int lsq_measure_peak(int precision, double *tflops_host, void *stream);
  * lsq_block_matmul_tri), into info_host[5]: the block triples of the computed blocks; the
  * block triples the MMAs execute (16 j x 8 i x k-list per tile, zero blocks included; each
  * costs 4 x 128 tensor flops with the split operands); the blocks gathered per launch (128
- * bytes each); the tiles; and, for products the LNV path ran with LSQ_TF32X3, which kernel
- * the timing chose (-1 not timed, 0 FP32 FMA, 1 tensor cores).  Host only.  No counterpart
- * in the paper. */
+ * bytes each); the tiles (these four are -1 when no plan is held: the LNV path's timing
+ * chose the FMA kernel and dropped it); and, for products the LNV path ran with LSQ_TF32X3,
+ * which kernel the timing chose (-1 not timed, 0 FP32 FMA, 1 tensor cores).  Host only.
+ * No counterpart in the paper. */
 int lsq_product_plan_info(lsq_geom g, int range_a, int range_b, int range_c, int triangle,
                           int64_t *info_host);
 

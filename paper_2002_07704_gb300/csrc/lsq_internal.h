@@ -122,12 +122,15 @@ struct TcPlan {
     DevBuf<int32_t> cta_stages;  // [grid] stages of each CTA
     DevBuf<int32_t> pos;         // stage records: block indices in op(A) or op(B)^T, or -1
     DevBuf<int32_t> cpos;        // [128 ntiles]: block (i, j) of C, -1 if not computed
-    // kMixedAuto products: -1 not yet timed, 0 the FP32 FMA schedule won, 1 this kernel won;
-    // and the two times (ms) of that comparison
-    int auto_choice = -1;
-    float auto_ms[2] = {0.f, 0.f};
     TcPlan() = default;
     TcPlan(TcPlan &&) = default;
+};
+
+// Outcome of the timing of a kMixedAuto product: 0 the FP32 FMA schedule won, 1 the
+// tensor-core kernel won; the two times (ms) of that comparison.
+struct TcChoice {
+    int choice = 0;
+    float ms[2] = {0.f, 0.f};
 };
 
 struct Reducer {
@@ -167,6 +170,8 @@ struct lsq_geom_s {
     // (hi, lo) operand copies they read (grown on demand), and the device error word of the
     // kernels with bounded waits (0: none)
     std::map<std::tuple<int, int, int>, lsq::TcPlan> tcplans;
+    // the kernel each kMixedAuto product was timed to run on (same keys)
+    std::map<std::tuple<int, int, int>, lsq::TcChoice> tc_choice;
     lsq::DevBuf<char> tc_a, tc_x;
     lsq::DevBuf<int> dev_err;
     // workspace of lsq_hotelling_inverse (grown on demand)

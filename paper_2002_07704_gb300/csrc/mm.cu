@@ -28,6 +28,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include <algorithm>
 #include <cstdint>
@@ -586,23 +587,51 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
     if (dtype != LSQ_F64 && dtype != LSQ_F32 && dtype != LSQ_TF32X3 && dtype != kMixedAuto)
         return set_error(LSQ_ERR_INVALID_ARG, "precision must be LSQ_F64, LSQ_F32 or LSQ_TF32X3");
     if (dtype == kMixedAuto) {
-        // the faster of the FP32 FMA schedules and the tensor-core kernel for this product
+        // the faster of the FP32 FMA schedules and the tensor-core kernel for this product,
+        // timed on its first call with beta = 0 and remembered by g; the losing kernel's plan
+        // is dropped (a later explicit call of that precision builds it again)
         if (b != 4 || g->n == 0) {
             dtype = LSQ_F32;
         } else {
             const int upper = sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0);
-            TcPlan *tp = nullptr;
-            int prc = tc_plan_get(g, ra, rb, rc, upper, &tp, s);
-            if (prc == LSQ_ERR_OOM || prc == LSQ_ERR_UNSUPPORTED) {
-                (void)cudaGetLastError();
-                clear_error();
-                dtype = LSQ_F32;
-            } else if (prc != LSQ_OK) {
-                return prc;
-            } else if (tp->auto_choice < 0 && beta != 0.0) {
+            const auto key = std::make_tuple(ra, rb, rc + 1000 * upper);
+            auto ch = g->tc_choice.find(key);
+            if (ch == g->tc_choice.end()) {
+                // a fixed choice instead of the timing (profiler runs, whose serialised launches
+                // distort it): LSQ_TC_CHOICE="ra:rb:rc:tri=k,...,all=k", k = 1 tensor cores, 0 FMA,
+                // tri the triangle code of the plans (0 all, 1 upper, 2 lower)
+                if (const char *env = std::getenv("LSQ_TC_CHOICE")) {
+                    int fixed = -1;
+                    for (const char *q = env; *q;) {
+                        int a0, a1, a2, a3, k;
+                        if (std::sscanf(q, "%d:%d:%d:%d=%d", &a0, &a1, &a2, &a3, &k) == 5) {
+                            if (a0 == ra && a1 == rb && a2 == rc && a3 == upper) fixed = k;
+                        } else if (std::sscanf(q, "all=%d", &k) == 1) {
+                            if (fixed < 0) fixed = k;
+                        }
+                        const char *c = std::strchr(q, ',');
+                        if (!c) break;
+                        q = c + 1;
+                    }
+                    if (fixed >= 0) ch = g->tc_choice.emplace(key, TcChoice{fixed ? 1 : 0, {0.f, 0.f}}).first;
+                }
+            }
+            if (ch != g->tc_choice.end()) {
+                dtype = ch->second.choice == 1 ? LSQ_TF32X3 : LSQ_F32;
+            } else if (beta != 0.0) {
                 dtype = LSQ_F32;  // no timing run on an accumulating call: FMA until timed
             } else {
-                if (tp->auto_choice < 0) {
+                TcPlan *tp = nullptr;
+                const int prc = tc_plan_get(g, ra, rb, rc, upper, &tp, s);
+                if (prc == LSQ_ERR_OOM || prc == LSQ_ERR_UNSUPPORTED) {
+                    (void)cudaGetLastError();
+                    clear_error();
+                    g->tc_choice[key] = TcChoice{0, {0.f, 0.f}};
+                    dtype = LSQ_F32;
+                } else if (prc != LSQ_OK) {
+                    return prc;
+                } else {
+                    const int64_t tr = tp->triples;
                     // time each once more after its own first call (plan, tuning) has run
                     cudaEvent_t e0, e1;
                     LSQ_CUDA_TRY(cudaEventCreate(&e0));
@@ -619,28 +648,19 @@ int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, in
                     }
                     cudaEventDestroy(e0);
                     cudaEventDestroy(e1);
-                    tp->auto_choice = ms[1] < ms[0] ? 1 : 0;
-                    tp->auto_ms[0] = ms[0];
-                    tp->auto_ms[1] = ms[1];
+                    const int choice = ms[1] < ms[0] ? 1 : 0;
+                    g->tc_choice[key] = TcChoice{choice, {ms[0], ms[1]}};
                     if (std::getenv("LSQ_TUNE_LOG"))
                         std::fprintf(stderr, "lsq autotune: ranges (%g, %g, %g) tri %d: FP32 FMA %.3f ms, TF32X3 %.3f ms -> %s\n",
                                      g->pats[ra].R, g->pats[rb].R, g->pats[rc].R, upper, ms[0], ms[1],
-                                     tp->auto_choice ? "tensor cores" : "FMA");
-                    if (tp->auto_choice == 1) {
-                        // the FMA plan of this product is not needed any more
-                        g->pplans.erase(std::make_tuple(ra, rb, rc + 1000 * upper));
-                    } else {
-                        // nor the tensor-core plan's records (the choice itself is kept)
-                        tp->pos.release();
-                        tp->cpos.release();
-                        tp->tile_nk.release();
-                        tp->tile_posoff.release();
-                        tp->cta_stages.release();
-                    }
-                    if (triples) *triples = tp->triples;
+                                     choice ? "tensor cores" : "FMA");
+                    if (choice == 1)
+                        g->pplans.erase(key);   // the FMA plan of this product is not needed any more
+                    else
+                        g->tcplans.erase(key);  // nor the tensor-core plan (tp is invalid from here)
+                    if (triples) *triples = tr;
                     return LSQ_OK;  // C holds the product (both runs wrote the same result)
                 }
-                dtype = tp->auto_choice == 1 ? LSQ_TF32X3 : LSQ_F32;
             }
         }
     }

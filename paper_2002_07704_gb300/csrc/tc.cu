@@ -786,6 +786,8 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     LSQ_TRY(tc_plan_get(g, ra, rb, rc, upper, &p, s));
     if (triples) *triples = p->triples;
     if (g->n == 0 || g->pats[rc].nnzb == 0 || p->ntiles == 0) return LSQ_OK;
+    if (!p->pos.p || !p->cpos.p || !p->tile_nk.p || !p->tile_posoff.p || !p->cta_stages.p)
+        return set_error(LSQ_ERR_CUDA, "tensor-core plan without its records");
     // op(A) and X = op(B)^T (B's rows when trans_b, else B read through its transpose map) in
     // split form, in buffers held by g
     LSQ_TRY(split_operand(g, ra, ta != 0, A, g->tc_a, s));
@@ -826,14 +828,20 @@ extern "C" int lsq_product_plan_info(lsq_geom g, int range_a, int range_b, int r
     if (!info_host) return set_error(LSQ_ERR_INVALID_ARG, "info_host is null");
     if (triangle < 0 || triangle > 3) return set_error(LSQ_ERR_INVALID_ARG, "triangle must be 0..3");
     const int upper = triangle == 3 ? 2 : (triangle >= 1 ? 1 : 0);
-    auto f = g->tcplans.find(std::make_tuple(range_a, range_b, range_c + 1000 * upper));
-    if (f == g->tcplans.end()) return set_error(LSQ_ERR_INVALID_ARG, "no tensor-core plan for these ranges yet");
-    const TcPlan &p = f->second;
-    info_host[0] = p.triples;
-    info_host[1] = p.dense_triples;
-    info_host[2] = p.units;
-    info_host[3] = p.ntiles;
-    info_host[4] = p.auto_choice;
+    const auto key = std::make_tuple(range_a, range_b, range_c + 1000 * upper);
+    auto f = g->tcplans.find(key);
+    auto ch = g->tc_choice.find(key);
+    if (f == g->tcplans.end() && ch == g->tc_choice.end())
+        return set_error(LSQ_ERR_INVALID_ARG, "no tensor-core plan or timing for these ranges yet");
+    for (int k = 0; k < 4; ++k) info_host[k] = -1;
+    if (f != g->tcplans.end()) {
+        const TcPlan &p = f->second;
+        info_host[0] = p.triples;
+        info_host[1] = p.dense_triples;
+        info_host[2] = p.units;
+        info_host[3] = p.ntiles;
+    }
+    info_host[4] = ch == g->tc_choice.end() ? -1 : ch->second.choice;
     return LSQ_OK;
 }
 

@@ -186,3 +186,65 @@ def test_tf32x3_full_size_sampled_rows():
     assert np.abs(got[sel] - ref.val[sel]).max() <= 1e-5 * scale
     up = pc.col >= prow
     assert np.abs(got[up] - Cf.double().cpu().numpy()[up]).max() <= 2e-5 * scale
+
+
+
+def _step_choices(g, nr):
+    """(range_a, range_b, range_c, upper) -> kernel the mixed step chose (1 tensor cores, 0 FMA)."""
+    out = {}
+    for ra in range(nr):
+        for rb in range(nr):
+            for rc in range(nr):
+                for tri, upper in ((0, 0), (2, 1), (3, 2)):
+                    try:
+                        info = g.product_plan_info(ra, rb, rc, tri)
+                    except lsq.LsqError:
+                        continue
+                    if info["auto_choice"] >= 0:
+                        out[(ra, rb, rc, tri)] = info["auto_choice"]
+    return out
+
+
+def _explicit_products_match(g, choices, seed):
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    for (ra, rb, rc, tri) in choices:
+        A = torch.randn((g.nnzb(ra), 4, 4), dtype=torch.float32, device="cuda", generator=gen)
+        B = torch.randn((g.nnzb(rb), 4, 4), dtype=torch.float32, device="cuda", generator=gen)
+        Ct = torch.zeros((g.nnzb(rc), 4, 4), dtype=torch.float32, device="cuda")
+        Cf = torch.zeros_like(Ct)
+        lsq.block_matmul(g, 4, A, ra, B, rb, Ct, rc, precision=lsq.TF32X3, trans_b=True, triangle=tri)
+        lsq.block_matmul(g, 4, A, ra, B, rb, Cf, rc, precision=lsq.F32, trans_b=True, triangle=tri)
+        torch.cuda.synchronize()
+        g.device_status()
+        assert g.product_plan_info(ra, rb, rc, tri)["tiles"] > 0
+        assert (Ct - Cf).abs().max().item() <= 2e-5 * Cf.abs().max().item()
+
+
+def test_explicit_tf32x3_after_the_mixed_choice(monkeypatch):
+    """The mixed step (LSQ_TF32X3 requested of the LNV path) keeps one kernel per product and
+    drops the other's plan.  A later explicit LSQ_TF32X3 product on the same ranges builds its
+    tensor-core plan again and matches LSQ_F32: after the timing (64 atoms, where the FMA
+    kernels win most products) and after LSQ_TC_CHOICE=all=0 fixed every choice to FMA."""
+    pos, cell = si(2, 0.05, config_seed(0))
+    ranges = lsq.lnv_required_ranges(6.6, 6.6, 8.0)
+    S_, H_ = None, None
+    for forced in (False, True):
+        if forced:
+            monkeypatch.setenv("LSQ_TC_CHOICE", "all=0")
+        g = gpu_geometry(pos, cell, ranges)
+        ctx = lsq.Lnv(g, 4, 6.6, 6.6, 8.0)
+        if S_ is None:
+            from gpu_common import gpu_pattern, si_hs
+            pH = gpu_pattern(g, ctx.rH)
+            H, S = si_hs(pos, cell, pH, 4)
+            S_, H_ = cuda(S), cuda(H)
+        L = torch.zeros((g.nnzb(ctx.rL), 4, 4), dtype=torch.float64, device="cuda")
+        ctx.init_L(S_, L)
+        ctx.energy_gradient(L, S_, H_, -2.0, precision=lsq.TF32X3)
+        g.device_status()
+        choices = _step_choices(g, len(g.ranges))
+        assert len(choices) >= 4
+        if forced:
+            assert set(choices.values()) == {0}
+        _explicit_products_match(g, choices, 4 + forced)
+        monkeypatch.delenv("LSQ_TC_CHOICE", raising=False)
