@@ -517,11 +517,14 @@ def run_ours(args):
     STEP_PRODUCTS = [("L.S", 2, 0, 3, 0), ("SL.(Q+Q^T)^T lower", 3, 5, 2, 3), ("SL.Q^T upper", 3, 5, 2, 2),
                      ("P = D.S", 2, 0, 3, 0), ("QD = H'.P", 0, 3, 5, 0), ("F = P.D", 3, 2, 5, 1),
                      ("Z = P^T.QD^T", 3, 5, 2, 1)]
-    choices = {}
+    choices, fixed = {}, []
     for name, ra_, rb_, rc_, tri in STEP_PRODUCTS:
         try:
             info = geom.product_plan_info(ra_, rb_, rc_, tri)
             choices[name] = {-1: "untimed", 0: "fp32 fma", 1: "tensor cores"}[info["auto_choice"]]
+            if info["auto_choice"] >= 0:
+                # the same choice as a fixed setting, for profiler runs of this bench
+                fixed.append("%d:%d:%d:%d=%d" % (ra_, rb_, rc_, (0, 1, 1, 2)[tri], info["auto_choice"]))
         except lsq.LsqError:
             choices[name] = "fp32 fma (no tensor-core plan)"
 
@@ -744,7 +747,8 @@ def run_ours(args):
                                     "elsewhere; float32 storage, float64 traces and CG",
                        "l2": "inputs larger than L2 (LSL alone is 885 MB in float32)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "product_kernels": choices},
+                       "product_kernels": choices,
+                       "product_choice_setting": "LSQ_TC_CHOICE=" + ",".join(sorted(set(fixed)))},
             "fp64": {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64, "steps": args.fp64_steps,
                      "roofline": {"bound": "fp64", "achieved": fp64_step_flops / ms64 / 1e9, "peak": dfma,
                                   "unit": "TFLOP/s", "frac": fp64_step_flops / ms64 / 1e9 / dfma,

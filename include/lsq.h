@@ -202,7 +202,14 @@ int lsq_measure_peak(int precision, double *tflops_host, void *stream);
  * bytes each); the tiles (these four are -1 when no plan is held: the LNV path's timing
  * chose the FMA kernel and dropped it); and, for products the LNV path ran with LSQ_TF32X3,
  * which kernel the timing chose (-1 not timed, 0 FP32 FMA, 1 tensor cores).  Host only.
- * No counterpart in the paper. */
+ * No counterpart in the paper.
+ *
+ * The LNV path's choice is timed on a product's first call with beta = 0 (both kernels run
+ * twice; the call synchronises).  The environment variable LSQ_TC_CHOICE replaces the timing
+ * with a fixed choice, read when a product has none yet: a comma-separated list of
+ * "range_a:range_b:range_c:t=k" (t = 0 whole C, 1 upper triangle, 2 lower triangle; k = 1
+ * tensor cores, 0 FP32 FMA) and "all=k" for the products not listed.  For profiler runs,
+ * whose serialised launches distort the timing. */
 int lsq_product_plan_info(lsq_geom g, int range_a, int range_b, int range_c, int triangle,
                           int64_t *info_host);
 
