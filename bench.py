@@ -117,6 +117,20 @@ def host_cpu():
     except OSError:
         pass
     if model is None:
+        # Arm hosts list an implementer and a part number instead of a model name
+        try:
+            ids = {}
+            for ln in open("/proc/cpuinfo"):
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    ids.setdefault(k.strip().lower(), v.strip().lower())
+            parts = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1",
+                     "0xd49": "Neoverse-N2", "0xd8e": "Neoverse-N3", "0xd84": "Neoverse-V3"}
+            if ids.get("cpu implementer") == "0x41" and ids.get("cpu part") in parts:
+                model = "Arm " + parts[ids["cpu part"]]
+        except OSError:
+            pass
+    if model is None:
         import platform
         model = platform.processor() or platform.machine()
     return os.cpu_count(), model

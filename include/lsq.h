@@ -326,7 +326,15 @@ int lsq_lnv_required_ranges(double R_S, double R_H, double R_L, double *out_host
  * Creates an LNV context (workspace for all products of one CG step) on
  * geometry g, whose ranges must include lsq_lnv_required_ranges(...)
  * (looked up by exact value).  Requires R_S <= R_H.  b: orbitals per atom.
- * Allocates device memory once; no later LNV call allocates.
+ * Allocates the small, fixed part of the workspace.  The product buffers (LS,
+ * LSL, Q, ... on the product ranges: most of the memory) are allocated by the
+ * first call that needs them, at 4 bytes per value while every call so far
+ * has been float32-only, and at 8 bytes once a call may run float64 work
+ * (precision LSQ_F64, refinement steps, the final float64 evaluation, or
+ * lsq_lnv_init_purify).  Such a call then reallocates them once.  Product
+ * plans and per-system state are allocated on first use too.  Once
+ * everything a call needs is allocated, repeating the call allocates
+ * nothing.
  */
 int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double R_L, lsq_lnv *out);
 int lsq_lnv_destroy(lsq_lnv ctx);
@@ -433,6 +441,28 @@ int lsq_lnv_minimise(lsq_lnv ctx, double *L_dev, const double *S_dev, const doub
 int lsq_lnv_minimise_batch(lsq_lnv ctx, double *L_dev, const double *S_dev, const double *H_dev,
                            const double *mu_host, const lsq_lnv_opts *opts, lsq_lnv_report *reps,
                            void *stream);
+
+/*
+ * lsq_lnv_minimise_batch over n_ctx contexts at once (1 <= n_ctx <= 16), each on its own
+ * lsq_geom_concat geometry with its own block size: a batch of uneven systems whose block
+ * sizes differ (4 x 4 and 13 x 13, say) in one call.  Arrays are per context: L_dev[c],
+ * S_dev[c], H_dev[c] on ctx[c]'s geometry as for lsq_lnv_minimise_batch, mu_host[c][n_sys of
+ * ctx[c]], reps[c][n_sys of ctx[c]] (reps or reps[c] may be null).  The first step of each
+ * phase runs context by context (building plans); every later step is one CUDA graph over all
+ * contexts in which each product of the step is a single persistent launch serving that
+ * product of every context: its thread blocks take work items (a chunk of blocks of C of one
+ * context's product) from a queue counter in device memory until the queue is empty, so the
+ * systems of all contexts share the GPU within each product.  The products in those launches
+ * use one fixed schedule per block size instead of the autotuned ones.  precision: LSQ_F64 or
+ * LSQ_F32 (LSQ_ERR_INVALID_ARG otherwise); opts->graph is implied.  The contexts' geometries
+ * must be distinct (LSQ_ERR_INVALID_ARG).  Systems, convergence, refinement, reports and
+ * return codes as for lsq_lnv_minimise_batch.  The first call of a context allocates its
+ * per-system state; each call builds and frees its step graphs.  No counterpart in the paper
+ * (Sec. 2.3.2 defines the minimisation of each system).
+ */
+int lsq_lnv_minimise_batch_group(int n_ctx, lsq_lnv *ctx, double **L_dev, const double **S_dev,
+                                 const double **H_dev, const double **mu_host, const lsq_lnv_opts *opts,
+                                 lsq_lnv_report **reps, void *stream);
 
 /*
  * Lets g_to use the kernel schedules the product autotuner chose in g_from

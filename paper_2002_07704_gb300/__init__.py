@@ -86,6 +86,7 @@ def load():
         "lsq_lnv_energy_gradient": (I, [P, P, P, P, D, D, I, P, P, P, P]),
         "lsq_lnv_minimise": (I, [P, P, P, P, D, P, P, P]),
         "lsq_lnv_minimise_batch": (I, [P, P, P, P, P, P, P, P]),
+        "lsq_lnv_minimise_batch_group": (I, [I, P, P, P, P, P, P, P, P]),
         "lsq_lnv_set_metric": (I, [P, I, P, I, P]),
         "lsq_lnv_init_purify": (I, [P, P, P, D, I, P, I, I, I, P, P, P]),
         "lsq_lnv_minimise_canonical": (I, [P, P, P, P, D, P, P, P, P]),
@@ -113,7 +114,7 @@ def exported_symbols():
             "lsq_trace_static", "lsq_hotelling_inverse",
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
-            "lsq_lnv_minimise_batch", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
+            "lsq_lnv_minimise_batch", "lsq_lnv_minimise_batch_group", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
             "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L",
             "lsq_geom_adopt_schedules", "lsq_device_status", "lsq_measure_peak", "lsq_product_plan_info"]
 
@@ -505,6 +506,37 @@ class Lnv:
             self.close()
         except Exception:
             pass
+
+
+def minimise_batch_group(ctxs, Ls, Ss, Hs, mus, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
+                         precision=F64, refine_iter=2, spin=2.0, stream=None, raise_on_status=False,
+                         final_eval=True):
+    """lsq_lnv_minimise_batch_group: several batched contexts (distinct geometries, any block
+    sizes) minimised in one call, each product of a step one grouped launch over all of them.
+    Ls, Ss, Hs: one tensor per context; mus: per context, one value per system.  Returns one
+    list of reports per context."""
+    import torch
+    n = len(ctxs)
+    if not (len(Ls) == len(Ss) == len(Hs) == len(mus) == n):
+        raise ValueError("one L, S, H and mu list per context")
+    o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
+                int(bool(final_eval)), 0, 1)
+    f = torch.float64
+    handles = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
+    for c, L, S, H in zip(ctxs, Ls, Ss, Hs):
+        c._need_lsh(L=L, S=S, H=H)
+    Lp = (ctypes.c_void_p * n)(*[_dev(L, f) for L in Ls])
+    Sp = (ctypes.c_void_p * n)(*[_dev(S, f) for S in Ss])
+    Hp = (ctypes.c_void_p * n)(*[_dev(H, f) for H in Hs])
+    mu_arrs = [_darr([float(m) for m in mu]) for mu in mus]
+    mup = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in mu_arrs])
+    rep_arrs = [(LnvReport * len(mu))() for mu in mus]
+    repp = (ctypes.c_void_p * n)(*[ctypes.cast(r, ctypes.c_void_p).value for r in rep_arrs])
+    rc = _lib.lsq_lnv_minimise_batch_group(n, handles, Lp, Sp, Hp, mup, ctypes.byref(o), repp,
+                                           _stream(stream))
+    if rc != 0 and (raise_on_status or rc not in (5, 6)):
+        _check(rc)
+    return [[r.as_dict() for r in reps] for reps in rep_arrs]
 
 
 def lnv_create(geom, b, R_S, R_H, R_L):

@@ -28,9 +28,11 @@
 // All matrices are symmetric; the CG keeps L exactly symmetric.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -419,8 +421,11 @@ struct lsq_lnv_s {
     int rS = -1, rH = -1, rL = -1, r1 = -1, r2 = -1, r3 = -1;
     // float64 working set
     DevBuf<double> Hp, Sh, G, Gp, D;
-    // product buffers, sized for float64 and reused for float32
+    // product buffers LS, SL, LSL, Q, QT, QD, G1, G2: sized for ws_es bytes per value (4 while
+    // only float32 work has run, 8 once float64 work has), grown by ensure_ws at the entry
+    // points; the float32 copies Lc, Dc, Hpc, Shc, Sc
     DevBuf<char> LS, SL, LSL, Q, QT, QD, G1, G2, Lc, Dc, Hpc, Shc, Sc;
+    size_t ws_es = 0;
     DevBuf<double> om_rows;  // per-row energy terms formed with the gradient (2 x n)
     // metric of the CG (lsq_lnv_set_metric): X ~ S^-1 on range rX, X G on range rXG
     int rX = -1, rXG = -1;
@@ -435,6 +440,41 @@ struct lsq_lnv_s {
 };
 
 static int64_t nvals(lsq_lnv c, int r) { return c->g->pats[r].nnzb * c->b * c->b; }
+
+// Sizes the product buffers for values of the precision prec (grown, never shrunk; the
+// contents do not survive a call).  Called by the entry points before any work is enqueued,
+// with the widest precision the call may use, so that no buffer is reallocated inside a call.
+static int ensure_ws(lsq_lnv c, int prec) {
+    const size_t es = prec == LSQ_F64 ? 8 : 4;
+    if (c->ws_es >= es) return LSQ_OK;
+    const bool mat = c->b == 4;  // transposed operands materialised (see energy_gradient)
+    const auto sz = [&](int r) { return es * (size_t)c->g->pats[r].nnzb * c->b * c->b; };
+    c->ws_es = 0;
+    LSQ_TRY(c->LS.alloc(sz(c->r1)));
+    LSQ_TRY(c->LSL.alloc(sz(c->r3)));
+    if (mat) {
+        LSQ_TRY(c->SL.alloc(sz(c->r1)));
+        LSQ_TRY(c->QT.alloc(sz(c->r3)));
+    }
+    LSQ_TRY(c->Q.alloc(sz(c->r3)));
+    LSQ_TRY(c->QD.alloc(sz(c->r3)));
+    LSQ_TRY(c->G1.alloc(sz(c->rL)));
+    LSQ_TRY(c->G2.alloc(sz(c->rL)));
+    c->ws_es = es;
+    return LSQ_OK;
+}
+
+// The product buffers hold values of the precision prec (a guard of the internal functions).
+static int need_ws(lsq_lnv c, int prec) {
+    if (c->ws_es < (prec == LSQ_F64 ? 8u : 4u))
+        return set_error(LSQ_ERR_INVALID_ARG, "internal: LNV workspace not sized for this precision");
+    return LSQ_OK;
+}
+
+// Widest precision a minimisation with these options uses.
+static int widest(const lsq_lnv_opts &o) {
+    return (o.precision == LSQ_F64 || o.refine_iter > 0 || o.final_eval) ? LSQ_F64 : LSQ_F32;
+}
 
 // Precision handed to the products: the float32 path runs them as c->mm32.
 static int mmp(lsq_lnv c, int prec) { return prec == LSQ_F32 ? c->mm32 : prec; }
@@ -453,6 +493,9 @@ static int take_precision(lsq_lnv c, int *prec) {
 // Steps between fresh products Q = H'LS in the single-system CG (Q is updated along the line
 // search in between).
 constexpr int kQFresh = 10;
+
+// Contexts of one grouped batch call.
+constexpr int kMaxGroupContexts = 16;
 
 extern "C" int lsq_lnv_default_opts(lsq_lnv_opts *o) {
     clear_error();
@@ -511,15 +554,9 @@ extern "C" int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double 
         return rc;
     };
     int rc;
-    size_t d = sizeof(double);
-    const bool mat = b == 4;  // transposed operands materialised (see energy_gradient)
     if ((rc = c->Hp.alloc(nvals(c, c->rH))) || (rc = c->Sh.alloc(nvals(c, c->rH))) ||
         (rc = c->G.alloc(nvals(c, c->rL))) || (rc = c->Gp.alloc(nvals(c, c->rL))) ||
-        (rc = c->D.alloc(nvals(c, c->rL))) || (rc = c->LS.alloc(d * nvals(c, c->r1))) ||
-        (rc = c->LSL.alloc(d * nvals(c, c->r3))) ||
-        (mat && (rc = c->SL.alloc(d * nvals(c, c->r1)))) || (mat && (rc = c->QT.alloc(d * nvals(c, c->r3)))) ||
-        (rc = c->Q.alloc(d * nvals(c, c->r3))) || (rc = c->QD.alloc(d * nvals(c, c->r3))) ||
-        (rc = c->G1.alloc(d * nvals(c, c->rL))) || (rc = c->G2.alloc(d * nvals(c, c->rL))) ||
+        (rc = c->D.alloc(nvals(c, c->rL))) ||
         (rc = c->Lc.alloc(4 * nvals(c, c->rL))) || (rc = c->Dc.alloc(4 * nvals(c, c->rL))) ||
         (rc = c->Hpc.alloc(4 * nvals(c, c->rH))) || (rc = c->Shc.alloc(4 * nvals(c, c->rH))) ||
         (rc = c->Sc.alloc(4 * nvals(c, c->rS))))
@@ -651,6 +688,7 @@ int seg_trace(lsq_lnv c, int prec, int rx, const void *X, int ry, const void *Y,
 int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *G,
                     double *omega, double *ne, cudaStream_t s, bool seg = false, bool want_ne = false,
                     bool reuse_q = false, bool s_as_h = false) {
+    LSQ_TRY(need_ws(c, prec));
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
@@ -754,6 +792,7 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
 // c1 = <G, D> (float64), c2, c3 from the products listed at the top of the file.
 int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int prec, double *c123,
                 cudaStream_t s, bool seg = false) {
+    LSQ_TRY(need_ws(c, prec));
     lsq_geom g = c->g;
     const int b = c->b;
     Ops o = operands(c, L, S, prec, s);
@@ -830,6 +869,7 @@ extern "C" int lsq_lnv_energy_gradient(lsq_lnv c, const double *L, const double 
     clear_error();
     if (!c || !L || !S || !H) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
     LSQ_TRY(take_precision(c, &prec));
+    LSQ_TRY(ensure_ws(c, prec));
     cudaStream_t s = (cudaStream_t)stream;
     LSQ_TRY(prepare_hs(c, S, H, mu, prec, s));
     double om = 0, n_e = 0;
@@ -985,6 +1025,7 @@ extern "C" int lsq_lnv_init_purify(lsq_lnv c, const double *S, const double *H, 
     LSQ_TRY(geom_check(g, range_x));
     LSQ_TRY(geom_check(g, range_xh));
     LSQ_TRY(take_precision(c, &precision));
+    LSQ_TRY(ensure_ws(c, LSQ_F64));  // X H and X H X are formed in float64 in any precision
     if (n_iter < 0) return set_error(LSQ_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (g->pats[range_xh].R < g->pats[range_x].R + g->pats[c->rH].R - 1e-9)
         return set_error(LSQ_ERR_INVALID_ARG, "range_xh must cover the natural range R_X + R_H of X H");
@@ -1104,6 +1145,7 @@ extern "C" int lsq_lnv_minimise(lsq_lnv c, double *L, const double *S, const dou
     LSQ_TRY(take_precision(c, &o.precision));
     if (o.max_iter < 0 || o.cg_reset < 1 || o.refine_iter < 0)
         return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
+    LSQ_TRY(ensure_ws(c, widest(o)));
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     const int n = c->g->n;
@@ -1233,6 +1275,7 @@ extern "C" int lsq_lnv_minimise_canonical(lsq_lnv c, double *L, const double *S,
     if (opts) o = *opts;
     LSQ_TRY(take_precision(c, &o.precision));
     if (o.max_iter < 0 || o.cg_reset < 1) return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
+    LSQ_TRY(ensure_ws(c, widest(o)));
     if (!(n_electrons > 0.0)) return set_error(LSQ_ERR_INVALID_ARG, "n_electrons must be positive");
     if (c->rX >= 0) return set_error(LSQ_ERR_UNSUPPORTED, "the canonical minimiser has no metric; clear it");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1451,26 +1494,134 @@ int batch_prepare_hs(lsq_lnv c, const double *S, const double *H, int prec, cuda
     return LSQ_OK;
 }
 
-}  // namespace
+// Step graphs of one batch call: kind 0 forms Q = H'LS afresh, kind 1 carries it along the line
+// search (every kQFresh-th step is fresh, as in the single-system minimiser).
+struct StepGraphs {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    std::vector<void *> dev;  // grouped launches' descriptors and queue counters
+    ~StepGraphs() {
+        for (int k = 0; k < 2; ++k) {
+            if (exec[k]) cudaGraphExecDestroy(exec[k]);
+            if (graph[k]) cudaGraphDestroy(graph[k]);
+        }
+        for (void *p : dev) cudaFree(p);
+    }
+};
 
-extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, const double *H,
-                                      const double *mu_host, const lsq_lnv_opts *opts,
-                                      lsq_lnv_report *reps, void *stream) {
-    clear_error();
-    if (c && c->rX >= 0)
-        return set_error(LSQ_ERR_UNSUPPORTED, "the batched minimiser has no metric; clear it with a null X");
-    if (!c || !L || !S || !H || !mu_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+// Adds a segment of a context's step to G after deps (an empty node for an empty segment).
+int add_segment(cudaGraph_t G, const std::vector<cudaGraphNode_t> &deps, cudaGraph_t seg, cudaGraphNode_t *out) {
+    size_t nn = 0;
+    LSQ_CUDA_TRY(cudaGraphGetNodes(seg, nullptr, &nn));
+    if (nn == 0)
+        LSQ_CUDA_TRY(cudaGraphAddEmptyNode(out, G, deps.data(), deps.size()));
+    else
+        LSQ_CUDA_TRY(cudaGraphAddChildGraphNode(out, G, deps.data(), deps.size(), seg));
+    return LSQ_OK;
+}
+
+// One CG step of every context as a single graph.  Each context's step is captured with its
+// products split out (GroupRecorder): segment k of every context runs, then the k-th products of
+// all contexts run as one grouped persistent launch (group_launch), then segment k + 1 of
+// every context.  Contexts whose step has fewer products simply have fewer segments.
+int capture_group_step(int nctx, lsq_lnv *cs, double **L, const double **S, double spin, int prec, double tol,
+                       int cg_reset, cudaStream_t s, bool reuse_q, StepGraphs &sg, int kind) {
+    std::vector<std::unique_ptr<GroupRecorder>> recs(nctx);
+    for (int c = 0; c < nctx; ++c) {
+        recs[c].reset(new GroupRecorder());
+        LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        g_group_rec = recs[c].get();
+        const int rc = batch_step(cs[c], L[c], S[c], spin, prec, tol, cg_reset, s, reuse_q);
+        g_group_rec = nullptr;
+        cudaGraph_t last = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &last);
+        if (last) recs[c]->segments.push_back(last);
+        if (rc != LSQ_OK) return rc;
+        if (ec != cudaSuccess) return set_error(LSQ_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(ec));
+    }
+    size_t nprod = 0;
+    for (int c = 0; c < nctx; ++c) nprod = std::max(nprod, recs[c]->products.size());
+    unsigned long long *counters = nullptr;
+    LSQ_CUDA_TRY(cudaMalloc(&counters, sizeof(unsigned long long) * std::max<size_t>(nprod, 1)));
+    sg.dev.push_back(counters);
+    cudaGraph_t G = nullptr;
+    LSQ_CUDA_TRY(cudaGraphCreate(&G, 0));
+    sg.graph[kind] = G;
+    cudaStream_t side = nullptr;
+    LSQ_CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    struct SideStream {
+        cudaStream_t s;
+        ~SideStream() { cudaStreamDestroy(s); }
+    } side_guard{side};
+    std::vector<cudaGraphNode_t> prev;
+    for (size_t k = 0; k <= nprod; ++k) {
+        std::vector<cudaGraphNode_t> deps;
+        for (int c = 0; c < nctx; ++c) {
+            if (k >= recs[c]->segments.size()) continue;
+            cudaGraphNode_t node;
+            LSQ_TRY(add_segment(G, prev, recs[c]->segments[k], &node));
+            deps.push_back(node);
+        }
+        if (k == nprod) break;
+        std::vector<GroupProduct> prods;
+        for (int c = 0; c < nctx; ++c)
+            if (k < recs[c]->products.size()) prods.push_back(recs[c]->products[k]);
+        GroupLaunch gl;
+        LSQ_TRY(group_prepare(prods.data(), (int)prods.size(), cs[0]->g, &gl));
+        sg.dev.push_back(gl.desc);
+        // the launch (queue reset and kernel) as a small graph of its own
+        LSQ_CUDA_TRY(cudaStreamBeginCapture(side, cudaStreamCaptureModeThreadLocal));
+        const int rc = group_launch(gl, counters + k, side);
+        cudaGraph_t pg = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(side, &pg);
+        if (rc != LSQ_OK) {
+            if (pg) cudaGraphDestroy(pg);
+            return rc;
+        }
+        if (ec != cudaSuccess) return set_error(LSQ_ERR_CUDA, std::string("product capture: ") + cudaGetErrorString(ec));
+        cudaGraphNode_t node;
+        const cudaError_t ea = cudaGraphAddChildGraphNode(&node, G, deps.data(), deps.size(), pg);
+        cudaGraphDestroy(pg);
+        if (ea != cudaSuccess) return set_error(LSQ_ERR_CUDA, std::string("product node: ") + cudaGetErrorString(ea));
+        prev.assign(1, node);
+    }
+    LSQ_CUDA_TRY(cudaGraphInstantiate(&sg.exec[kind], G, 0));
+    return LSQ_OK;
+}
+
+// The batched minimiser over nctx contexts (each on its own block-diagonal geometry, with its own
+// block size).  grouped: the steps after the first run as graphs whose products are grouped
+// launches over all contexts (capture_group_step); otherwise (one context) each step is captured
+// as it runs, with the tuned product kernels.
+int minimise_batch_impl(int nctx, lsq_lnv *cs, double **L, const double **S, const double **H,
+                        const double **mu_host, const lsq_lnv_opts *opts, lsq_lnv_report **reps, cudaStream_t us,
+                        bool grouped) {
+    if (nctx < 1 || !cs || !L || !S || !H || !mu_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    for (int c = 0; c < nctx; ++c) {
+        if (!cs[c] || !L[c] || !S[c] || !H[c] || !mu_host[c]) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+        if (cs[c]->rX >= 0)
+            return set_error(LSQ_ERR_UNSUPPORTED, "the batched minimiser has no metric; clear it with a null X");
+        for (int d = 0; d < c; ++d)
+            if (cs[d]->g == cs[c]->g)
+                return set_error(LSQ_ERR_INVALID_ARG, "the contexts of a grouped batch need distinct geometries");
+    }
     lsq_lnv_opts o;
     lsq_lnv_default_opts(&o);
     if (opts) o = *opts;
-    LSQ_TRY(take_precision(c, &o.precision));
+    if (grouped && o.precision != LSQ_F64 && o.precision != LSQ_F32)
+        return set_error(LSQ_ERR_INVALID_ARG, "a grouped batch runs LSQ_F64 or LSQ_F32 products");
+    for (int c = 0; c < nctx; ++c) {
+        int pr = o.precision;
+        LSQ_TRY(take_precision(cs[c], &pr));
+        if (c == nctx - 1) o.precision = pr;
+    }
     if (o.max_iter < 0 || o.cg_reset < 1 || o.refine_iter < 0)
         return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
-    cudaStream_t us = (cudaStream_t)stream;
-    lsq_geom g = c->g;
-    const int ns = g->n_sys;
     auto t0 = std::chrono::steady_clock::now();
-    LSQ_TRY(batch_alloc(c));
+    for (int c = 0; c < nctx; ++c) {
+        LSQ_TRY(ensure_ws(cs[c], widest(o)));
+        LSQ_TRY(batch_alloc(cs[c]));
+    }
     // Work runs on a private stream ordered after the caller's (a graph cannot be captured
     // from the legacy default stream); the caller's stream waits for it at the end.
     cudaStream_t s = nullptr;
@@ -1482,6 +1633,7 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
         cudaStream_t us, s;
         cudaEvent_t a, b;
         ~Cleanup() {
+            g_group_rec = nullptr;
             if (b && s) {
                 cudaEventRecord(b, s);
                 cudaStreamWaitEvent(us, b, 0);
@@ -1494,118 +1646,159 @@ extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, con
     } cleanup{us, s, ev_in, ev_out};
     LSQ_CUDA_TRY(cudaEventRecord(ev_in, us));
     LSQ_CUDA_TRY(cudaStreamWaitEvent(s, ev_in, 0));
-    const int64_t nl = nvals(c, c->rL);
-    LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_mu.p, mu_host, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
-    LSQ_TRY(batch_prepare_hs(c, S, H, LSQ_F64, s));
-    if (o.precision == LSQ_F32) LSQ_TRY(batch_prepare_hs(c, S, H, LSQ_F32, s));
-    LSQ_CUDA_TRY(cudaMemsetAsync(c->Gp.p, 0, sizeof(double) * nl, s));
-    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_frozen.p, 0, sizeof(int) * ns, s));
-    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_iters.p, 0, sizeof(int) * ns, s));
-    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_gg_prev.p, 0, sizeof(double) * ns, s));
-    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_dom.p, 0, sizeof(double) * ns, s));
-    {
+    std::vector<int> nsys(nctx);
+    for (int c = 0; c < nctx; ++c) {
+        lsq_lnv x = cs[c];
+        const int ns = x->g->n_sys;
+        nsys[c] = ns;
+        const int64_t nl = nvals(x, x->rL);
+        LSQ_CUDA_TRY(cudaMemcpyAsync(x->b_mu.p, mu_host[c], sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_TRY(batch_prepare_hs(x, S[c], H[c], LSQ_F64, s));
+        if (o.precision == LSQ_F32) LSQ_TRY(batch_prepare_hs(x, S[c], H[c], LSQ_F32, s));
+        LSQ_CUDA_TRY(cudaMemsetAsync(x->Gp.p, 0, sizeof(double) * nl, s));
+        LSQ_CUDA_TRY(cudaMemsetAsync(x->b_frozen.p, 0, sizeof(int) * ns, s));
+        LSQ_CUDA_TRY(cudaMemsetAsync(x->b_iters.p, 0, sizeof(int) * ns, s));
+        LSQ_CUDA_TRY(cudaMemsetAsync(x->b_gg_prev.p, 0, sizeof(double) * ns, s));
+        LSQ_CUDA_TRY(cudaMemsetAsync(x->b_dom.p, 0, sizeof(double) * ns, s));
         std::vector<int> one(ns, 1), st(ns, o.tol_ha_per_atom > 0.0 ? LSQ_ERR_NOT_CONVERGED : LSQ_OK);
-        LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
-        LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_status.p, st.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(x->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(x->b_status.p, st.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    std::vector<int> iters64(ns, 0), frozen(ns, 0), status(ns, 0), it_before(ns, 0);
+    std::vector<std::vector<int>> iters64(nctx), frozen(nctx), status(nctx), it_before(nctx);
+    for (int c = 0; c < nctx; ++c) {
+        iters64[c].assign(nsys[c], 0);
+        frozen[c].assign(nsys[c], 0);
+        status[c].assign(nsys[c], 0);
+        it_before[c].assign(nsys[c], 0);
+    }
     const int nphase = o.precision == LSQ_F32 ? 2 : 1;
     const int check_every = 5;
     for (int phase = 0; phase < nphase; ++phase) {
         const int prec = phase == 0 ? o.precision : LSQ_F64;
         const int budget = phase == 0 ? o.max_iter : o.refine_iter;
-        if (phase == 1) {
-            // refinement: float64 steps from a fresh direction for every system that did not fail
-            LSQ_CUDA_TRY(cudaMemcpy(status.data(), c->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
-            LSQ_CUDA_TRY(cudaMemcpy(it_before.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
-            for (int k = 0; k < ns; ++k) frozen[k] = status[k] == LSQ_ERR_UNSTABLE ? 1 : 0;
-            std::vector<int> one(ns, 1);
-            LSQ_CUDA_TRY(cudaMemcpy(c->b_frozen.p, frozen.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
-            LSQ_CUDA_TRY(cudaMemcpy(c->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+        for (int c = 0; c < nctx; ++c) {
+            lsq_lnv x = cs[c];
+            const int ns = nsys[c];
+            if (phase == 1) {
+                // refinement: float64 steps from a fresh direction for every system that did not fail
+                LSQ_CUDA_TRY(cudaMemcpy(status[c].data(), x->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+                LSQ_CUDA_TRY(cudaMemcpy(it_before[c].data(), x->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+                for (int k = 0; k < ns; ++k) frozen[c][k] = status[c][k] == LSQ_ERR_UNSTABLE ? 1 : 0;
+                std::vector<int> one(ns, 1);
+                LSQ_CUDA_TRY(cudaMemcpy(x->b_frozen.p, frozen[c].data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+                LSQ_CUDA_TRY(cudaMemcpy(x->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+            }
+            LSQ_CUDA_TRY(cudaMemsetAsync(x->b_step.p, 0, sizeof(int), s));
         }
-        LSQ_CUDA_TRY(cudaMemsetAsync(c->b_step.p, 0, sizeof(int), s));
         // tol = 0 freezes nothing; the refinement uses tol = 0 (fixed number of steps)
         const double tol = phase == 0 ? o.tol_ha_per_atom : 0.0;
-        // Two step graphs: one that forms Q = H'LS afresh, one that carries it along the line
-        // search (every kQFresh-th step is fresh, as in the single-system minimiser).
-        struct StepGraphs {
-            cudaGraphExec_t exec[2] = {nullptr, nullptr};
-            cudaGraph_t graph[2] = {nullptr, nullptr};
-            ~StepGraphs() {
-                for (int k = 0; k < 2; ++k) {
-                    if (exec[k]) cudaGraphExecDestroy(exec[k]);
-                    if (graph[k]) cudaGraphDestroy(graph[k]);
-                }
-            }
-        } sg;
+        StepGraphs sg;
         for (int it = 0; it < budget; ++it) {
             const int kind = it % std::min(o.cg_reset, kQFresh) != 0 ? 1 : 0;
-            if (it >= 1 && o.graph && !sg.exec[kind]) {
+            if (it >= 1 && (o.graph || grouped) && !sg.exec[kind]) {
                 // plans, maps and autotuning exist after the first step: capture this kind of step
-                LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-                int rc = batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s, kind == 1);
-                cudaError_t ec = cudaStreamEndCapture(s, &sg.graph[kind]);
-                if (rc != LSQ_OK) return rc;
-                if (ec != cudaSuccess) return set_error(LSQ_ERR_CUDA, cudaGetErrorString(ec));
-                LSQ_CUDA_TRY(cudaGraphInstantiate(&sg.exec[kind], sg.graph[kind], 0));
+                if (grouped) {
+                    LSQ_TRY(capture_group_step(nctx, cs, L, S, o.spin, prec, tol, o.cg_reset, s, kind == 1, sg,
+                                               kind));
+                } else {
+                    LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                    int rc = batch_step(cs[0], L[0], S[0], o.spin, prec, tol, o.cg_reset, s, kind == 1);
+                    cudaError_t ec = cudaStreamEndCapture(s, &sg.graph[kind]);
+                    if (rc != LSQ_OK) return rc;
+                    if (ec != cudaSuccess) return set_error(LSQ_ERR_CUDA, cudaGetErrorString(ec));
+                    LSQ_CUDA_TRY(cudaGraphInstantiate(&sg.exec[kind], sg.graph[kind], 0));
+                }
             }
             if (sg.exec[kind]) {
                 LSQ_CUDA_TRY(cudaGraphLaunch(sg.exec[kind], s));
             } else {
-                LSQ_TRY(batch_step(c, L, S, o.spin, prec, tol, o.cg_reset, s, kind == 1));
+                for (int c = 0; c < nctx; ++c)
+                    LSQ_TRY(batch_step(cs[c], L[c], S[c], o.spin, prec, tol, o.cg_reset, s, kind == 1));
             }
             if (tol > 0.0 && (it + 1) % check_every == 0) {
-                LSQ_CUDA_TRY(cudaMemcpyAsync(frozen.data(), c->b_frozen.p, sizeof(int) * ns,
-                                             cudaMemcpyDeviceToHost, s));
-                LSQ_CUDA_TRY(cudaStreamSynchronize(s));
                 bool all = true;
-                for (int k = 0; k < ns; ++k) all = all && frozen[k];
+                for (int c = 0; c < nctx; ++c) {
+                    LSQ_CUDA_TRY(cudaMemcpyAsync(frozen[c].data(), cs[c]->b_frozen.p, sizeof(int) * nsys[c],
+                                                 cudaMemcpyDeviceToHost, s));
+                    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+                    for (int k = 0; k < nsys[c]; ++k) all = all && frozen[c][k];
+                }
                 if (all) break;
             }
         }
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));
-        if (phase == 1) {
-            std::vector<int> it_after(ns);
-            LSQ_CUDA_TRY(cudaMemcpy(it_after.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
-            for (int k = 0; k < ns; ++k) iters64[k] = it_after[k] - it_before[k];
-        } else if (prec == LSQ_F64) {
-            LSQ_CUDA_TRY(cudaMemcpy(iters64.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+        for (int c = 0; c < nctx; ++c) {
+            const int ns = nsys[c];
+            if (phase == 1) {
+                std::vector<int> it_after(ns);
+                LSQ_CUDA_TRY(cudaMemcpy(it_after.data(), cs[c]->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+                for (int k = 0; k < ns; ++k) iters64[c][k] = it_after[k] - it_before[c][k];
+            } else if (prec == LSQ_F64) {
+                LSQ_CUDA_TRY(cudaMemcpy(iters64[c].data(), cs[c]->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+            }
         }
     }
     // final float64 Omega and N_e of every system (without it the report keeps the Omega of the
     // last step's energy evaluation, in the working precision, and no N_e)
-    if (o.final_eval) LSQ_TRY(energy_gradient(c, L, S, o.spin, LSQ_F64, nullptr, nullptr, nullptr, s, true, true));
-    std::vector<double> slots((size_t)ns * kSlots), dom(ns);
-    std::vector<int> iters(ns);
-    LSQ_CUDA_TRY(cudaMemcpyAsync(slots.data(), c->b_slots.p, sizeof(double) * ns * kSlots, cudaMemcpyDeviceToHost, s));
-    LSQ_CUDA_TRY(cudaMemcpyAsync(dom.data(), c->b_dom.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
-    LSQ_CUDA_TRY(cudaMemcpyAsync(iters.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
-    LSQ_CUDA_TRY(cudaMemcpyAsync(status.data(), c->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
-    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (o.final_eval)
+        for (int c = 0; c < nctx; ++c)
+            LSQ_TRY(energy_gradient(cs[c], L[c], S[c], o.spin, LSQ_F64, nullptr, nullptr, nullptr, s, true, true));
     const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int worst = LSQ_OK;
-    for (int k = 0; k < ns; ++k) {
-        const double *sl = slots.data() + (size_t)k * kSlots;
-        const int na = (int)(g->sys_atom_off[k + 1] - g->sys_atom_off[k]);
-        int st = status[k];
-        if (nphase == 2 && st != LSQ_ERR_UNSTABLE && o.tol_ha_per_atom > 0.0 && iters64[k] > 0 &&
-            dom[k] < o.tol_ha_per_atom)
-            st = LSQ_OK;
-        if (reps) {
-            reps[k].iterations = iters[k];
-            reps[k].iterations_fp64 = iters64[k];
-            reps[k].status = st;
-            reps[k].omega_ev = o.spin * (3.0 * sl[0] - 2.0 * sl[1]);
-            reps[k].ne = o.final_eval ? o.spin * (3.0 * sl[2] - 2.0 * sl[3]) : std::nan("");
-            reps[k].omega_ha_per_atom = reps[k].omega_ev / kHartreeEv / std::max(na, 1);
-            reps[k].last_domega_ha_per_atom = dom[k];
-            reps[k].seconds = sec;
+    for (int c = 0; c < nctx; ++c) {
+        lsq_lnv x = cs[c];
+        lsq_geom g = x->g;
+        const int ns = nsys[c];
+        std::vector<double> slots((size_t)ns * kSlots), dom(ns);
+        std::vector<int> iters(ns);
+        LSQ_CUDA_TRY(cudaMemcpyAsync(slots.data(), x->b_slots.p, sizeof(double) * ns * kSlots, cudaMemcpyDeviceToHost, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(dom.data(), x->b_dom.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(iters.data(), x->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(status[c].data(), x->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+        LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int k = 0; k < ns; ++k) {
+            const double *sl = slots.data() + (size_t)k * kSlots;
+            const int na = (int)(g->sys_atom_off[k + 1] - g->sys_atom_off[k]);
+            int st = status[c][k];
+            if (nphase == 2 && st != LSQ_ERR_UNSTABLE && o.tol_ha_per_atom > 0.0 && iters64[c][k] > 0 &&
+                dom[k] < o.tol_ha_per_atom)
+                st = LSQ_OK;
+            if (reps && reps[c]) {
+                lsq_lnv_report &r = reps[c][k];
+                r.iterations = iters[k];
+                r.iterations_fp64 = iters64[c][k];
+                r.status = st;
+                r.omega_ev = o.spin * (3.0 * sl[0] - 2.0 * sl[1]);
+                r.ne = o.final_eval ? o.spin * (3.0 * sl[2] - 2.0 * sl[3]) : std::nan("");
+                r.omega_ha_per_atom = r.omega_ev / kHartreeEv / std::max(na, 1);
+                r.last_domega_ha_per_atom = dom[k];
+                r.seconds = sec;
+            }
+            if (st == LSQ_ERR_UNSTABLE) worst = LSQ_ERR_UNSTABLE;
+            else if (st == LSQ_ERR_NOT_CONVERGED && worst == LSQ_OK) worst = LSQ_ERR_NOT_CONVERGED;
         }
-        if (st == LSQ_ERR_UNSTABLE) worst = LSQ_ERR_UNSTABLE;
-        else if (st == LSQ_ERR_NOT_CONVERGED && worst == LSQ_OK) worst = LSQ_ERR_NOT_CONVERGED;
     }
     if (worst == LSQ_ERR_UNSTABLE) return set_error(worst, "a system has no local minimum along its CG direction");
     if (worst == LSQ_ERR_NOT_CONVERGED) return set_error(worst, "iteration limit reached for a system");
     return LSQ_OK;
+}
+
+}  // namespace
+
+extern "C" int lsq_lnv_minimise_batch(lsq_lnv c, double *L, const double *S, const double *H,
+                                      const double *mu_host, const lsq_lnv_opts *opts,
+                                      lsq_lnv_report *reps, void *stream) {
+    clear_error();
+    if (!c || !L || !S || !H || !mu_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    return minimise_batch_impl(1, &c, &L, &S, &H, &mu_host, opts, &reps, (cudaStream_t)stream, false);
+}
+
+extern "C" int lsq_lnv_minimise_batch_group(int n_ctx, lsq_lnv *ctx, double **L_dev, const double **S_dev,
+                                            const double **H_dev, const double **mu_host,
+                                            const lsq_lnv_opts *opts, lsq_lnv_report **reps, void *stream) {
+    clear_error();
+    if (n_ctx < 1 || n_ctx > kMaxGroupContexts)
+        return set_error(LSQ_ERR_INVALID_ARG, "n_ctx must be in [1, " + std::to_string(kMaxGroupContexts) + "]");
+    return minimise_batch_impl(n_ctx, ctx, L_dev, S_dev, H_dev, mu_host, opts, reps, (cudaStream_t)stream, true);
 }

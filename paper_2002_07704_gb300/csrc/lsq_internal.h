@@ -226,6 +226,49 @@ int fetch_scalars(lsq_geom g, int nslots, double *out, cudaStream_t s);
 
 inline size_t dtype_size(int dtype) { return dtype == LSQ_F64 ? 8 : 4; }
 
+// ---- grouped products (the batched minimiser over several contexts) ----------
+// One product as the plan kernels would have been launched with it.  For b = 4 the operands
+// are op(A) and X = op(B)^T with rows contiguous (transposed into scratch beforehand); for
+// other b, A and B as given, read through the transpose maps when ta / tb.
+struct GroupProduct {
+    int b = 0, dtype = 0, ta = 0, tb = 0, upper = 0, n = 0;
+    int64_t nblocks = 0;
+    const int64_t *c_ptr = nullptr, *perm = nullptr, *item_ptr = nullptr, *a_ptr = nullptr,
+                  *x_ptr = nullptr, *c_row = nullptr, *a_tm = nullptr, *b_tm = nullptr;
+    const uint32_t *items = nullptr;
+    const int32_t *c_col = nullptr;
+    const void *A = nullptr, *X = nullptr;
+    void *C = nullptr;
+    double alpha = 1.0, beta = 0.0;
+};
+
+// While a step is captured for a grouped launch, g_group_rec is set (per host thread): the plan
+// launches then record their product and split the capture (the work before the product is
+// one graph segment, the work after it starts the next) instead of launching a kernel.
+// segments[k] precedes products[k]; the last segment follows the last product.
+struct GroupRecorder {
+    std::vector<cudaGraph_t> segments;
+    std::vector<GroupProduct> products;
+    int split(cudaStream_t s);
+    ~GroupRecorder();
+};
+extern thread_local GroupRecorder *g_group_rec;
+
+// Device descriptors of a grouped launch (uploaded once; see group_launch).
+struct GroupLaunch {
+    void *desc = nullptr;  // device copy of the products' descriptors
+    int nprod = 0, dtype = 0;
+    int64_t nchunks = 0;   // work items of the launch's queue
+    int grid = 0;
+};
+// Uploads the descriptors of products (all of one dtype) into out->desc (device memory owned by
+// the caller: free with cudaFree).  Synchronous; call it outside stream capture.
+int group_prepare(const GroupProduct *products, int n, const lsq_geom g_any, GroupLaunch *out);
+// The grouped product: one persistent launch whose thread blocks take work items (a chunk of
+// blocks of C of one product) from a queue in device memory until it is empty.  counter is
+// reset on s before the launch.
+int group_launch(const GroupLaunch &gl, unsigned long long *counter, cudaStream_t s);
+
 // Internal product precision (not part of the ABI): float32 storage, and per product the
 // faster of the FP32 FMA schedules and the LSQ_TF32X3 tensor-core kernel, timed on the
 // product's first call (with beta = 0).  The LNV path uses it when asked for LSQ_TF32X3.

@@ -293,6 +293,27 @@ __device__ __forceinline__ void plan_store(const PlanArgs &g, T *__restrict__ C,
     *dst = g.beta != 0.0 ? fma((T)g.beta, *dst, v) : v;
 }
 
+// Blocks t0, t0 + step, ... (< t1) of C in the plan's order, one per team of 16 lanes (lane
+// (r, c) = threadIdx.x % 16 accumulates C_ij[r][c]).
+template <typename T, int UNROLL>
+__device__ __forceinline__ void b4_blocks(const PlanArgs &g, int64_t t0, int64_t t1, int64_t step) {
+    const T *__restrict__ A = static_cast<const T *>(g.A);
+    const T *__restrict__ X = static_cast<const T *>(g.X);
+    T *__restrict__ C = static_cast<T *>(g.C);
+    const int sub = threadIdx.x & 15;
+    const int r = sub >> 2, c = sub & 3;
+    for (int64_t t = t0; t < t1; t += step) {
+        const int64_t s = g.perm[t];
+        const int i = (int)g.c_row[s];
+        if (tri_skip(g.upper, i, g.c_col[s])) continue;
+        const T *__restrict__ arow = A + 16 * g.a_ptr[i] + 4 * r;
+        const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
+        const int64_t i0 = g.item_ptr[s];
+        const T v = plan_items<T, UNROLL>(g.items + i0, (int)(g.item_ptr[s + 1] - i0), arow, xrow);
+        plan_store(g, C, s, sub, v);
+    }
+}
+
 // Two schedules of the same work (the plan's autotuner picks one per product):
 //  ROWS = false: teams take blocks of C in the plan's order across the whole grid;
 //  ROWS = true:  a thread block works on one row i of C at a time, so the row i of A it
@@ -322,16 +343,7 @@ __global__ void __launch_bounds__(ROWS ? 1024 : 256) k_mm_plan_b4(PlanArgs g) {
     } else {
         const int64_t team0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
         const int64_t nteams = ((int64_t)gridDim.x * blockDim.x) >> 4;
-        for (int64_t t = team0; t < g.nblocks; t += nteams) {
-            const int64_t s = g.perm[t];
-            const int i = (int)g.c_row[s];
-            if (tri_skip(g.upper, i, g.c_col[s])) continue;
-            const T *__restrict__ arow = A + 16 * g.a_ptr[i] + 4 * r;
-            const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c;
-            const int64_t i0 = g.item_ptr[s];
-            const T v = plan_items<T, UNROLL>(g.items + i0, (int)(g.item_ptr[s + 1] - i0), arow, xrow);
-            plan_store(g, C, s, sub, v);
-        }
+        b4_blocks<T, UNROLL>(g, team0, g.nblocks, nteams);
     }
 }
 
@@ -587,13 +599,14 @@ struct PlanArgsGen {
     const int64_t *b_tm;  // transpose map of B's pattern (!TB)
 };
 
+// Blocks t0, t0 + step, ... (< t1) of C in the plan's order, one per warp; As and Xs are the
+// warp's two b x b staging areas in shared memory.
 template <typename T, bool TA, bool TB>
-__global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
+__device__ __forceinline__ void gen_blocks(const PlanArgsGen &ga, int64_t t0, int64_t t1, int64_t step, T *As,
+                                           T *Xs) {
     const PlanArgs &g = ga.p;
     const int b = ga.b, bb = b * b;
-    __shared__ T stage[8][2][256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T *As = stage[w][0], *Xs = stage[w][1];
+    const int lane = threadIdx.x & 31;
     const T *__restrict__ A = static_cast<const T *>(g.A);
     const T *__restrict__ X = static_cast<const T *>(g.X);
     T *__restrict__ C = static_cast<T *>(g.C);
@@ -602,9 +615,7 @@ __global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
     const int r = lane % b, part = lane / b;
     const bool active = part < nparts;
     const int cbeg = min(b, part * cw), cend = min(b, cbeg + cw);
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = w0; t < g.nblocks; t += nw) {
+    for (int64_t t = t0; t < t1; t += step) {
         const int64_t s = g.perm[t];
         const int i = (int)g.c_row[s];
         if (tri_skip(g.upper, i, g.c_col[s])) continue;
@@ -647,6 +658,15 @@ __global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
     }
 }
 
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_mm_plan_gen(PlanArgsGen ga) {
+    __shared__ T stage[8][2][256];
+    const int w = threadIdx.x >> 5;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    gen_blocks<T, TA, TB>(ga, w0, ga.p.nblocks, nw, stage[w][0], stage[w][1]);
+}
+
 // Lower blocks of a symmetric 4 x 4 result: C_ij = (C_ji)^T for j < i (tm: transpose map of C's
 // pattern).  In a sorted symmetric pattern block (i, j) precedes (j, i) exactly when i < j, so
 // the lower blocks are those with p > tm[p].
@@ -668,15 +688,18 @@ __global__ void k_mirror_lower(int64_t nnzb, const int64_t *__restrict__ tm, T *
 // 4(l / 8) and columns 2(l % 8): per t one 4-vector of At and one 2-vector of Xt feed 8 FMAs.
 // The next item's blocks are fetched into registers while the current one is multiplied.
 // Frame entries beyond b are never initialised; they only reach accumulators that are not stored.
+constexpr int kT16Stride = 20;  // frame row stride: 16-byte rows for float and double
+
+// Blocks t0, t0 + step, ... (< t1) of C in the plan's order, one per warp; At and Xt are the
+// warp's two 16 x kT16Stride frames in shared memory (16-byte aligned).
 template <typename T, bool TA, bool TB>
-__global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
+__device__ __forceinline__ void t16_blocks(const PlanArgsGen &ga, int64_t t0, int64_t t1, int64_t step, T *At,
+                                           T *Xt) {
     const PlanArgs &g = ga.p;
     const int b = ga.b, bb = b * b;
-    constexpr int ST = 20;  // frame row stride: 16-byte rows for float and double
+    constexpr int ST = kT16Stride;
     constexpr int PF = 8;   // values of a block per lane (256 / 32)
-    __shared__ __align__(16) T stage[8][2][16 * ST];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T *At = stage[w][0], *Xt = stage[w][1];
+    const int lane = threadIdx.x & 31;
     const int r0 = 4 * (lane >> 3), c0 = 2 * (lane & 7);
     const T *__restrict__ A = static_cast<const T *>(g.A);
     const T *__restrict__ X = static_cast<const T *>(g.X);
@@ -690,9 +713,7 @@ __global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
         offA[k] = TA ? u * ST + v : v * ST + u;
         offX[k] = TB ? v * ST + u : u * ST + v;
     }
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = w0; t < g.nblocks; t += nw) {
+    for (int64_t t = t0; t < t1; t += step) {
         const int64_t s = g.perm[t];
         const int i = (int)g.c_row[s];
         if (tri_skip(g.upper, i, g.c_col[s])) continue;
@@ -759,6 +780,15 @@ __global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
                     dst[e] = g.beta != 0.0 ? fma((T)g.beta, dst[e], v) : v;
                 }
     }
+}
+
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_mm_plan_t16(PlanArgsGen ga) {
+    __shared__ __align__(16) T stage[8][2][16 * kT16Stride];
+    const int w = threadIdx.x >> 5;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    t16_blocks<T, TA, TB>(ga, w0, ga.p.nblocks, nw, stage[w][0], stage[w][1]);
 }
 
 // Lower blocks of a symmetric result, any block size: one warp per block (lower blocks are
@@ -985,6 +1015,39 @@ int run_variant(lsq_geom g, const Variant &v, const PlanArgs &a, int64_t nblocks
 }
 }  // namespace
 
+namespace {
+int plan_launch_tuned(lsq_geom g, int dtype, ProductPlan &p, int ra, int rb, int rc, const PlanArgs &a,
+                      cudaStream_t s);
+
+GroupProduct group_product(const PlanArgs &a, int b, int dtype, int ta, int tb, const int64_t *a_tm,
+                           const int64_t *b_tm) {
+    GroupProduct q;
+    q.b = b;
+    q.dtype = dtype;
+    q.ta = ta;
+    q.tb = tb;
+    q.upper = a.upper;
+    q.n = a.n;
+    q.nblocks = a.nblocks;
+    q.c_ptr = a.c_ptr;
+    q.perm = a.perm;
+    q.item_ptr = a.item_ptr;
+    q.a_ptr = a.a_ptr;
+    q.x_ptr = a.x_ptr;
+    q.c_row = a.c_row;
+    q.a_tm = a_tm;
+    q.b_tm = b_tm;
+    q.items = a.items;
+    q.c_col = a.c_col;
+    q.A = a.A;
+    q.X = a.X;
+    q.C = a.C;
+    q.alpha = a.alpha;
+    q.beta = a.beta;
+    return q;
+}
+}  // namespace
+
 int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, int rc, const void *Aop,
                 const void *X, void *C, double alpha, double beta, cudaStream_t s, bool mirror) {
     ProductPlan &p = const_cast<ProductPlan &>(pc);
@@ -1006,6 +1069,34 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
     a.C = C;
     a.alpha = alpha;
     a.beta = beta;
+    if (g_group_rec) {
+        // a step captured for a grouped launch: record the product, split the capture
+        g_group_rec->products.push_back(group_product(a, 4, dtype, 0, 0, nullptr, nullptr));
+        LSQ_TRY(g_group_rec->split(s));
+    } else {
+        LSQ_TRY(plan_launch_tuned(g, dtype, p, ra, rb, rc, a, s));
+    }
+    if (p.upper == 1 && mirror) {
+        LSQ_TRY(ensure_tmap(g, rc, s));
+        const int64_t m = g->pats[rc].nnzb * 16;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16));
+        note_launch();
+        if (dtype == LSQ_F64)
+            k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (double *)C);
+        else
+            k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (float *)C);
+        LSQ_CHECK_LAUNCH();
+    }
+    return LSQ_OK;
+}
+
+namespace {
+// The product of plan_launch with the schedule tuned for it (timing every schedule on the
+// first call).
+int plan_launch_tuned(lsq_geom g, int dtype, ProductPlan &p, int ra, int rb, int rc, const PlanArgs &a,
+                      cudaStream_t s) {
+    const void *Aop = a.A, *X = a.X;
+    const double beta = a.beta;
     int nv = 0;
     const Variant *v = dtype == LSQ_F64 ? variants<double>(&nv) : variants<float>(&nv);
     const int di = dtype == LSQ_F64 ? 0 : 1;
@@ -1063,20 +1154,9 @@ int plan_launch(lsq_geom g, int dtype, const ProductPlan &pc, int ra, int rb, in
     }
     // a later call may pass operands that the tuned variant cannot read
     const int use = smem_for(choice) >= 0 ? choice : std::max(p.variant16[di], 0);
-    LSQ_TRY(run_variant(g, v[use], a, p.nblocks, s, smem_for(use)));
-    if (p.upper == 1 && mirror) {
-        LSQ_TRY(ensure_tmap(g, rc, s));
-        const int64_t m = g->pats[rc].nnzb * 16;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16));
-        note_launch();
-        if (dtype == LSQ_F64)
-            k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (double *)C);
-        else
-            k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (float *)C);
-        LSQ_CHECK_LAUNCH();
-    }
-    return LSQ_OK;
+    return run_variant(g, v[use], a, p.nblocks, s, smem_for(use));
 }
+}  // namespace
 
 int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, int ta, int rb, int tb, int rc,
                     const void *A, const void *B, void *C, double alpha, double beta, cudaStream_t s,
@@ -1103,6 +1183,13 @@ int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, 
     ga.b = b;
     ga.a_tm = g->pats[ra].tmap.p;
     ga.b_tm = g->pats[rb].tmap.p;
+    if (g_group_rec) {
+        // a step captured for a grouped launch: record the product, split the capture
+        g_group_rec->products.push_back(group_product(a, b, dtype, ta, tb, ga.a_tm, ga.b_tm));
+        LSQ_TRY(g_group_rec->split(s));
+        if (p.upper == 1 && mirror) LSQ_TRY(mirror_lower_gen(g, rc, b, dtype, C, s));
+        return LSQ_OK;
+    }
     const int threads = 256;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((p.nblocks + 7) / 8, (int64_t)g->num_sms * 8));
     note_launch();
@@ -1124,6 +1211,167 @@ int plan_launch_gen(lsq_geom g, int b, int dtype, const ProductPlan &p, int ra, 
         // C_ij = (C_ji)^T for j < i, any block size
         LSQ_TRY(mirror_lower_gen(g, rc, b, dtype, C, s));
     }
+    return LSQ_OK;
+}
+
+// ---- grouped products: one persistent launch over the products of several contexts -----
+thread_local GroupRecorder *g_group_rec = nullptr;
+
+int GroupRecorder::split(cudaStream_t s) {
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &gr);
+    if (e != cudaSuccess) return set_error(LSQ_ERR_CUDA, std::string("ending a step segment: ") + cudaGetErrorString(e));
+    segments.push_back(gr);
+    LSQ_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    return LSQ_OK;
+}
+
+GroupRecorder::~GroupRecorder() {
+    for (cudaGraph_t gr : segments)
+        if (gr) cudaGraphDestroy(gr);
+}
+
+namespace {
+// A product of a grouped launch, as the device sees it.
+struct GroupDesc {
+    PlanArgsGen ga;   // plan and operands; ga.b the block size
+    int ta, tb;       // operands read through transpose maps (b != 4)
+    int per_chunk;    // blocks of C per work item
+    int64_t chunk0;   // first work item of this product in the launch's queue
+};
+
+// The two forms of a work item, kept out of line so that the kernel's registers are those of
+// the larger form rather than of both together.
+template <typename T>
+__device__ __noinline__ void group_b4(const PlanArgs &a, int64_t t0, int64_t t1) {
+    b4_blocks<T, 4>(a, t0, t1, 16);
+}
+
+template <typename T, bool TA, bool TB>
+__device__ __noinline__ void group_t16(const PlanArgsGen &ga, int64_t t0, int64_t t1, T *S0, T *S1) {
+    t16_blocks<T, TA, TB>(ga, t0, t1, 8, S0, S1);
+}
+
+template <typename T, bool TA, bool TB>
+__device__ __noinline__ void group_gen(const PlanArgsGen &ga, int64_t t0, int64_t t1, T *S0, T *S1) {
+    gen_blocks<T, TA, TB>(ga, t0, t1, 8, S0, S1);
+}
+
+template <typename T>
+__device__ __forceinline__ void group_frames(const GroupDesc &q, int64_t t0, int64_t t1, T *S0, T *S1) {
+    if (q.ga.b >= 9) {
+        if (q.ta && q.tb) group_t16<T, true, true>(q.ga, t0, t1, S0, S1);
+        else if (q.ta) group_t16<T, true, false>(q.ga, t0, t1, S0, S1);
+        else if (q.tb) group_t16<T, false, true>(q.ga, t0, t1, S0, S1);
+        else group_t16<T, false, false>(q.ga, t0, t1, S0, S1);
+    } else {
+        if (q.ta && q.tb) group_gen<T, true, true>(q.ga, t0, t1, S0, S1);
+        else if (q.ta) group_gen<T, true, false>(q.ga, t0, t1, S0, S1);
+        else if (q.tb) group_gen<T, false, true>(q.ga, t0, t1, S0, S1);
+        else group_gen<T, false, false>(q.ga, t0, t1, S0, S1);
+    }
+}
+
+// Persistent: every thread block takes work items (per_chunk consecutive blocks of C, in the
+// plan's order, of one product) from the queue counter until it runs past nchunks.  The
+// blocks of an item are shared as in the stand-alone kernels: 16 lanes per 4 x 4 block, one
+// warp per larger block (16 x 16 frames for b >= 9).  Items only ever move forward, so no
+// thread block waits on another.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_mm_group(const GroupDesc *__restrict__ d, int nd, int64_t nchunks,
+                                                  unsigned long long *__restrict__ counter) {
+    __shared__ __align__(16) T stage[8][2][16 * kT16Stride];
+    __shared__ int64_t s_item;
+    const int w = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        __syncthreads();
+        if (item >= nchunks) break;
+        int k = 0;
+        while (k + 1 < nd && d[k + 1].chunk0 <= item) ++k;
+        const GroupDesc &q = d[k];
+        const int64_t t0 = (item - q.chunk0) * q.per_chunk;
+        const int64_t t1 = min(t0 + (int64_t)q.per_chunk, q.ga.p.nblocks);
+        const int b = q.ga.b;
+        if (b == 4) group_b4<T>(q.ga.p, t0 + (threadIdx.x >> 4), t1);
+        else group_frames<T>(q, t0 + w, t1, stage[w][0], stage[w][1]);
+    }
+}
+}  // namespace
+
+int group_prepare(const GroupProduct *products, int n, const lsq_geom g_any, GroupLaunch *out) {
+    if (n < 1 || !g_any) return set_error(LSQ_ERR_INVALID_ARG, "empty product group");
+    const int dtype = products[0].dtype;
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) {
+        if (products[k].dtype != dtype) return set_error(LSQ_ERR_INVALID_ARG, "a product group mixes precisions");
+        order[k] = k;
+    }
+    // the products with the costliest blocks first, so that the queue ends on short items
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return products[x].b > products[y].b; });
+    std::vector<GroupDesc> d(n);
+    int64_t chunks = 0;
+    for (int k = 0; k < n; ++k) {
+        const GroupProduct &q = products[order[k]];
+        GroupDesc &e = d[k];
+        PlanArgs &a = e.ga.p;
+        a.n = q.n;
+        a.upper = q.upper;
+        a.c_ptr = q.c_ptr;
+        a.nblocks = q.nblocks;
+        a.perm = q.perm;
+        a.item_ptr = q.item_ptr;
+        a.items = q.items;
+        a.a_ptr = q.a_ptr;
+        a.x_ptr = q.x_ptr;
+        a.c_row = q.c_row;
+        a.c_col = q.c_col;
+        a.A = q.A;
+        a.X = q.X;
+        a.C = q.C;
+        a.alpha = q.alpha;
+        a.beta = q.beta;
+        e.ga.b = q.b;
+        e.ga.a_tm = q.a_tm;
+        e.ga.b_tm = q.b_tm;
+        e.ta = q.ta;
+        e.tb = q.tb;
+        e.per_chunk = q.b == 4 ? 64 : 16;
+        e.chunk0 = chunks;
+        chunks += (q.nblocks + e.per_chunk - 1) / e.per_chunk;
+    }
+    void *dev = nullptr;
+    LSQ_CUDA_TRY(cudaMalloc(&dev, sizeof(GroupDesc) * n));
+    cudaError_t e = cudaMemcpy(dev, d.data(), sizeof(GroupDesc) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return set_error(LSQ_ERR_CUDA, std::string("uploading a product group: ") + cudaGetErrorString(e));
+    }
+    int per_sm = 1;
+    if (dtype == LSQ_F64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_group<double>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_group<float>, 256, 0);
+    out->desc = dev;
+    out->nprod = n;
+    out->dtype = dtype;
+    out->nchunks = chunks;
+    out->grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)g_any->num_sms * std::max(per_sm, 1)));
+    return LSQ_OK;
+}
+
+int group_launch(const GroupLaunch &gl, unsigned long long *counter, cudaStream_t s) {
+    LSQ_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    note_launch();
+    if (gl.dtype == LSQ_F64)
+        k_mm_group<double><<<gl.grid, 256, 0, s>>>(static_cast<const GroupDesc *>(gl.desc), gl.nprod, gl.nchunks,
+                                                   counter);
+    else
+        k_mm_group<float><<<gl.grid, 256, 0, s>>>(static_cast<const GroupDesc *>(gl.desc), gl.nprod, gl.nchunks,
+                                                  counter);
+    LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
 

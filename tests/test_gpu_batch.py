@@ -99,3 +99,103 @@ def test_batch_mixed_precision_converges_to_float64():
     for a, b in zip(r64, r32):
         assert a["status"] == 0
         assert abs(a["omega_ha_per_atom"] - b["omega_ha_per_atom"]) < 1e-6
+
+
+def _group_inputs():
+    """A batch with 4 x 4 blocks and one with 13 x 13 blocks (uneven systems in each)."""
+    specs4 = [(2, 0.05, batch_system_seed(5), None), (1, 0.1, batch_system_seed(6), None),
+              (3, 0.15, batch_system_seed(7), None)]
+    specs13 = [(1, 0.1, batch_system_seed(26), batch_system_seed(26) + 7),
+               (2, 0.05, batch_system_seed(27), batch_system_seed(27) + 7)]
+    out = []
+    for specs, b in ((specs4, 4), (specs13, 13)):
+        systems, bg, H, S = _batch(specs, b)
+        ctx = lsq.Lnv(bg, b, R_S, R_H, R_L)
+        out.append((systems, bg, ctx, H, S, b))
+    return out
+
+
+def _group_setup(mus):
+    parts = _group_inputs()
+    Ls, Ss, Hs = [], [], []
+    for systems, bg, ctx, H, S, b in parts:
+        Ls.append(_init_L(ctx, bg, S, b))
+        Ss.append(cuda(S))
+        Hs.append(cuda(H))
+    return parts, Ls, Ss, Hs
+
+
+def test_grouped_batch_matches_separate_batches_float64():
+    """One lsq_lnv_minimise_batch_group call over a 4 x 4 and a 13 x 13 batch (every product of
+    a step after the first one grouped persistent launch over both) against the two batches
+    minimised separately with their tuned kernels: the same trajectory to rounding (1e-9
+    relative in Omega and N_e after 14 steps; both paths sum each block's terms in float64, in
+    different orders)."""
+    lsq.build()
+    mus = [[-2.0, -1.5, -2.2], [-2.0, -1.8]]
+    parts, Ls, Ss, Hs = _group_setup(mus)
+    L_sep = [L.clone() for L in Ls]
+    reps = lsq.minimise_batch_group([p[2] for p in parts], Ls, Ss, Hs, mus, max_iter=14)
+    for c, (systems, bg, ctx, H, S, b) in enumerate(parts):
+        sep = ctx.minimise_batch(L_sep[c], Ss[c], Hs[c], mus[c], max_iter=14)
+        assert len(reps[c]) == len(sep) == len(systems)
+        for a, r in zip(reps[c], sep):
+            assert a["iterations"] == r["iterations"] == 14
+            assert abs(a["omega_ev"] - r["omega_ev"]) <= 1e-9 * abs(r["omega_ev"])
+            assert abs(a["ne"] - r["ne"]) <= 1e-9 * abs(r["ne"])
+        scale = L_sep[c].abs().max().item()
+        assert (Ls[c] - L_sep[c]).abs().max().item() <= 1e-7 * scale
+
+
+def test_grouped_batch_mixed_precision_minimum():
+    """Float32 products in the grouped launches, then float64 refinement: every system of both
+    batches converges and its minimum lies within 1e-6 Ha/atom of its float64 minimum from the
+    separate batch (the metric's tolerance)."""
+    lsq.build()
+    mus = [[-2.0, -1.5, -2.2], [-2.0, -1.8]]
+    parts, Ls, Ss, Hs = _group_setup(mus)
+    L_sep = [L.clone() for L in Ls]
+    reps = lsq.minimise_batch_group([p[2] for p in parts], Ls, Ss, Hs, mus, max_iter=300,
+                                    tol_ha_per_atom=1e-9, precision=lsq.F32, refine_iter=3)
+    for c, (systems, bg, ctx, H, S, b) in enumerate(parts):
+        ref = ctx.minimise_batch(L_sep[c], Ss[c], Hs[c], mus[c], max_iter=300, tol_ha_per_atom=1e-11)
+        for a, r in zip(reps[c], ref):
+            assert r["status"] == 0
+            assert a["iterations_fp64"] == 3
+            assert abs(a["omega_ha_per_atom"] - r["omega_ha_per_atom"]) < 1e-6
+
+
+def test_grouped_batch_block13_against_oracle():
+    """The 13 x 13 systems of a grouped call against the oracle's own minimisation (6 steps)."""
+    lsq.build()
+    parts = _group_inputs()
+    mus = [[-2.0, -2.0, -2.0], [-2.0, -2.0]]
+    Ls = [_init_L(p[2], p[1], p[4], p[5]) for p in parts]
+    reps = lsq.minimise_batch_group([p[2] for p in parts], Ls, [cuda(p[4]) for p in parts],
+                                    [cuda(p[3]) for p in parts], mus, max_iter=6)
+    systems = parts[1][0]
+    for k, (pos, cell, g, pH, Hk, Sk) in enumerate(systems):
+        m = OL.System(pos, cell)
+        pHo = m.pattern(R_H)
+        ref = OL.Lnv(m, oracle.Bsr(pHo, 13, Sk), oracle.Bsr(pHo, 13, Hk), R_L, mus[1][k])
+        L0 = OL.onsite_inverse_half(oracle.Bsr(pHo, 13, Sk), ref.pat_L)
+        Lr, _ = OL.minimise(ref, L0, 6)
+        om_ref, ne_ref = ref.energy(Lr)
+        assert abs(reps[1][k]["omega_ev"] - om_ref) <= 1e-8 * abs(om_ref)
+        assert abs(reps[1][k]["ne"] - ne_ref) <= 1e-8 * abs(ne_ref)
+
+
+def test_grouped_batch_argument_checks():
+    """Distinct geometries, a product precision the grouped launch runs, matching list lengths."""
+    lsq.build()
+    parts = _group_inputs()
+    systems, bg, ctx, H, S, b = parts[0]
+    L = _init_L(ctx, bg, S, b)
+    with pytest.raises(lsq.LsqError):
+        lsq.minimise_batch_group([ctx, ctx], [L, L.clone()], [cuda(S)] * 2, [cuda(H)] * 2,
+                                 [[-2.0] * 3] * 2, max_iter=1)
+    with pytest.raises(lsq.LsqError):
+        lsq.minimise_batch_group([ctx], [L], [cuda(S)], [cuda(H)], [[-2.0] * 3], max_iter=1,
+                                 precision=lsq.TF32X3)
+    with pytest.raises(ValueError):
+        lsq.minimise_batch_group([ctx], [L], [cuda(S)], [], [[-2.0] * 3], max_iter=1)
