@@ -228,10 +228,10 @@ class Geometry:
 
     def product_plan_info(self, range_a, range_b, range_c, triangle=0):
         """Statistics of the tensor-core plan of a product already run (lsq_product_plan_info)."""
-        out = (ctypes.c_int64 * 5)()
+        out = (ctypes.c_int64 * 6)()
         _check(load().lsq_product_plan_info(self.handle, range_a, range_b, range_c, triangle, out))
-        return {"triples": out[0], "dense_triples": out[1], "blocks_gathered": out[2], "tiles": out[3],
-                "auto_choice": out[4]}
+        return {"triples": out[0], "dense_triples": out[1], "block_slots": out[2], "tiles": out[3],
+                "auto_choice": out[4], "blocks_copied": out[5]}
 
     def adopt_schedules(self, other):
         """Use the product schedules tuned in another geometry of the same ranges."""

@@ -115,7 +115,8 @@ struct TcPlan {
     int grid = 0;                // CTAs the plan was laid out for
     int upper = 0;
     int64_t triples = 0;         // exact block triples of the computed blocks of C
-    int64_t units = 0;           // operand blocks gathered per launch (incl. zero fills)
+    int64_t units = 0;           // operand block slots filled per launch (incl. zeros)
+    int64_t present = 0;         // of those, blocks copied from op(A) or op(B)^T
     int64_t dense_triples = 0;   // block triples the MMAs execute (incl. zero blocks)
     DevBuf<int32_t> tile_nk;     // [ntiles] k-list length (a multiple of 16)
     DevBuf<int64_t> tile_posoff; // [ntiles] first stage record of the tile

@@ -18,9 +18,11 @@
 //    epilogue: one pass gives hi.hi + hi.lo + lo.hi + lo.lo.
 //  * Gathers.  The blocks of a stage (16 k of the list for the 16 rows j and the 8 rows i)
 //    are copied into shared memory by 16-byte asynchronous copies (cp.async), eight lanes
-//    per 128-byte block, so one warp instruction moves four whole cache lines; blocks a row
-//    does not hold are copied from a line of zeros, so every stage lands whole.  Each
-//    copying thread arrives on the stage's mbarrier when its copies complete.  The block
+//    per 128-byte block, so one warp instruction moves four whole cache lines; the lanes of
+//    a block a row does not hold store zeros instead (no L2 request), so every stage lands
+//    whole.  Each copying thread arrives on the stage's mbarrier twice: after its stores of
+//    zeros (with a proxy fence, as the MMAs read through the async proxy) and when its copies
+//    complete.  The block
 //    indices a CTA gathers are laid out by the plan as one stream of stage records, read
 //    four stages ahead, so no copy waits on an index load.  (Bulk copies of runs of
 //    consecutive blocks were measured first: at the ~4 blocks a run averages, their request
@@ -67,11 +69,6 @@ constexpr int kThreads = 352;                 // warps 7-10 read the accumulator
 constexpr int kRec = kRows * kKS;             // entries of a stage record
 constexpr uint16_t kAbsent = 0xffff;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait (1 s)
-
-// Sources of the copies that fill absent blocks: one 128-byte line per SM (up to 256), so
-// that the SMs' copies of zeros spread over the L2 slices.
-constexpr int kZeroBufs = 256;
-__device__ __align__(128) float g_tc_zero[kZeroBufs][32];
 
 // Index of (row r, block kk) in a stage record.  Rows come in six groups of four, one per
 // copying warp; lane l of warp w loads entries 64 w + 2 l and 64 w + 2 l + 1 and, for copy
@@ -133,6 +130,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
 // (the arrival counts against the count the barrier was initialised with).
 __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -202,6 +202,15 @@ __global__ void k_split_tf32(int64_t nnzb, const int64_t *__restrict__ tm, const
 }
 
 // ---- plan ------------------------------------------------------------------------------
+// Number of entries of pos[0, m) that name a block (>= 0).
+__global__ void k_count_present(int64_t m, const int32_t *__restrict__ pos, unsigned long long *__restrict__ out) {
+    unsigned long long c = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        c += pos[e] >= 0 ? 1ull : 0ull;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 struct TcBuild {
     int n, ngroups, upper;
     const int64_t *a_ptr, *x_ptr, *c_ptr;
@@ -453,7 +462,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(full(s), 32 * kCopyWarps);
+            // per copying thread and stage: one arrival after its stores of zeros, one when its
+            // copies have landed
+            mbar_init(full(s), 2 * 32 * kCopyWarps);
             mbar_init(empty(s), 1);
         }
         for (int b = 0; b < kPartials; ++b) {
@@ -481,7 +492,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         // four blocks: lane l copies 16-byte chunk l % 8 of block 4 (q % 4) + l / 8 of row
         // 4 w + q / 4 (q = 0..15).  The CTA's stage records are read four stages ahead.
         const char *arr = warp < 4 ? p.Xs : p.As;
-        const char *zero = reinterpret_cast<const char *>(g_tc_zero[blockIdx.x & (kZeroBufs - 1)]) + 16 * (lane & 7);
         const int sub = lane >> 3;
         const int S = p.cta_stages[blockIdx.x];
         const int32_t *rec = p.pos + p.tile_posoff[blockIdx.x] + 64 * warp + 2 * lane;
@@ -501,9 +511,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int v = __shfl_sync(0xffffffffu, (q & 1) ? p0.y : p0.x, 8 * sub + (q >> 1));
-                const char *src = v < 0 ? zero : arr + (int64_t)kUnit * v + 16 * (lane & 7);
-                cp_async16(dst0 + (uint32_t)((q >> 2) * (kKS * kUnit) + (4 * (q & 3) + sub) * kUnit), src);
+                const uint32_t dst = dst0 + (uint32_t)((q >> 2) * (kKS * kUnit) + (4 * (q & 3) + sub) * kUnit);
+                if (v < 0)
+                    st_shared_zero16(dst);  // a block the row does not hold
+                else
+                    cp_async16(dst, arr + (int64_t)kUnit * v + 16 * (lane & 7));
             }
+            // the zeros are generic-proxy stores that the MMAs read through the async proxy
+            fence_proxy_async();
+            mbar_arrive(full(slot));
             cp_async_arrive(full(slot));
             p0 = p1;
             p1 = p2;
@@ -734,7 +750,18 @@ int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cud
         note_launch();
         k_tc_fill<<<grid, 512, smem_fill, s>>>(a);
         LSQ_CHECK_LAUNCH();
+        // blocks the launches copy (the other slots are zeros stored in shared memory)
+        DevBuf<unsigned long long> cnt;
+        LSQ_TRY(cnt.alloc(1));
+        LSQ_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+        note_launch();
+        k_count_present<<<std::max(1, std::min<int>((int)((total + 255) / 256), g->num_sms * 8)), 256, 0, s>>>(
+            total, p.pos.p, cnt.p);
+        LSQ_CHECK_LAUNCH();
+        unsigned long long h = 0;
+        LSQ_CUDA_TRY(cudaMemcpyAsync(&h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
         LSQ_CUDA_TRY(cudaStreamSynchronize(s));  // the scratch lists are freed on return
+        p.present = (int64_t)h;
     }
     LSQ_TRY(plan_count_triples(g, ra, rb, rc, upper, &p.triples, s));
     if (std::getenv("LSQ_TC_LOG")) {
@@ -833,13 +860,14 @@ extern "C" int lsq_product_plan_info(lsq_geom g, int range_a, int range_b, int r
     auto ch = g->tc_choice.find(key);
     if (f == g->tcplans.end() && ch == g->tc_choice.end())
         return set_error(LSQ_ERR_INVALID_ARG, "no tensor-core plan or timing for these ranges yet");
-    for (int k = 0; k < 4; ++k) info_host[k] = -1;
+    for (int k = 0; k < 6; ++k) info_host[k] = -1;
     if (f != g->tcplans.end()) {
         const TcPlan &p = f->second;
         info_host[0] = p.triples;
         info_host[1] = p.dense_triples;
         info_host[2] = p.units;
         info_host[3] = p.ntiles;
+        info_host[5] = p.present;
     }
     info_host[4] = ch == g->tc_choice.end() ? -1 : ch->second.choice;
     return LSQ_OK;
