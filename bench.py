@@ -213,23 +213,33 @@ class Clocks:
         self.path = os.path.join("/tmp", "lsq_clocks_%d_%d.csv" % (os.getpid(), index))
 
     def start(self):
+        """Starts sampling every 50 ms and returns once the first sample is written (nvidia-smi
+        takes a moment to start), so that the timed region that follows is covered."""
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+        self.t_begin = time.time()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.06)  # one more sample after the timed region
         self.proc.terminate()
         self.proc.wait()
         self.f.close()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in open(self.path):
+        lines = open(self.path).read().splitlines()
+        # the first line was written before the timed region began
+        for ln in lines[1:] if len(lines) > 1 else lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -243,7 +253,7 @@ class Clocks:
                     reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 50}
 
 
 # ---- our arm -------------------------------------------------------------------
