@@ -184,16 +184,20 @@ __device__ __forceinline__ float tf32_round(float v) {
     return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
 }
 
-// Unit p of out: hi and lo of block p of X, or of X^T read through the transpose map tm
-// (block (i, j) of X^T is (X_ji)^T).  v - hi is exact in float32.
-template <bool TRANS>
+// Unit p of out: hi and lo of block p of X (MODE 0), of X^T read through the transpose map tm
+// (MODE 1; block (i, j) of X^T is (X_ji)^T), or of X + X^T (MODE 2, X on a symmetric pattern;
+// the sum rounded once in float32, as a separate symmetric sum would).  v - hi is exact in
+// float32.
+template <int MODE>
 __global__ void k_split_tf32(int64_t nnzb, const int64_t *__restrict__ tm, const float *__restrict__ X,
                              float *__restrict__ out) {
     const int64_t m = nnzb * 16;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = e >> 4;
         const int rc = (int)(e & 15);
-        const float v = TRANS ? X[16 * tm[p] + (rc & 3) * 4 + (rc >> 2)] : X[e];
+        const float v = MODE == 0   ? X[e]
+                        : MODE == 1 ? X[16 * tm[p] + (rc & 3) * 4 + (rc >> 2)]
+                                    : X[e] + X[16 * tm[p] + (rc & 3) * 4 + (rc >> 2)];
         const float hi = tf32_round(v);
         const float lo = tf32_round(v - hi);
         out[32 * p + rc] = hi;
@@ -779,17 +783,21 @@ int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cud
 
 namespace {
 
-int split_operand(lsq_geom g, int r, bool trans, const float *X, DevBuf<char> &buf, cudaStream_t s) {
+// mode: 0 X, 1 X^T, 2 X + X^T (see k_split_tf32).
+int split_operand(lsq_geom g, int r, int mode, const float *X, DevBuf<char> &buf, cudaStream_t s) {
     const int64_t nnzb = g->pats[r].nnzb;
     const size_t need = (size_t)kUnit * (size_t)std::max<int64_t>(nnzb, 1);
     if (buf.n < need) LSQ_TRY(buf.alloc(need));
     if (nnzb == 0) return LSQ_OK;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb * 16 + 255) / 256, (int64_t)g->num_sms * 16));
+    float *out = reinterpret_cast<float *>(buf.p);
     note_launch();
-    if (trans)
-        k_split_tf32<true><<<blocks, 256, 0, s>>>(nnzb, g->pats[r].tmap.p, X, reinterpret_cast<float *>(buf.p));
+    if (mode == 1)
+        k_split_tf32<1><<<blocks, 256, 0, s>>>(nnzb, g->pats[r].tmap.p, X, out);
+    else if (mode == 2)
+        k_split_tf32<2><<<blocks, 256, 0, s>>>(nnzb, g->pats[r].tmap.p, X, out);
     else
-        k_split_tf32<false><<<blocks, 256, 0, s>>>(nnzb, nullptr, X, reinterpret_cast<float *>(buf.p));
+        k_split_tf32<0><<<blocks, 256, 0, s>>>(nnzb, nullptr, X, out);
     LSQ_CHECK_LAUNCH();
     return LSQ_OK;
 }
@@ -806,7 +814,8 @@ int dev_err_ptr(lsq_geom g, int **out) {
 }
 
 int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, const float *B, int rc, float *C,
-                    double alpha, double beta, int upper, bool mirror, int64_t *triples, cudaStream_t s) {
+                    double alpha, double beta, int upper, bool mirror, int64_t *triples, cudaStream_t s,
+                    bool b_sym, bool reuse_a) {
     LSQ_TRY(ensure_tmap(g, ra, s));
     LSQ_TRY(ensure_tmap(g, rb, s));
     TcPlan *p = nullptr;
@@ -815,10 +824,18 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     if (g->n == 0 || g->pats[rc].nnzb == 0 || p->ntiles == 0) return LSQ_OK;
     if (!p->pos.p || !p->cpos.p || !p->tile_nk.p || !p->tile_posoff.p || !p->cta_stages.p)
         return set_error(LSQ_ERR_CUDA, "tensor-core plan without its records");
-    // op(A) and X = op(B)^T (B's rows when trans_b, else B read through its transpose map) in
-    // split form, in buffers held by g
-    LSQ_TRY(split_operand(g, ra, ta != 0, A, g->tc_a, s));
-    LSQ_TRY(split_operand(g, rb, tb == 0, B, g->tc_x, s));
+    // op(A) and X = op(B)^T (B's rows when trans_b, else B read through its transpose map; B +
+    // B^T when b_sym) in split form, in buffers held by g.  The split of A is kept when the
+    // caller says A is unchanged since the previous split of the same array.
+    const bool keep = reuse_a && g->tc_a_src == A && g->tc_a_range == ra && g->tc_a_trans == (ta != 0);
+    if (!keep) {
+        g->tc_a_src = nullptr;
+        LSQ_TRY(split_operand(g, ra, ta != 0 ? 1 : 0, A, g->tc_a, s));
+        g->tc_a_src = A;
+        g->tc_a_range = ra;
+        g->tc_a_trans = ta != 0;
+    }
+    LSQ_TRY(split_operand(g, rb, b_sym ? 2 : (tb == 0 ? 1 : 0), B, g->tc_x, s));
     int *err = nullptr;
     LSQ_TRY(dev_err_ptr(g, &err));
     TcArgs a;

@@ -444,3 +444,34 @@ def test_lnv_canonical_matches_oracle_trajectory(prec):
         assert abs(E - Er) <= 1e-4 * abs(Er)
         assert abs(N - Nr) <= 1e-4 * n0          # the last step's drift, before its correction
         assert abs(rep["ne"] - n0) <= 1e-5 * n0  # N_e held at the start of the last step
+
+
+def test_lnv_tf32x3_all_products_on_tensor_cores(monkeypatch):
+    """Every 4 x 4 product of the mixed step on the tensor cores (LSQ_TC_CHOICE=all=1 fixes the
+    choice instead of the timing), which also takes the step's fused tensor-core forms: the
+    split copy of Q + Q^T formed from Q, SL's split shared by the two gradient products, and
+    QD^T read through its transpose map.  Omega within 1e-6 Ha/atom and G within 2e-5 of max
+    abs G of the oracle at an intermediate L (216 atoms), and the minimum (float64 refinement
+    and final Omega) within 1e-6 Ha/atom of the oracle's."""
+    monkeypatch.setenv("LSQ_TC_CHOICE", "all=1")
+    g, ctx, ref, Hb, Sb = _lnv_setup(3, 0.05, config_seed(0), 8.0)
+    n = g.n_atoms
+    L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
+    L1, _ = OL.minimise(ref, L0, 3)
+    G = torch.zeros((ref.pat_L.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        om, _ = ctx.energy_gradient(cuda(L1.val), cuda(Sb.val), cuda(Hb.val), MU, G=G, precision=lsq.TF32X3)
+    g.device_status()
+    for ra, rb, rc, tri in ((3, 5, 2, 3), (3, 5, 2, 2), (2, 0, 3, 0)):
+        assert g.product_plan_info(ra, rb, rc, tri)["auto_choice"] == 1
+    om_ref, _ = ref.energy(L1)
+    assert abs(om - om_ref) / lsq.HARTREE_EV / n < 1e-6
+    Gr = ref.gradient(L1)
+    assert rel_err(G.cpu().numpy(), 0.5 * (Gr.val + oracle.transpose(Gr, Gr.pat).val)) < 2e-5
+    Lr, _ = OL.minimise(ref, L0, 200, tol_ha_per_atom=1e-10)
+    om_min = ref.energy(Lr)[0]
+    Lg = cuda(L0.val)
+    rep = ctx.minimise(Lg, cuda(Sb.val), cuda(Hb.val), MU, max_iter=200, tol_ha_per_atom=1e-9,
+                       precision=lsq.TF32X3, refine_iter=3)
+    g.device_status()
+    assert abs(rep["omega_ev"] - om_min) / lsq.HARTREE_EV / n < 1e-6
