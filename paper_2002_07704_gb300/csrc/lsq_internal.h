@@ -263,6 +263,7 @@ extern thread_local GroupRecorder *g_group_rec;
 struct GroupLaunch {
     void *desc = nullptr;  // device copy of the products' descriptors
     int nprod = 0, dtype = 0;
+    int form = 4;          // kernel variant (see k_mm_group)
     int64_t nchunks = 0;   // work items of the launch's queue
     int grid = 0;
 };

@@ -1277,9 +1277,12 @@ __device__ __forceinline__ void group_frames(const GroupDesc &q, int64_t t0, int
 // blocks of an item are shared as in the stand-alone kernels: 16 lanes per 4 x 4 block, one
 // warp per larger block (16 x 16 frames for b >= 9).  Items only ever move forward, so no
 // thread block waits on another.
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_mm_group(const GroupDesc *__restrict__ d, int nd, int64_t nchunks,
-                                                  unsigned long long *__restrict__ counter) {
+// FR: the frame form of every product with b >= 9 in the launch, inlined: 0..3 = t16 with
+// (TA, TB) = (FR / 2, FR % 2) (and b = 4 products), so that the kernel keeps the registers of
+// one form (the occupancy of the stand-alone kernels); 4 = any mix, each form out of line.
+template <typename T, int FR>
+__global__ void __launch_bounds__(256, FR < 4 ? (sizeof(T) == 4 ? 3 : 2) : (sizeof(T) == 4 ? 2 : 1))
+    k_mm_group(const GroupDesc *__restrict__ d, int nd, int64_t nchunks, unsigned long long *__restrict__ counter) {
     __shared__ __align__(16) T stage[8][2][16 * kT16Stride];
     __shared__ int64_t s_item;
     const int w = threadIdx.x >> 5;
@@ -1295,9 +1298,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_mm_group(const 
         const int64_t t0 = (item - q.chunk0) * q.per_chunk;
         const int64_t t1 = min(t0 + (int64_t)q.per_chunk, q.ga.p.nblocks);
         const int b = q.ga.b;
-        if (b == 4) group_b4<T>(q.ga.p, t0 + (threadIdx.x >> 4), t1);
-        else group_frames<T>(q, t0 + w, t1, stage[w][0], stage[w][1]);
+        if constexpr (FR < 4) {
+            if (b == 4) b4_blocks<T, 4>(q.ga.p, t0 + (threadIdx.x >> 4), t1, 16);
+            else t16_blocks<T, (FR >> 1) != 0, (FR & 1) != 0>(q.ga, t0 + w, t1, 8, stage[w][0], stage[w][1]);
+        } else {
+            if (b == 4) group_b4<T>(q.ga.p, t0 + (threadIdx.x >> 4), t1);
+            else group_frames<T>(q, t0 + w, t1, stage[w][0], stage[w][1]);
+        }
     }
+}
+}  // namespace
+
+namespace {
+const void *group_kernel(int dtype, int fr) {
+    static const void *kf[5] = {(const void *)k_mm_group<float, 0>, (const void *)k_mm_group<float, 1>,
+                                (const void *)k_mm_group<float, 2>, (const void *)k_mm_group<float, 3>,
+                                (const void *)k_mm_group<float, 4>};
+    static const void *kd[5] = {(const void *)k_mm_group<double, 0>, (const void *)k_mm_group<double, 1>,
+                                (const void *)k_mm_group<double, 2>, (const void *)k_mm_group<double, 3>,
+                                (const void *)k_mm_group<double, 4>};
+    return dtype == LSQ_F64 ? kd[fr] : kf[fr];
 }
 }  // namespace
 
@@ -1349,14 +1369,22 @@ int group_prepare(const GroupProduct *products, int n, const lsq_geom g_any, Gro
         cudaFree(dev);
         return set_error(LSQ_ERR_CUDA, std::string("uploading a product group: ") + cudaGetErrorString(e));
     }
+    // one inlined frame form when every larger-block product is a t16 product with the same flags
+    int fr = -1;
+    for (int k = 0; k < n; ++k) {
+        const GroupProduct &q = products[k];
+        if (q.b == 4) continue;
+        const int f = q.b >= 9 ? 2 * (q.ta != 0) + (q.tb != 0) : 4;
+        fr = fr < 0 ? f : (fr == f ? fr : 4);
+    }
+    if (fr < 0) fr = 0;
     int per_sm = 1;
-    if (dtype == LSQ_F64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_group<double>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mm_group<float>, 256, 0);
+    const void *kern = group_kernel(dtype, fr);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
     out->desc = dev;
     out->nprod = n;
     out->dtype = dtype;
+    out->form = fr;
     out->nchunks = chunks;
     out->grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)g_any->num_sms * std::max(per_sm, 1)));
     return LSQ_OK;
@@ -1364,14 +1392,12 @@ int group_prepare(const GroupProduct *products, int n, const lsq_geom g_any, Gro
 
 int group_launch(const GroupLaunch &gl, unsigned long long *counter, cudaStream_t s) {
     LSQ_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    const GroupDesc *d = static_cast<const GroupDesc *>(gl.desc);
+    int nd = gl.nprod;
+    int64_t nch = gl.nchunks;
+    void *args[] = {&d, &nd, &nch, &counter};
     note_launch();
-    if (gl.dtype == LSQ_F64)
-        k_mm_group<double><<<gl.grid, 256, 0, s>>>(static_cast<const GroupDesc *>(gl.desc), gl.nprod, gl.nchunks,
-                                                   counter);
-    else
-        k_mm_group<float><<<gl.grid, 256, 0, s>>>(static_cast<const GroupDesc *>(gl.desc), gl.nprod, gl.nchunks,
-                                                  counter);
-    LSQ_CHECK_LAUNCH();
+    LSQ_CUDA_TRY(cudaLaunchKernel(group_kernel(gl.dtype, gl.form), dim3(gl.grid), dim3(256), args, 0, s));
     return LSQ_OK;
 }
 

@@ -149,8 +149,8 @@ def test_grouped_batch_matches_separate_batches_float64():
 
 def test_grouped_batch_mixed_precision_minimum():
     """Float32 products in the grouped launches, then float64 refinement: every system of both
-    batches converges and its minimum lies within 1e-6 Ha/atom of its float64 minimum from the
-    separate batch (the metric's tolerance)."""
+    batches ends within 1e-6 Ha/atom (the metric's tolerance) of its float64 minimum, taken
+    from the separate batch run to |dOmega| < 1e-10 Ha/atom."""
     lsq.build()
     mus = [[-2.0, -1.5, -2.2], [-2.0, -1.8]]
     parts, Ls, Ss, Hs = _group_setup(mus)
@@ -158,7 +158,7 @@ def test_grouped_batch_mixed_precision_minimum():
     reps = lsq.minimise_batch_group([p[2] for p in parts], Ls, Ss, Hs, mus, max_iter=300,
                                     tol_ha_per_atom=1e-9, precision=lsq.F32, refine_iter=3)
     for c, (systems, bg, ctx, H, S, b) in enumerate(parts):
-        ref = ctx.minimise_batch(L_sep[c], Ss[c], Hs[c], mus[c], max_iter=300, tol_ha_per_atom=1e-11)
+        ref = ctx.minimise_batch(L_sep[c], Ss[c], Hs[c], mus[c], max_iter=400, tol_ha_per_atom=1e-10)
         for a, r in zip(reps[c], ref):
             assert r["status"] == 0
             assert a["iterations_fp64"] == 3
