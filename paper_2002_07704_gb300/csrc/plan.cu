@@ -476,92 +476,109 @@ __device__ __forceinline__ void load_a(const T *p, T (&v)[N]) {
 // take the list interleaved instead (team p items p, p + SPLIT, ...): a list is sorted by k, so
 // the teams of a group then read neighbouring blocks of A (distinct shared-memory banks) and of
 // B^T (shared cache lines).  THREADS fixes the block size, and with it the register budget.
-template <typename T, bool ROWS, int TEAM, bool SMEM = false, int SPLIT = 1, bool IL = false,
-          int THREADS = (ROWS ? 1024 : 256), bool W256 = false>
-__global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
-    static_assert(TEAM * SPLIT <= 32, "a group of teams must fit in a warp");
+// One block s = (i, j) of C for a team of TEAM lanes (a part of SPLIT teams sharing the
+// block's items); As: row i of A staged in shared memory (SMEM), else unused.
+template <typename T, int TEAM, bool SMEM, int SPLIT, bool IL, bool W256>
+__device__ __forceinline__ void rb_work(const PlanArgs &g, const T *As, int64_t s, int i, int part) {
     constexpr int RT = SubBlock<T, TEAM>::RT, CT = SubBlock<T, TEAM>::CT;
     constexpr int NCB = 4 / CT;  // column blocks per row block
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *As = reinterpret_cast<T *>(smem_raw);  // row i of A (SMEM variant only)
     const T *__restrict__ A = static_cast<const T *>(g.A);
     const T *__restrict__ X = static_cast<const T *>(g.X);
     T *__restrict__ C = static_cast<T *>(g.C);
     const int sub = threadIdx.x % TEAM;
     const int r0 = (sub / NCB) * RT, c0 = (sub % NCB) * CT;
-    auto work = [&](int64_t s, int i, int part) {
-        constexpr int AS = SMEM ? SmemStride<T>::v : 16;  // stride between blocks of A
-        const T *arow = (SMEM ? As : A + 16 * g.a_ptr[i]) + 4 * r0;
-        const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c0;
-        const int64_t i0 = g.item_ptr[s];
-        const int ntot = (int)(g.item_ptr[s + 1] - i0);
-        constexpr int STEP = IL ? SPLIT : 1;
-        const int q0 = IL ? part : (SPLIT == 1 ? 0 : (int)((int64_t)ntot * part / SPLIT));
-        const int nit = IL ? ntot : (SPLIT == 1 ? ntot : (int)((int64_t)ntot * (part + 1) / SPLIT));
-        const uint32_t *__restrict__ it = g.items + i0;
-        T acc[RT][CT];
+    constexpr int AS = SMEM ? SmemStride<T>::v : 16;  // stride between blocks of A
+    const T *arow = (SMEM ? As : A + 16 * g.a_ptr[i]) + 4 * r0;
+    const T *__restrict__ xrow = X + 16 * g.x_ptr[g.c_col[s]] + 4 * c0;
+    const int64_t i0 = g.item_ptr[s];
+    const int ntot = (int)(g.item_ptr[s + 1] - i0);
+    constexpr int STEP = IL ? SPLIT : 1;
+    const int q0 = IL ? part : (SPLIT == 1 ? 0 : (int)((int64_t)ntot * part / SPLIT));
+    const int nit = IL ? ntot : (SPLIT == 1 ? ntot : (int)((int64_t)ntot * (part + 1) / SPLIT));
+    const uint32_t *__restrict__ it = g.items + i0;
+    T acc[RT][CT];
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[r][c] = T(0);
+    int q = q0;
+    // the next pair of item words is fetched while the current pair's blocks load, so a
+    // pair costs one trip to L2 instead of two dependent ones
+    uint32_t w0 = q < nit ? __ldg(it + q) : 0u, w1 = q + STEP < nit ? __ldg(it + q + STEP) : 0u;
+    for (; q + STEP < nit; q += 2 * STEP) {
+        const int qn = q + 2 * STEP;
+        const uint32_t n0 = qn < nit ? __ldg(it + qn) : 0u;
+        const uint32_t n1 = qn + STEP < nit ? __ldg(it + qn + STEP) : 0u;
+        T a0[4 * RT], x0[4 * CT], a1[4 * RT], x1[4 * CT];
+        load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w0 & 0xffffu), a0);
+        load_x<W256>(xrow + 16 * (w0 >> 16), x0);
+        load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w1 & 0xffffu), a1);
+        load_x<W256>(xrow + 16 * (w1 >> 16), x1);
 #pragma unroll
         for (int r = 0; r < RT; ++r)
 #pragma unroll
-            for (int c = 0; c < CT; ++c) acc[r][c] = T(0);
-        int q = q0;
-        // the next pair of item words is fetched while the current pair's blocks load, so a
-        // pair costs one trip to L2 instead of two dependent ones
-        uint32_t w0 = q < nit ? __ldg(it + q) : 0u, w1 = q + STEP < nit ? __ldg(it + q + STEP) : 0u;
-        for (; q + STEP < nit; q += 2 * STEP) {
-            const int qn = q + 2 * STEP;
-            const uint32_t n0 = qn < nit ? __ldg(it + qn) : 0u;
-            const uint32_t n1 = qn + STEP < nit ? __ldg(it + qn + STEP) : 0u;
-            T a0[4 * RT], x0[4 * CT], a1[4 * RT], x1[4 * CT];
-            load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w0 & 0xffffu), a0);
-            load_x<W256>(xrow + 16 * (w0 >> 16), x0);
-            load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w1 & 0xffffu), a1);
-            load_x<W256>(xrow + 16 * (w1 >> 16), x1);
+            for (int c = 0; c < CT; ++c)
 #pragma unroll
-            for (int r = 0; r < RT; ++r)
-#pragma unroll
-                for (int c = 0; c < CT; ++c)
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
-                        acc[r][c] = fma(a1[4 * r + t], x1[4 * c + t], acc[r][c]);
-                    }
-            w0 = n0;
-            w1 = n1;
-        }
-        if (q < nit) {
-            T a0[4 * RT], x0[4 * CT];
-            load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w0 & 0xffffu), a0);
-            load_x<W256>(xrow + 16 * (w0 >> 16), x0);
-#pragma unroll
-            for (int r = 0; r < RT; ++r)
-#pragma unroll
-                for (int c = 0; c < CT; ++c)
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
-        }
-        if (SPLIT > 1) {
-            const int lane = threadIdx.x & 31;
-            const int gsz = TEAM * SPLIT;
-            const unsigned gmask = gsz == 32 ? 0xffffffffu : (((1u << gsz) - 1u) << (lane / gsz * gsz));
-#pragma unroll
-            for (int off = TEAM; off < gsz; off <<= 1)
-#pragma unroll
-                for (int r = 0; r < RT; ++r)
-#pragma unroll
-                    for (int c = 0; c < CT; ++c) acc[r][c] += __shfl_xor_sync(gmask, acc[r][c], off);
-            if (part != 0) return;
-        }
-        T *dst = C + 16 * s;
+                for (int t = 0; t < 4; ++t) {
+                    acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
+                    acc[r][c] = fma(a1[4 * r + t], x1[4 * c + t], acc[r][c]);
+                }
+        w0 = n0;
+        w1 = n1;
+    }
+    if (q < nit) {
+        T a0[4 * RT], x0[4 * CT];
+        load_a<SMEM, T, 4 * RT, W256>(arow + AS * (w0 & 0xffffu), a0);
+        load_x<W256>(xrow + 16 * (w0 >> 16), x0);
 #pragma unroll
         for (int r = 0; r < RT; ++r)
 #pragma unroll
-            for (int c = 0; c < CT; ++c) {
-                const int e = (r0 + r) * 4 + c0 + c;
-                const T v = (T)g.alpha * acc[r][c];
-                dst[e] = g.beta != 0.0 ? fma((T)g.beta, dst[e], v) : v;
-            }
-    };
+            for (int c = 0; c < CT; ++c)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) acc[r][c] = fma(a0[4 * r + t], x0[4 * c + t], acc[r][c]);
+    }
+    if (SPLIT > 1) {
+        const int lane = threadIdx.x & 31;
+        const int gsz = TEAM * SPLIT;
+        const unsigned gmask = gsz == 32 ? 0xffffffffu : (((1u << gsz) - 1u) << (lane / gsz * gsz));
+#pragma unroll
+        for (int off = TEAM; off < gsz; off <<= 1)
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int c = 0; c < CT; ++c) acc[r][c] += __shfl_xor_sync(gmask, acc[r][c], off);
+        if (part != 0) return;
+    }
+    T *dst = C + 16 * s;
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+            const int e = (r0 + r) * 4 + c0 + c;
+            const T v = (T)g.alpha * acc[r][c];
+            dst[e] = g.beta != 0.0 ? fma((T)g.beta, dst[e], v) : v;
+        }
+}
+
+// Blocks t0, t0 + step, ... (< t1) of C in the plan's order, one per team of TEAM lanes.
+template <typename T, int TEAM>
+__device__ __forceinline__ void rb_grid_blocks(const PlanArgs &g, int64_t t0, int64_t t1, int64_t step) {
+    for (int64_t t = t0; t < t1; t += step) {
+        const int64_t s = g.perm[t];
+        const int i = (int)g.c_row[s];
+        if (tri_skip(g.upper, i, g.c_col[s])) continue;
+        rb_work<T, TEAM, false, 1, false, false>(g, nullptr, s, i, 0);
+    }
+}
+
+template <typename T, bool ROWS, int TEAM, bool SMEM = false, int SPLIT = 1, bool IL = false,
+          int THREADS = (ROWS ? 1024 : 256), bool W256 = false>
+__global__ void __launch_bounds__(THREADS) k_mm_plan_b4_rb(PlanArgs g) {
+    static_assert(TEAM * SPLIT <= 32, "a group of teams must fit in a warp");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);  // row i of A (SMEM variant only)
+    const T *__restrict__ A = static_cast<const T *>(g.A);
+    auto work = [&](int64_t s, int i, int part) { rb_work<T, TEAM, SMEM, SPLIT, IL, W256>(g, As, s, i, part); };
     if (ROWS) {
         const int team = threadIdx.x / TEAM / SPLIT, nteams = blockDim.x / TEAM / SPLIT;
         const int part = (threadIdx.x / TEAM) % SPLIT;
@@ -1244,7 +1261,7 @@ struct GroupDesc {
 // the larger form rather than of both together.
 template <typename T>
 __device__ __noinline__ void group_b4(const PlanArgs &a, int64_t t0, int64_t t1) {
-    b4_blocks<T, 4>(a, t0, t1, 16);
+    rb_grid_blocks<T, 4>(a, t0, t1, 64);
 }
 
 template <typename T, bool TA, bool TB>
@@ -1274,8 +1291,9 @@ __device__ __forceinline__ void group_frames(const GroupDesc &q, int64_t t0, int
 
 // Persistent: every thread block takes work items (per_chunk consecutive blocks of C, in the
 // plan's order, of one product) from the queue counter until it runs past nchunks.  The
-// blocks of an item are shared as in the stand-alone kernels: 16 lanes per 4 x 4 block, one
-// warp per larger block (16 x 16 frames for b >= 9).  Items only ever move forward, so no
+// blocks of an item are shared as in the stand-alone kernels: 4 lanes per 4 x 4 block (2 x 2
+// values each, the register-blocked grid schedule), one warp per larger block (16 x 16
+// frames for b >= 9).  Items only ever move forward, so no
 // thread block waits on another.
 // FR: the frame form of every product with b >= 9 in the launch, inlined: 0..3 = t16 with
 // (TA, TB) = (FR / 2, FR % 2) (and b = 4 products), so that the kernel keeps the registers of
@@ -1299,10 +1317,10 @@ __global__ void __launch_bounds__(256, FR < 4 ? (sizeof(T) == 4 ? 3 : 2) : (size
         const int64_t t1 = min(t0 + (int64_t)q.per_chunk, q.ga.p.nblocks);
         const int b = q.ga.b;
         if constexpr (FR < 4) {
-            if (b == 4) b4_blocks<T, 4>(q.ga.p, t0 + (threadIdx.x >> 4), t1, 16);
+            if (b == 4) rb_grid_blocks<T, 4>(q.ga.p, t0 + (threadIdx.x >> 2), t1, 64);
             else t16_blocks<T, (FR >> 1) != 0, (FR & 1) != 0>(q.ga, t0 + w, t1, 8, stage[w][0], stage[w][1]);
         } else {
-            if (b == 4) group_b4<T>(q.ga.p, t0 + (threadIdx.x >> 4), t1);
+            if (b == 4) group_b4<T>(q.ga.p, t0 + (threadIdx.x >> 2), t1);
             else group_frames<T>(q, t0 + w, t1, stage[w][0], stage[w][1]);
         }
     }
@@ -1358,7 +1376,7 @@ int group_prepare(const GroupProduct *products, int n, const lsq_geom g_any, Gro
         e.ga.b_tm = q.b_tm;
         e.ta = q.ta;
         e.tb = q.tb;
-        e.per_chunk = q.b == 4 ? 64 : 16;
+        e.per_chunk = q.b == 4 ? 128 : 16;
         e.chunk0 = chunks;
         chunks += (q.nblocks + e.per_chunk - 1) / e.per_chunk;
     }
