@@ -177,10 +177,10 @@ int lsq_block_matmul_tri(lsq_geom g, int b, int precision,
 
 /*
  * With precision LSQ_TF32X3 and b = 4, lsq_block_matmul(_tri) runs the tensor-core product:
- * atoms i in groups of 8 and the atoms j of their rows of C in tiles of 32; per tile the
+ * atoms i in groups of 8 and the atoms j of their rows of C in tiles of 16; per tile the
  * blocks of op(B)^T and op(A) over the union of the group's rows of op(A) are gathered into
- * shared memory by 16-byte asynchronous copies (zeros stored for absent blocks) and
- * contracted by tcgen05.mma (kind::tf32) into float32 accumulators in tensor memory.  op(A) and op(B)^T are first copied in split form
+ * shared memory by bulk asynchronous copies and contracted by tcgen05.mma (kind::tf32) into
+ * a float32 accumulator in tensor memory.  op(A) and op(B)^T are first copied in split form
  * (a 128-byte hi/lo unit per block) into buffers held by g and grown on demand; the plan of
  * the first call for a (range_a, range_b, range_c, triangle) allocates and synchronises.
  * Arrays need only float alignment.  Limits: rows of at most 65534 blocks and at most
@@ -197,7 +197,7 @@ int lsq_measure_peak(int precision, double *tflops_host, void *stream);
 
 /* Statistics of the LSQ_TF32X3 plan of a product already run on g (triangle as for
  * lsq_block_matmul_tri), into info_host[6]: [0] the block triples of the computed blocks;
- * [1] the block triples the MMAs execute (32 j x 8 i x k-list per tile, zero blocks included;
+ * [1] the block triples the MMAs execute (16 j x 8 i x k-list per tile, zero blocks included;
  * each costs 4 x 128 tensor flops with the split operands); [2] the operand block slots a
  * launch fills in shared memory (128 bytes each); [3] the tiles; [5] the slots filled by
  * copying a block (128 bytes from op(A) or op(B)^T; the others are zeros stored in shared

@@ -9,34 +9,32 @@
 //    lo = tf32(v - hi), so hi + lo carries v to 22 bits.  A block is one 128-byte unit: the
 //    4 x 4 hi values (row-major), then the 4 x 4 lo values.
 //  * Tiles.  Atoms i are taken in groups of 8 (one diamond cell in cell-ordered systems).
-//    The atoms j of the group's rows of C are cut into tiles of 32, and each tile has one
+//    The atoms j of the group's rows of C are cut into tiles of 16, and each tile has one
 //    list of atoms k: the union of the group's rows of op(A), restricted to atoms that the
-//    tile's rows of op(B)^T hold (padded to a multiple of 8).  A tile is two accumulators
-//    (halves: atoms j 0-15 and 16-31) of M = 128 rows (16 j x {hi, lo} x 4 rows c of
-//    X_jk = (B_kj)^T) by N = 64 columns (8 i x {hi, lo} x 4 rows r of A_ik), and one MMA takes
-//    K = 8 (two atoms k x 4).  The {hi, lo} x {hi, lo} cross terms land in separate rows and
-//    columns and are summed in the epilogue: one pass gives hi.hi + hi.lo + lo.hi + lo.lo.
-//    Both halves share the stage's op(A) blocks, so a tile of 32 j copies fewer blocks per
-//    useful triple than two tiles of 16 (measured on the 4096-atom patterns: 0.39 against
-//    0.45 copied blocks per triple).
-//  * Gathers.  The blocks of a stage (8 k of the list for the 32 rows j and the 8 rows i)
+//    tile's rows of op(B)^T hold (padded to a multiple of 16).  A tile is one accumulator of
+//    M = 128 rows (16 j x {hi, lo} x 4 rows c of X_jk = (B_kj)^T) by N = 64 columns
+//    (8 i x {hi, lo} x 4 rows r of A_ik), and one MMA takes K = 8 (two atoms k x 4).  The
+//    {hi, lo} x {hi, lo} cross terms land in separate rows and columns and are summed in the
+//    epilogue: one pass gives hi.hi + hi.lo + lo.hi + lo.lo.
+//  * Gathers.  The blocks of a stage (16 k of the list for the 16 rows j and the 8 rows i)
 //    are copied into shared memory by 16-byte asynchronous copies (cp.async), eight lanes
 //    per 128-byte block, so one warp instruction moves four whole cache lines; the lanes of
 //    a block a row does not hold store zeros instead (no L2 request), so every stage lands
 //    whole.  Each copying thread arrives on the stage's mbarrier twice: after its stores of
 //    zeros (with a proxy fence, as the MMAs read through the async proxy) and when its copies
-//    complete.  The block indices a CTA gathers are laid out by the plan as one stream of
-//    stage records, read four stages ahead, so no copy waits on an index load.  (Bulk copies of runs of
+//    complete.  The block
+//    indices a CTA gathers are laid out by the plan as one stream of stage records, read
+//    four stages ahead, so no copy waits on an index load.  (Bulk copies of runs of
 //    consecutive blocks were measured first: at the ~4 blocks a run averages, their request
 //    rate, not the bytes, bounded the kernel.)
-//  * Roles.  Five warps issue the copies through a ring of four stages, one thread issues
-//    the MMAs, eight warps (four per half) read the accumulators (tcgen05.ld) and write the
-//    blocks of C the plan keeps.  The tensor core's float32 additions truncate, which biases
-//    long sums, so each stage (4 MMAs per half) accumulates into fresh accumulators of a
-//    ring of four in tensor memory (all 512 columns) and the epilogue adds the stages in
-//    float32 with rounding to nearest.  Every wait on an mbarrier is bounded: past the
-//    limit the kernel records an error code in a device word, stops issuing work, waits
-//    (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
+//  * Roles.  Six warps issue the copies through a ring of stages, one thread issues the
+//    MMAs, four warps read the accumulator (tcgen05.ld) and write the blocks of C the plan
+//    keeps.  The tensor core's float32 additions truncate, which biases long sums, so each
+//    stage (8 MMAs) accumulates into a fresh accumulator of a ring of four in tensor memory
+//    and the epilogue adds the stages in float32 with rounding to nearest.  Every wait on an
+//    mbarrier is bounded: past the limit the kernel records an error code in a device word,
+//    stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its tensor
+//    memory and returns.
 //
 // The plan (which blocks to gather, where to write) is built on the GPU once per geometry
 // and product, like the FMA path's plan.
@@ -55,33 +53,29 @@ namespace lsq {
 namespace {
 
 constexpr int kG = 8;                         // atoms i per group
-constexpr int kJT = 32;                       // atoms j per tile (two accumulator halves of 16)
-constexpr int kKS = 8;                        // atoms k per pipeline stage
+constexpr int kJT = 16;                       // atoms j per tile
+constexpr int kKS = 16;                       // atoms k per pipeline stage
 constexpr int kStages = 4;                    // stages in the ring
 constexpr int kUnit = 128;                    // bytes of a split block (hi 64, lo 64)
 constexpr int kRows = kJT + kG;               // gathered rows per stage
 constexpr int kPanelX = kJT * kKS * kUnit;    // X rows of a stage (M side), 32 KB
-constexpr int kStageBytes = kRows * kKS * kUnit;  // 40 KB
-constexpr int kHalfX = 16 * kKS * kUnit;      // X rows of one accumulator half (16 atoms j)
-constexpr int kN = 8 * kG;                    // accumulator columns of a tile half
+constexpr int kStageBytes = kRows * kKS * kUnit;  // 48 KB
+constexpr int kN = 8 * kG;                    // accumulator columns of a tile
 constexpr int kPartials = 4;                  // ring of per-stage accumulators in tensor memory
-constexpr int kStageCols = 2 * kN;            // two halves per stage
-constexpr int kTmemCols = kPartials * kStageCols;  // 512: all of tensor memory
-constexpr int kCopyWarps = 5;                 // warps 0-4 copy (8 rows of a stage each)
-constexpr int kMmaWarp = 5;                   // one thread of warp 5 issues the MMAs
-constexpr int kEpiWarps = 8;                  // warps 6-13 read the accumulators
-constexpr int kThreads = 32 * (kCopyWarps + 1 + kEpiWarps);  // 448
-constexpr int kTileC = kG * kJT;              // blocks (i, j) of C per tile
+constexpr int kTmemCols = kPartials * kN;
+constexpr int kCopyWarps = 6;                 // warps 0-5 copy (4 rows of a stage each)
+constexpr int kMmaWarp = 6;                   // one thread of warp 6 issues the MMAs
+constexpr int kThreads = 352;                 // warps 7-10 read the accumulator
 constexpr int kRec = kRows * kKS;             // entries of a stage record
 constexpr uint16_t kAbsent = 0xffff;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait (1 s)
 
-// Index of (row r, block kk) in a stage record.  Rows come in five groups of eight, one per
+// Index of (row r, block kk) in a stage record.  Rows come in six groups of four, one per
 // copying warp; lane l of warp w loads entries 64 w + 2 l and 64 w + 2 l + 1 and, for copy
-// instruction q (row 8 w + q / 2, block 4 (q % 2) + l / 8), finds its block index in lane
+// instruction q (row 4 w + q / 4, block 4 (q % 4) + l / 8), finds its block index in lane
 // 8 (l / 8) + q / 2, entry q % 2.
 __host__ __device__ constexpr int rec_index(int r, int kk) {
-    return 64 * (r >> 3) + 16 * (kk & 3) + 2 * (r & 7) + (kk >> 2);
+    return 64 * (r >> 2) + 16 * (kk & 3) + 2 * ((4 * (r & 3) + (kk >> 2)) >> 1) + ((4 * (r & 3) + (kk >> 2)) & 1);
 }
 
 __device__ __forceinline__ bool tri_skip_tc(int tri, int i, int j) {
@@ -434,7 +428,7 @@ __global__ void __launch_bounds__(512) k_tc_fill(TcBuild a) {
                 int32_t v = -1;
                 if (i < i1 && j >= 0 && !tri_skip_tc(a.upper, i, j) && map[j] != kAbsent)
                     v = (int32_t)(a.c_ptr[i] + map[j]);
-                a.cpos[(int64_t)kTileC * t + kJT * rr + jj] = v;
+                a.cpos[(int64_t)128 * t + kJT * rr + jj] = v;
             }
             __syncthreads();
             if (i < i1) map_row(a.c_ptr, a.c_col, i, map, false);
@@ -479,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         }
         for (int b = 0; b < kPartials; ++b) {
             mbar_init(tfull(b), 1);
-            mbar_init(tempty(b), kEpiWarps);
+            mbar_init(tempty(b), 4);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -497,11 +491,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp < kCopyWarps) {
-        // ---- copies.  Warp w fills rows 8w .. 8w + 7 of every stage (rows 0-31: atoms j of the
-        // tile, rows of X; 32-39: atoms i of the group, rows of op(A)).  One instruction moves
-        // four blocks: lane l copies 16-byte chunk l % 8 of block 4 (q % 2) + l / 8 of row
-        // 8 w + q / 2 (q = 0..15).  The CTA's stage records are read four stages ahead.
-        const char *arr = warp < kJT / 8 ? p.Xs : p.As;
+        // ---- copies.  Warp w fills rows 4w .. 4w + 3 of every stage (rows 0-15: atoms j of the
+        // tile, rows of X; 16-23: atoms i of the group, rows of op(A)).  One instruction moves
+        // four blocks: lane l copies 16-byte chunk l % 8 of block 4 (q % 4) + l / 8 of row
+        // 4 w + q / 4 (q = 0..15).  The CTA's stage records are read four stages ahead.
+        const char *arr = warp < 4 ? p.Xs : p.As;
         const int sub = lane >> 3;
         const int S = p.cta_stages[blockIdx.x];
         const int32_t *rec = p.pos + p.tile_posoff[blockIdx.x] + 64 * warp + 2 * lane;
@@ -509,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
             return st < S ? *reinterpret_cast<const int2 *>(rec + (int64_t)kRec * st) : make_int2(-1, -1);
         };
         int2 p0 = ld(0), p1 = ld(1), p2 = ld(2), p3 = ld(3);
-        const uint32_t dlane = (uint32_t)(8 * warp * kKS * kUnit + 16 * (lane & 7));
+        const uint32_t dlane = (uint32_t)(4 * warp * kKS * kUnit + 16 * (lane & 7));
         for (int st = 0; st < S; ++st) {
             const int2 p4 = ld(st + 4);
             const int slot = st % kStages;
@@ -521,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int v = __shfl_sync(0xffffffffu, (q & 1) ? p0.y : p0.x, 8 * sub + (q >> 1));
-                const uint32_t dst = dst0 + (uint32_t)((q >> 1) * (kKS * kUnit) + (4 * (q & 1) + sub) * kUnit);
+                const uint32_t dst = dst0 + (uint32_t)((q >> 2) * (kKS * kUnit) + (4 * (q & 3) + sub) * kUnit);
                 if (v < 0)
                     st_shared_zero16(dst);  // a block the row does not hold
                 else
@@ -540,10 +534,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
-            // ---- MMAs: per stage and accumulator half (atoms j 0-15 and 16-31 of the tile) 4 of
-            // M = 128, N = 64, K = 8 (two atoms k), into fresh accumulators of the ring (the
-            // tensor core's float32 additions truncate, so sums are kept to one stage there
-            // and the stages are added by the epilogue)
+            // ---- MMAs: per stage 8 of M = 128, N = 64, K = 8 (two atoms k), into a fresh
+            // accumulator of the ring (the tensor core's float32 additions truncate, so sums
+            // are kept to one stage there and the stages are added by the epilogue)
             constexpr uint32_t idesc = idesc_tf32(128, kN);
             int it = 0;
             bool ok = true;
@@ -560,16 +553,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                     // through the async proxy
                     fence_proxy_async();
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(buf * kStageCols);
+                    const uint32_t d = tmem + (uint32_t)(buf * kN);
                     const uint32_t sa = sbase + (uint32_t)slot * kStageBytes, sb = sa + kPanelX;
 #pragma unroll
                     for (int kk = 0; kk < kKS; kk += 2) {
+                        const uint64_t ad = sdesc(sa + kk * kUnit, kUnit, kKS * kUnit);
                         const uint64_t bd = sdesc(sb + kk * kUnit, kUnit, kKS * kUnit);
-#pragma unroll
-                        for (int hf = 0; hf < 2; ++hf) {
-                            const uint64_t ad = sdesc(sa + hf * kHalfX + kk * kUnit, kUnit, kKS * kUnit);
-                            mma_tf32(d + (uint32_t)(hf * kN), ad, bd, idesc, kk > 0 ? 1u : 0u);
-                        }
+                        mma_tf32(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
                     mma_commit(empty(slot));
                     mma_commit(tfull(buf));
@@ -585,23 +575,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                 }
         }
     } else {
-        // ---- epilogue: warps 6-9 read accumulator half 0 (atoms j 0-15 of the tile), warps
-        // 10-13 half 1, each warp the lanes of its quarter (warp % 4).  Thread row
-        // m = 8 (jj % 16) + 4 h + c of its half.  The stages' partial accumulators of a tile are
-        // added here in float32 (rounded to nearest), then the {hi, lo} cross terms are
-        // combined and the blocks of C written.
+        // ---- epilogue: thread row m = 8 jj + 4 h + c of the accumulator.  The stages' partial
+        // accumulators of a tile are added here in float32 (rounded to nearest), then the
+        // {hi, lo} cross terms are combined and the blocks of C written.
         const int sub = warp & 3;
-        const int half = (warp - kMmaWarp - 1) >> 2;
         const int m = 32 * sub + lane;
-        const int jj = 16 * half + (m >> 3), h = (m >> 2) & 1, c = m & 3;
-        const uint32_t tlane = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(half * kN);
+        const int jj = m >> 3, h = (m >> 2) & 1, c = m & 3;
+        const uint32_t tlane = tmem + ((uint32_t)(32 * sub) << 16);
         int it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
             const int nst = p.tile_nk[t] / kKS;
             int32_t cp[kG];
 #pragma unroll
-            for (int ii = 0; ii < kG; ++ii) cp[ii] = p.cpos[(int64_t)kTileC * t + kJT * ii + jj];
+            for (int ii = 0; ii < kG; ++ii) cp[ii] = p.cpos[(int64_t)128 * t + kJT * ii + jj];
             float acc[kN];
 #pragma unroll
             for (int e = 0; e < kN; ++e) acc[e] = 0.f;
@@ -614,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
 #pragma unroll
                 for (int q = 0; q < kN / 16; ++q) {
                     uint32_t v[16];
-                    tmem_ld16(tlane + (uint32_t)(buf * kStageCols + 16 * q), v);
+                    tmem_ld16(tlane + (uint32_t)(buf * kN + 16 * q), v);
                     tmem_wait_ld();
 #pragma unroll
                     for (int e = 0; e < 16; ++e) acc[16 * q + e] += __uint_as_float(v[e]);
@@ -714,7 +701,7 @@ int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cud
     LSQ_TRY(tile_j.alloc((size_t)kJT * T));
     LSQ_TRY(p.tile_nk.alloc(T));
     LSQ_TRY(p.tile_posoff.alloc(T));
-    LSQ_TRY(p.cpos.alloc((size_t)kTileC * T));
+    LSQ_TRY(p.cpos.alloc((size_t)128 * T));
     std::vector<int32_t> tnk(T, 0);
     std::vector<int64_t> tpo(T, 0), tko(T, 0);
     int64_t total = 0, klen = 0;
