@@ -11,31 +11,30 @@
 //  * Tiles.  Atoms i are taken in groups of 8 (one diamond cell in cell-ordered systems).
 //    The atoms j of the group's rows of C are cut into tiles of 16, and each tile has one
 //    list of atoms k: the union of the group's rows of op(A), restricted to atoms that the
-//    tile's rows of op(B)^T hold (padded to a multiple of 8).  A tile is one accumulator of
+//    tile's rows of op(B)^T hold (padded to a multiple of 16).  A tile is one accumulator of
 //    M = 128 rows (16 j x {hi, lo} x 4 rows c of X_jk = (B_kj)^T) by N = 64 columns
 //    (8 i x {hi, lo} x 4 rows r of A_ik), and one MMA takes K = 8 (two atoms k x 4).  The
 //    {hi, lo} x {hi, lo} cross terms land in separate rows and columns and are summed in the
 //    epilogue: one pass gives hi.hi + hi.lo + lo.hi + lo.lo.
-//  * Gathers.  The blocks of a stage (8 k of the list for the 16 rows j and the 8 rows i)
+//  * Gathers.  The blocks of a stage (16 k of the list for the 16 rows j and the 8 rows i)
 //    are copied into shared memory by 16-byte asynchronous copies (cp.async), eight lanes
 //    per 128-byte block, so one warp instruction moves four whole cache lines; the lanes of
 //    a block a row does not hold store zeros instead (no L2 request), so every stage lands
 //    whole.  Each copying thread arrives on the stage's mbarrier twice: after its stores of
 //    zeros (with a proxy fence, as the MMAs read through the async proxy) and when its copies
-//    complete.  The block indices a CTA gathers are laid out by the plan as one stream of
-//    stage records, read four stages ahead, so no copy waits on an index load.  The kernel
-//    is bound by the latency of these gathers (its rate follows the bytes in flight, not the
-//    DRAM traffic), so the ring has nine stages of 24 KB: up to 216 KB of copies in flight
-//    per SM.  (Bulk copies of runs of consecutive blocks were measured first: at the ~4
-//    blocks a run averages, their request rate, not the bytes, bounded the kernel.)
-//  * Roles.  Six warps issue the copies through the ring of stages, one thread issues the
+//    complete.  The block
+//    indices a CTA gathers are laid out by the plan as one stream of stage records, read
+//    four stages ahead, so no copy waits on an index load.  (Bulk copies of runs of
+//    consecutive blocks were measured first: at the ~4 blocks a run averages, their request
+//    rate, not the bytes, bounded the kernel.)
+//  * Roles.  Six warps issue the copies through a ring of stages, one thread issues the
 //    MMAs, four warps read the accumulator (tcgen05.ld) and write the blocks of C the plan
 //    keeps.  The tensor core's float32 additions truncate, which biases long sums, so each
-//    stage (4 MMAs) accumulates into a fresh accumulator of a ring of eight in tensor memory
-//    (all 512 columns) and the epilogue adds the stages in float32 with rounding to nearest.
-//    Every wait on an mbarrier is bounded: past the limit the kernel records an error code in
-//    a device word, stops issuing work, waits (bounded) for its copies and MMAs in flight,
-//    frees its tensor memory and returns.
+//    stage (8 MMAs) accumulates into a fresh accumulator of a ring of four in tensor memory
+//    and the epilogue adds the stages in float32 with rounding to nearest.  Every wait on an
+//    mbarrier is bounded: past the limit the kernel records an error code in a device word,
+//    stops issuing work, waits (bounded) for its copies and MMAs in flight, frees its tensor
+//    memory and returns.
 //
 // The plan (which blocks to gather, where to write) is built on the GPU once per geometry
 // and product, like the FMA path's plan.
@@ -55,17 +54,16 @@ namespace {
 
 constexpr int kG = 8;                         // atoms i per group
 constexpr int kJT = 16;                       // atoms j per tile
-constexpr int kKS = 8;                        // atoms k per pipeline stage
-constexpr int kStages = 9;                    // stages in the ring (216 KB of copies in flight)
+constexpr int kKS = 16;                       // atoms k per pipeline stage
+constexpr int kStages = 4;                    // stages in the ring
 constexpr int kUnit = 128;                    // bytes of a split block (hi 64, lo 64)
 constexpr int kRows = kJT + kG;               // gathered rows per stage
 constexpr int kPanelX = kJT * kKS * kUnit;    // X rows of a stage (M side), 32 KB
-constexpr int kStageBytes = kRows * kKS * kUnit;  // 24 KB
+constexpr int kStageBytes = kRows * kKS * kUnit;  // 48 KB
 constexpr int kN = 8 * kG;                    // accumulator columns of a tile
-constexpr int kPartials = 8;                  // ring of per-stage accumulators in tensor memory
+constexpr int kPartials = 4;                  // ring of per-stage accumulators in tensor memory
 constexpr int kTmemCols = kPartials * kN;
 constexpr int kCopyWarps = 6;                 // warps 0-5 copy (4 rows of a stage each)
-static_assert(kRows == 4 * kCopyWarps && kKS == 8, "copy mapping: 4 rows of 8 blocks per warp");
 constexpr int kMmaWarp = 6;                   // one thread of warp 6 issues the MMAs
 constexpr int kThreads = 352;                 // warps 7-10 read the accumulator
 constexpr int kRec = kRows * kKS;             // entries of a stage record
@@ -73,10 +71,11 @@ constexpr uint16_t kAbsent = 0xffff;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait (1 s)
 
 // Index of (row r, block kk) in a stage record.  Rows come in six groups of four, one per
-// copying warp; lane l of warp w loads entry 32 w + l and, for copy instruction q (row
-// 4 w + q / 2, block 4 (q % 2) + l / 8), finds its block index in lane 8 (l / 8) + q.
+// copying warp; lane l of warp w loads entries 64 w + 2 l and 64 w + 2 l + 1 and, for copy
+// instruction q (row 4 w + q / 4, block 4 (q % 4) + l / 8), finds its block index in lane
+// 8 (l / 8) + q / 2, entry q % 2.
 __host__ __device__ constexpr int rec_index(int r, int kk) {
-    return 32 * (r >> 2) + 8 * (kk & 3) + 2 * (r & 3) + (kk >> 2);
+    return 64 * (r >> 2) + 16 * (kk & 3) + 2 * ((4 * (r & 3) + (kk >> 2)) >> 1) + ((4 * (r & 3) + (kk >> 2)) & 1);
 }
 
 __device__ __forceinline__ bool tri_skip_tc(int tri, int i, int j) {
@@ -316,7 +315,7 @@ __global__ void __launch_bounds__(512) k_tc_groups(TcBuild a, int32_t *__restric
     }
 }
 
-// Pass 2: atoms j of each tile and the length of its k-list (a multiple of 8).
+// Pass 2: atoms j of each tile and the length of its k-list (a multiple of 16).
 __global__ void __launch_bounds__(512) k_tc_tiles(TcBuild a) {
     extern __shared__ __align__(16) uint32_t bm[];
     __shared__ int sh[32];
@@ -494,17 +493,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
     if (warp < kCopyWarps) {
         // ---- copies.  Warp w fills rows 4w .. 4w + 3 of every stage (rows 0-15: atoms j of the
         // tile, rows of X; 16-23: atoms i of the group, rows of op(A)).  One instruction moves
-        // four blocks: lane l copies 16-byte chunk l % 8 of block 4 (q % 2) + l / 8 of row
-        // 4 w + q / 2 (q = 0..7).  The CTA's stage records are read four stages ahead.
+        // four blocks: lane l copies 16-byte chunk l % 8 of block 4 (q % 4) + l / 8 of row
+        // 4 w + q / 4 (q = 0..15).  The CTA's stage records are read four stages ahead.
         const char *arr = warp < 4 ? p.Xs : p.As;
         const int sub = lane >> 3;
         const int S = p.cta_stages[blockIdx.x];
-        const int32_t *rec = p.pos + p.tile_posoff[blockIdx.x] + 32 * warp + lane;
-        auto ld = [&](int st) -> int { return st < S ? rec[(int64_t)kRec * st] : -1; };
-        int p0 = ld(0), p1 = ld(1), p2 = ld(2), p3 = ld(3);
+        const int32_t *rec = p.pos + p.tile_posoff[blockIdx.x] + 64 * warp + 2 * lane;
+        auto ld = [&](int st) -> int2 {
+            return st < S ? *reinterpret_cast<const int2 *>(rec + (int64_t)kRec * st) : make_int2(-1, -1);
+        };
+        int2 p0 = ld(0), p1 = ld(1), p2 = ld(2), p3 = ld(3);
         const uint32_t dlane = (uint32_t)(4 * warp * kKS * kUnit + 16 * (lane & 7));
         for (int st = 0; st < S; ++st) {
-            const int p4 = ld(st + 4);
+            const int2 p4 = ld(st + 4);
             const int slot = st % kStages;
             const uint32_t ph = (uint32_t)(st / kStages) & 1u;
             bool ok = mbar_wait(empty(slot), ph ^ 1u, abort_flag, p.err, 1);
@@ -512,9 +513,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
             if (!ok) break;
             const uint32_t dst0 = sbase + (uint32_t)slot * kStageBytes + dlane;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int v = __shfl_sync(0xffffffffu, p0, 8 * sub + q);
-                const uint32_t dst = dst0 + (uint32_t)((q >> 1) * (kKS * kUnit) + (4 * (q & 1) + sub) * kUnit);
+            for (int q = 0; q < 16; ++q) {
+                const int v = __shfl_sync(0xffffffffu, (q & 1) ? p0.y : p0.x, 8 * sub + (q >> 1));
+                const uint32_t dst = dst0 + (uint32_t)((q >> 2) * (kKS * kUnit) + (4 * (q & 3) + sub) * kUnit);
                 if (v < 0)
                     st_shared_zero16(dst);  // a block the row does not hold
                 else
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
-            // ---- MMAs: per stage 4 of M = 128, N = 64, K = 8 (two atoms k), into a fresh
+            // ---- MMAs: per stage 8 of M = 128, N = 64, K = 8 (two atoms k), into a fresh
             // accumulator of the ring (the tensor core's float32 additions truncate, so sums
             // are kept to one stage there and the stages are added by the epilogue)
             constexpr uint32_t idesc = idesc_tf32(128, kN);
@@ -642,8 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 512;
-static_assert((2 * kStages + 2 * kPartials + 1) * 8 + 8 <= 512, "barriers, TMEM slot and flag");
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 256;
 
 }  // namespace
 
