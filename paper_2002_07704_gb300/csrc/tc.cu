@@ -598,14 +598,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
+                // all four loads of the stage in flight before one wait
+                uint32_t v[kN / 16][16];
 #pragma unroll
-                for (int q = 0; q < kN / 16; ++q) {
-                    uint32_t v[16];
-                    tmem_ld16(tlane + (uint32_t)(buf * kN + 16 * q), v);
-                    tmem_wait_ld();
+                for (int q = 0; q < kN / 16; ++q) tmem_ld16(tlane + (uint32_t)(buf * kN + 16 * q), v[q]);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) acc[16 * q + e] += __uint_as_float(v[e]);
-                }
+                for (int q = 0; q < kN / 16; ++q)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) acc[16 * q + e] += __uint_as_float(v[q][e]);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty(buf));
