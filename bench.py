@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-tol", action="store_true", help="skip the runs to tolerance")
     p.add_argument("--cpu-sample-rows", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-steps", type=int, default=3,
+                   help="timed steps of the 48-system batched workload in the default line (0: skip)")
     p.add_argument("--md-steps", type=int, default=8,
                    help="extended-Lagrangian MD steps of the 4096-atom system (0: skip)")
     p.add_argument("--cells", default="4,6,8,10,12,16",
@@ -741,6 +743,17 @@ def run_ours(args):
                           "with the float64 evaluation of the result and the copy of L back"
                           % args.steps)}
 
+    # --- the 48-system batched workload (uneven sizes, 4x4 and 13x13 blocks), float32 products:
+    # one grouped call over both halves against the halves run separately; single GPU only ---
+    batch = None
+    if world == 1 and args.batch_steps > 0:
+        ctx.close()
+        geom.close()
+        del ctx, geom, L, L0, Lt, Lm, L64, Hd, Sd, Ldev, Sdev, Hdev
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        batch = batch_section(lsq, torch, stream, args.batch_steps, 2, 0)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -832,6 +845,7 @@ def run_ours(args):
                                                "on the 6.6 A range"),
             "clocks": clocks,
             "e2e": e2e,
+            "batch": batch,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "last_report": {"mixed": rep, "fp64": rep64, "mixed_f32": rep_f32, "e2e": rep_e2e},

@@ -185,8 +185,10 @@ int lsq_block_matmul_tri(lsq_geom g, int b, int precision,
  * the first call for a (range_a, range_b, range_c, triangle) allocates and synchronises.
  * Arrays need only float alignment.  Limits: rows of at most 65534 blocks and at most
  * 2^31 - 1 blocks in C (LSQ_ERR_UNSUPPORTED).  The kernel bounds every wait on its
- * pipeline barriers (1 s); if one expires it records an error in g and returns early, and
- * lsq_device_status reports it.  Calls on different streams race on the split buffers.
+ * pipeline barriers (1 s; the environment variable LSQ_TC_WAIT_NS, in ns, lowers it for
+ * tests of this path); if one expires it records an error in g, drains its copies and MMAs,
+ * frees its tensor memory and returns early, and lsq_device_status reports it.  Calls on
+ * different streams race on the split buffers.
  */
 
 /* Measured FMA rate of this GPU in TFLOP/s (2 flop per fused multiply-add): a loop of

@@ -22,11 +22,11 @@
 //    a block a row does not hold store zeros instead (no L2 request), so every stage lands
 //    whole.  Each copying thread arrives on the stage's mbarrier twice: after its stores of
 //    zeros (with a proxy fence, as the MMAs read through the async proxy) and when its copies
-//    complete.  The block
-//    indices a CTA gathers are laid out by the plan as one stream of stage records, read
-//    four stages ahead, so no copy waits on an index load.  (Bulk copies of runs of
-//    consecutive blocks were measured first: at the ~4 blocks a run averages, their request
-//    rate, not the bytes, bounded the kernel.)
+//    complete.  The block indices a CTA gathers are laid out by the plan as one stream of
+//    stage records, read four stages ahead, so no copy waits on an index load.  The kernel
+//    is bound by the rate of these gathers (about 10 TB/s of scattered 128-byte lines), not
+//    by DRAM.  (Bulk copies of runs of consecutive blocks were measured first: at the ~4
+//    blocks a run averages, their request rate, not the bytes, bounded the kernel.)
 //  * Roles.  Six warps issue the copies through a ring of stages, one thread issues the
 //    MMAs, four warps read the accumulator (tcgen05.ld) and write the blocks of C the plan
 //    keeps.  The tensor core's float32 additions truncate, which biases long sums, so each
@@ -111,11 +111,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Waits for the phase of the given parity; false if the CTA aborted or the wait ran past
 // its limit (which then records `code` in *err and raises the abort flag).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
-                                          int code) {
+                                          int code, unsigned long long limit_ns) {
     const unsigned long long t0 = globaltimer();
     while (!mbar_try(bar, parity)) {
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             *abort_flag = 1;
             return false;
@@ -447,6 +447,7 @@ struct TcArgs {
     float *C;
     float alpha, beta;
     int *err;
+    unsigned long long wait_ns;  // bound of the pipeline waits (the final drain keeps kWaitNs)
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
             const int2 p4 = ld(st + 4);
             const int slot = st % kStages;
             const uint32_t ph = (uint32_t)(st / kStages) & 1u;
-            bool ok = mbar_wait(empty(slot), ph ^ 1u, abort_flag, p.err, 1);
+            bool ok = mbar_wait(empty(slot), ph ^ 1u, abort_flag, p.err, 1, p.wait_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             const uint32_t dst0 = sbase + (uint32_t)slot * kStageBytes + dlane;
@@ -544,10 +545,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                 const int nk = p.tile_nk[t];
                 for (int k0 = 0; k0 < nk; k0 += kKS, ++it) {
                     const int buf = it % kPartials;
-                    ok = mbar_wait(tempty(buf), ((uint32_t)(it / kPartials) & 1u) ^ 1u, abort_flag, p.err, 3);
+                    ok = mbar_wait(tempty(buf), ((uint32_t)(it / kPartials) & 1u) ^ 1u, abort_flag, p.err, 3, p.wait_ns);
                     if (!ok) break;
                     const int slot = it % kStages;
-                    ok = mbar_wait(full(slot), (uint32_t)(it / kStages) & 1u, abort_flag, p.err, 2);
+                    ok = mbar_wait(full(slot), (uint32_t)(it / kStages) & 1u, abort_flag, p.err, 2, p.wait_ns);
                     if (!ok) break;
                     // the stage was written by cp.async (generic proxy); the MMAs read it
                     // through the async proxy
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
             for (int e = 0; e < kN; ++e) acc[e] = 0.f;
             for (int st = 0; st < nst; ++st, ++it) {
                 const int buf = it % kPartials;
-                ok = mbar_wait(tfull(buf), (uint32_t)(it / kPartials) & 1u, abort_flag, p.err, 4);
+                ok = mbar_wait(tfull(buf), (uint32_t)(it / kPartials) & 1u, abort_flag, p.err, 4, p.wait_ns);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
@@ -852,6 +853,10 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     a.alpha = (float)alpha;
     a.beta = (float)beta;
     a.err = err;
+    // LSQ_TC_WAIT_NS lowers the bound of the pipeline waits (0: any wait that does not succeed at
+    // once expires), so that a test can check the timeout path and its status; default 1 s
+    a.wait_ns = kWaitNs;
+    if (const char *w = std::getenv("LSQ_TC_WAIT_NS")) a.wait_ns = std::strtoull(w, nullptr, 10);
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_tc_product, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
     note_launch();
     k_tc_product<<<p->grid, kThreads, kSmemBytes, s>>>(a);

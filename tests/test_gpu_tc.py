@@ -248,3 +248,35 @@ def test_explicit_tf32x3_after_the_mixed_choice(monkeypatch):
             assert set(choices.values()) == {0}
         _explicit_products_match(g, choices, 4 + forced)
         monkeypatch.delenv("LSQ_TC_CHOICE", raising=False)
+
+
+def test_tf32x3_expired_wait_reports_timeout(monkeypatch):
+    """Failure detection of the tensor-core product without a GPU fault.  With the bound of its
+    pipeline waits set to 0 ns (LSQ_TC_WAIT_NS=0) a wait that does not succeed at once expires:
+    the kernel records which wait gave up, drains its copies and MMAs (the final drain keeps its
+    1 s bound), frees its tensor memory and returns.  lsq_device_status then reports
+    LSQ_ERR_TIMEOUT once and clears it, and the geometry stays usable: the same product with the
+    default bound matches the float32 FMA product (512 atoms)."""
+    pos, cell = si(4, 0.05, config_seed(0))
+    ranges = lsq.lnv_required_ranges(6.6, 6.6, 8.0)
+    g = gpu_geometry(pos, cell, ranges)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.randn((g.nnzb(3), 4, 4), dtype=torch.float32, device="cuda", generator=gen)
+    B = torch.randn((g.nnzb(5), 4, 4), dtype=torch.float32, device="cuda", generator=gen)
+    C = torch.zeros((g.nnzb(2), 4, 4), dtype=torch.float32, device="cuda")
+    kw = dict(trans_b=True, triangle=2)
+    lsq.block_matmul(g, 4, A, 3, B, 5, C, 2, precision=lsq.TF32X3, **kw)  # plan built, default bound
+    g.device_status()
+    monkeypatch.setenv("LSQ_TC_WAIT_NS", "0")
+    lsq.block_matmul(g, 4, A, 3, B, 5, C, 2, precision=lsq.TF32X3, **kw)
+    with pytest.raises(lsq.LsqError) as e:
+        g.device_status()
+    assert e.value.code == 8
+    g.device_status()  # reported once, then cleared
+    monkeypatch.delenv("LSQ_TC_WAIT_NS")
+    Cf = torch.zeros_like(C)
+    lsq.block_matmul(g, 4, A, 3, B, 5, C, 2, precision=lsq.TF32X3, **kw)
+    lsq.block_matmul(g, 4, A, 3, B, 5, Cf, 2, precision=lsq.F32, **kw)
+    torch.cuda.synchronize()
+    g.device_status()
+    assert (C - Cf).abs().max().item() <= 2e-5 * Cf.abs().max().item()
