@@ -445,6 +445,7 @@ struct TcArgs {
     const int32_t *pos;
     const char *As, *Xs;  // split units of op(A) and of X = op(B)^T
     float *C;
+    const int64_t *c_tm;  // transpose map of C's pattern: also write C_ji = C_ij^T (or null)
     float alpha, beta;
     int *err;
     unsigned long long wait_ns;  // bound of the pipeline waits (the final drain keeps kWaitNs)
@@ -629,10 +630,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
                 for (int ii = 0; ii < kG; ++ii) {
                     if (cp[ii] < 0) continue;
                     float *dst = p.C + 16 * (int64_t)cp[ii] + c;
+                    float w[4];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         const float v = p.alpha * s[ii][r];
-                        dst[4 * r] = p.beta != 0.f ? fmaf(p.beta, dst[4 * r], v) : v;
+                        w[r] = p.beta != 0.f ? fmaf(p.beta, dst[4 * r], v) : v;
+                        dst[4 * r] = w[r];
+                    }
+                    if (p.c_tm) {
+                        // symmetric result: row c of the mirrored block C_ji is column c of C_ij
+                        const int64_t q = p.c_tm[cp[ii]];
+                        if (q != cp[ii]) {
+                            float *m = p.C + 16 * q + 4 * c;
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) m[r] = w[r];
+                        }
                     }
                 }
             }
@@ -850,6 +862,11 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     a.As = g->tc_a.p;
     a.Xs = g->tc_x.p;
     a.C = C;
+    a.c_tm = nullptr;
+    if (upper == 1 && mirror) {
+        LSQ_TRY(ensure_tmap(g, rc, s));
+        a.c_tm = g->pats[rc].tmap.p;
+    }
     a.alpha = (float)alpha;
     a.beta = (float)beta;
     a.err = err;
@@ -861,7 +878,7 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     note_launch();
     k_tc_product<<<p->grid, kThreads, kSmemBytes, s>>>(a);
     LSQ_CHECK_LAUNCH();
-    if (upper == 1 && mirror) LSQ_TRY(mirror_lower4(g, rc, LSQ_F32, C, s));
+    // (a symmetric result's lower blocks are written by the kernel itself, see c_tm)
     return LSQ_OK;
 }
 
