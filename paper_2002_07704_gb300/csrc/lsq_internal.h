@@ -285,8 +285,6 @@ int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cud
 
 // Exact block triples of a product restricted to a triangle (upper: 0 all, 1 j >= i, 2 j <= i).
 int plan_count_triples(lsq_geom g, int ra, int rb, int rc, int upper, int64_t *out, cudaStream_t s);
-// Lower blocks of a symmetric 4 x 4 result from the upper ones (pattern rc).
-int mirror_lower4(lsq_geom g, int rc, int dtype, void *C, cudaStream_t s);
 // Loads the fixed scratch array of lsq_trace_static on the current device (noalloc.cu).
 int noalloc_prime();
 // Device error word of g (allocated and cleared on first use).

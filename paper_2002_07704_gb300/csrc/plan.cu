@@ -882,20 +882,6 @@ int plan_count_triples(lsq_geom g, int ra, int rb, int rc, int upper, int64_t *o
     return LSQ_OK;
 }
 
-int mirror_lower4(lsq_geom g, int rc, int dtype, void *C, cudaStream_t s) {
-    LSQ_TRY(ensure_tmap(g, rc, s));
-    const int64_t m = g->pats[rc].nnzb * 16;
-    if (m == 0) return LSQ_OK;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16));
-    note_launch();
-    if (dtype == LSQ_F64)
-        k_mirror_lower<double><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (double *)C);
-    else
-        k_mirror_lower<float><<<blocks, 256, 0, s>>>(g->pats[rc].nnzb, g->pats[rc].tmap.p, (float *)C);
-    LSQ_CHECK_LAUNCH();
-    return LSQ_OK;
-}
-
 __global__ void k_rows_of(int n, const int64_t *__restrict__ c_ptr, int64_t *__restrict__ c_row) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
