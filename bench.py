@@ -824,7 +824,7 @@ def run_ours(args):
                          "gathered_note": "64-byte float32 blocks copied from L2/HBM into shared memory per "
                                           "launch (split into hi/lo TF32 there); the other block slots of "
                                           "the tiles are zeros stored in shared memory",
-                         "bound_note": "gathering the operand blocks (scattered 64-byte float32 blocks through L2) "
+                         "bound_note": "gathering the operand blocks (scattered 128-byte lines through L2) "
                                        "bounds this kernel, not the tensor pipe",
                          "vs_fma": rms / tms},
             "roofline_fma": {"bound": "alu", "achieved": rflops / rms / 1e9, "peak": fp32_peak,
