@@ -818,12 +818,12 @@ def run_ours(args):
                          "traffic": traffic_tc,
                          "algorithmic_tflops": rflops / tms / 1e9,
                          "useful_fraction": tinfo["triples"] / max(tinfo["dense_triples"], 1),
-                         "gathered_gbs": 64.0 * tinfo["blocks_copied"] / tms / 1e6,
-                         "gathered_bytes": 64 * tinfo["blocks_copied"],
+                         "gathered_gbs": 128.0 * tinfo["blocks_copied"] / tms / 1e6,
+                         "gathered_bytes": 128 * tinfo["blocks_copied"],
                          "block_slots": tinfo["block_slots"],
-                         "gathered_note": "64-byte float32 blocks copied from L2/HBM into shared memory per "
-                                          "launch (split into hi/lo TF32 there); the other block slots of "
-                                          "the tiles are zeros stored in shared memory",
+                         "gathered_note": "128-byte split blocks copied from L2/HBM into shared memory per "
+                                          "launch; the other block slots of the tiles are zeros stored in "
+                                          "shared memory",
                          "bound_note": "gathering the operand blocks (scattered 128-byte lines through L2) "
                                        "bounds this kernel, not the tensor pipe",
                          "vs_fma": rms / tms},

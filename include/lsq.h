@@ -202,9 +202,9 @@ int lsq_measure_peak(int precision, double *tflops_host, void *stream);
  * lsq_block_matmul_tri), into info_host[6]: [0] the block triples of the computed blocks;
  * [1] the block triples the MMAs execute (16 j x 8 i x k-list per tile, zero blocks included;
  * each costs 4 x 128 tensor flops with the split operands); [2] the operand block slots a
- * launch fills in shared memory (a 128-byte hi/lo unit each); [3] the tiles; [5] the slots
- * filled by copying a block (64 float32 bytes from op(A) or op(B)^T; the others are zeros
- * stored in shared memory); [0..3] and [5] are -1 when no plan is held (the LNV path's timing chose the FMA
+ * launch fills in shared memory (128 bytes each); [3] the tiles; [5] the slots filled by
+ * copying a block (128 bytes from op(A) or op(B)^T; the others are zeros stored in shared
+ * memory); [0..3] and [5] are -1 when no plan is held (the LNV path's timing chose the FMA
  * kernel and dropped it); [4], for products the LNV path ran with LSQ_TF32X3, which kernel
  * the timing chose (-1 not timed, 0 FP32 FMA, 1 tensor cores).  Host only.
  * No counterpart in the paper.
