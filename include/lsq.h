@@ -178,18 +178,17 @@ int lsq_block_matmul_tri(lsq_geom g, int b, int precision,
 /*
  * With precision LSQ_TF32X3 and b = 4, lsq_block_matmul(_tri) runs the tensor-core product:
  * atoms i in groups of 8 and the atoms j of their rows of C in tiles of 16; per tile the
- * float32 blocks of op(B)^T and op(A) over the union of the group's rows of op(A) are
- * gathered into shared memory by 16-byte asynchronous copies (zeros stored for absent
- * blocks), split there into hi + lo TF32 values and contracted by tcgen05.mma (kind::tf32)
- * into float32 accumulators in tensor memory.  Operands are read in place when op(X) = X
- * and the array is 16-byte aligned; a transposed or unaligned operand is first transposed
- * or copied into scratch held by g (grown on demand).  The plan of the first call for a
- * (range_a, range_b, range_c, triangle) allocates and synchronises.  Limits: rows of at
- * most 65534 blocks and at most 2^31 - 1 blocks in C (LSQ_ERR_UNSUPPORTED).  The kernel
- * bounds every wait on its pipeline barriers (1 s; the environment variable
- * LSQ_TC_WAIT_NS, in ns, lowers it for tests of this path); if one expires it records an
- * error in g, drains its copies and MMAs, frees its tensor memory and returns early, and
- * lsq_device_status reports it.  Calls on different streams race on the scratch buffers.
+ * blocks of op(B)^T and op(A) over the union of the group's rows of op(A) are gathered into
+ * shared memory by bulk asynchronous copies and contracted by tcgen05.mma (kind::tf32) into
+ * a float32 accumulator in tensor memory.  op(A) and op(B)^T are first copied in split form
+ * (a 128-byte hi/lo unit per block) into buffers held by g and grown on demand; the plan of
+ * the first call for a (range_a, range_b, range_c, triangle) allocates and synchronises.
+ * Arrays need only float alignment.  Limits: rows of at most 65534 blocks and at most
+ * 2^31 - 1 blocks in C (LSQ_ERR_UNSUPPORTED).  The kernel bounds every wait on its
+ * pipeline barriers (1 s; the environment variable LSQ_TC_WAIT_NS, in ns, lowers it for
+ * tests of this path); if one expires it records an error in g, drains its copies and MMAs,
+ * frees its tensor memory and returns early, and lsq_device_status reports it.  Calls on
+ * different streams race on the split buffers.
  */
 
 /* Measured FMA rate of this GPU in TFLOP/s (2 flop per fused multiply-add): a loop of

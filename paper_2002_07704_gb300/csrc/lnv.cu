@@ -733,13 +733,25 @@ int energy_gradient(lsq_lnv c, const double *L, const double *S, double spin, in
         // kernel walks is SL on L+S's range rather than Q + Q^T on R3: G1 holds T1's upper
         // blocks transposed.
         void *Qs = c->QD.p;
-        LSQ_TRY(sym_sum_on(g, c->r3, b, prec, c->Q.p, Qs, s));
-        if (mat)
-            LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, c->SL.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
-        else
-            LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 1, c->LS.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
+        // With the tensor-core kernel chosen for a product (LSQ_TF32X3), its split operand copy
+        // is formed from Q + Q^T directly, and the split of SL is shared by T1 and T2.
+        const bool tc1 = mat && mmp(c, prec) == kMixedAuto && mixed_choice(g, c->r1, c->r3, c->rL, 3, 0.0) == 1;
+        const bool tc2 = mat && mmp(c, prec) == kMixedAuto && mixed_choice(g, c->r1, c->r3, c->rL, 2, 0.0) == 1;
+        if (tc1) {
+            LSQ_TRY(tc_block_matmul(g, c->r1, 0, (const float *)c->SL.p, c->r3, 1, (const float *)c->Q.p, c->rL,
+                                    (float *)c->G1.p, 1.0, 0.0, 2, false, nullptr, s, true, false));
+        } else {
+            LSQ_TRY(sym_sum_on(g, c->r3, b, prec, c->Q.p, Qs, s));
+            if (mat)
+                LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, c->SL.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
+            else
+                LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 1, c->LS.p, c->r3, 1, Qs, c->rL, c->G1.p, 1.0, 0.0, nullptr, s, 3));
+        }
         // T2 = SL.Q^T: op(B) = Q^T, read as rows of Q; op(A) = SL (materialised for 4 x 4 blocks)
-        if (mat)
+        if (tc2)
+            LSQ_TRY(tc_block_matmul(g, c->r1, 0, (const float *)c->SL.p, c->r3, 1, (const float *)c->Q.p, c->rL,
+                                    (float *)c->G2.p, 1.0, 0.0, 1, false, nullptr, s, false, tc1));
+        else if (mat)
             LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, c->SL.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
         else
             LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 1, c->LS.p, c->r3, 1, c->Q.p, c->rL, c->G2.p, 1.0, 0.0, nullptr, s, 2));
@@ -815,7 +827,12 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
     // Z = QD^T.P is symmetric, so it is formed as P^T.QD: the operand whose rows the kernel
     // walks (and stages in shared memory) is then P^T on L+S's range, not QD^T on R3
-    if (mat) {
+    if (mat && mmp(c, prec) == kMixedAuto && mixed_choice(g, c->r1, c->r3, c->rL, 1, 0.0) == 1) {
+        // on the tensor cores: the split copy of QD^T is read through the transpose map, so QD^T
+        // is not materialised
+        LSQ_TRY(tc_block_matmul(g, c->r1, 0, (const float *)PT, c->r3, 0, (const float *)c->QD.p, c->rL,
+                                (float *)Z, 1.0, 0.0, 1, true, nullptr, s));
+    } else if (mat) {
         LSQ_TRY(transpose_on(g, c->r3, b, prec, c->QD.p, QDT, s));
         LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, PT, c->r3, 1, QDT, c->rL, Z, 1.0, 0.0, nullptr, s, 1));
     } else {

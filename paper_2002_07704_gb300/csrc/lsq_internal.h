@@ -167,11 +167,17 @@ struct lsq_geom_s {
     std::map<std::tuple<int, int, int>, std::array<int, 4>> schedule_hints;
     // scratch for transposed operands of lsq_block_matmul (grown on demand)
     lsq::DevBuf<char> scratch_a, scratch_x;
-    // tensor-core plans keyed by (range_a, range_b, range_c + 1000 * triangle), and the device
-    // error word of the kernels with bounded waits (0: none)
+    // tensor-core plans keyed by (range_a, range_b, range_c + 1000 * triangle), the split
+    // (hi, lo) operand copies they read (grown on demand), and the device error word of the
+    // kernels with bounded waits (0: none)
     std::map<std::tuple<int, int, int>, lsq::TcPlan> tcplans;
     // the kernel each kMixedAuto product was timed to run on (same keys)
     std::map<std::tuple<int, int, int>, lsq::TcChoice> tc_choice;
+    lsq::DevBuf<char> tc_a, tc_x;
+    // what tc_a holds the split of (see tc_block_matmul's reuse_a)
+    const void *tc_a_src = nullptr;
+    int tc_a_range = -1;
+    bool tc_a_trans = false;
     lsq::DevBuf<int> dev_err;
     // workspace of lsq_hotelling_inverse (grown on demand)
     lsq::DevBuf<char> hot_ws;
@@ -284,11 +290,14 @@ int noalloc_prime();
 // Device error word of g (allocated and cleared on first use).
 int dev_err_ptr(lsq_geom g, int **out);
 // Tensor-core truncated 4 x 4 product in split TF32 (see tc.cu); float32 operands and result.
-// b_sym: op(B)^T = B + B^T (B on a symmetric pattern; tb ignored), formed in g's scratch.
+// b_sym: op(B) = B + B^T (B on a symmetric pattern; tb ignored), without forming the sum.
+// reuse_a: A (same array, range and flag) is unchanged since the previous call split it.
 int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, const float *B, int rc,
                     float *C, double alpha, double beta, int upper, bool mirror, int64_t *triples,
-                    cudaStream_t s, bool b_sym = false);
-
+                    cudaStream_t s, bool b_sym = false, bool reuse_a = false);
+// The kernel the kMixedAuto timing chose for this product (-1 not timed yet, 0 FP32 FMA, 1
+// tensor cores); sym and beta as for block_matmul.
+int mixed_choice(lsq_geom g, int ra, int rb, int rc, int sym, double beta);
 
 #ifdef __CUDACC__
 // Error-free float32 sum (Knuth's TwoSum): s = fl(a + b) and s + e = a + b exactly.

@@ -577,6 +577,12 @@ static int get_plan(lsq_geom g, int b, int dtype, int ra, int ta, int rb, int tb
     return LSQ_OK;
 }
 
+int mixed_choice(lsq_geom g, int ra, int rb, int rc, int sym, double beta) {
+    const int upper = sym == 3 ? 2 : (sym == 2 || (sym == 1 && beta == 0.0) ? 1 : 0);
+    auto ch = g->tc_choice.find(std::make_tuple(ra, rb, rc + 1000 * upper));
+    return ch == g->tc_choice.end() ? -1 : ch->second.choice;
+}
+
 int block_matmul(lsq_geom g, int b, int dtype, int ra, int ta, const void *A, int rb, int tb,
                  const void *B, int rc, void *C, double alpha, double beta, int64_t *triples,
                  cudaStream_t s, int sym) {

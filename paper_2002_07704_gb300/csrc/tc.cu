@@ -5,9 +5,9 @@
 // 4 x 4 blocks are contracted on the tensor cores (tcgen05.mma, kind::tf32, FP32
 // accumulation in tensor memory):
 //
-//  * Split TF32 operands.  Every float32 value v is used as hi = tf32(v) and
-//    lo = tf32(v - hi), so hi + lo carries v to 22 bits.  In shared memory a block is one
-//    128-byte unit: the 4 x 4 hi values (row-major), then the 4 x 4 lo values.
+//  * Split TF32 operands.  Every float32 value v is held as hi = tf32(v) and
+//    lo = tf32(v - hi), so hi + lo carries v to 22 bits.  A block is one 128-byte unit: the
+//    4 x 4 hi values (row-major), then the 4 x 4 lo values.
 //  * Tiles.  Atoms i are taken in groups of 8 (one diamond cell in cell-ordered systems).
 //    The atoms j of the group's rows of C are cut into tiles of 16, and each tile has one
 //    list of atoms k: the union of the group's rows of op(A), restricted to atoms that the
@@ -16,22 +16,20 @@
 //    (8 i x {hi, lo} x 4 rows r of A_ik), and one MMA takes K = 8 (two atoms k x 4).  The
 //    {hi, lo} x {hi, lo} cross terms land in separate rows and columns and are summed in the
 //    epilogue: one pass gives hi.hi + hi.lo + lo.hi + lo.lo.
-//  * Gathers.  The float32 blocks of a stage (16 k of the list for the 16 rows j and the
-//    8 rows i, 64 bytes each) are copied from op(A) and op(B)^T into a staging ring by 16-byte
-//    asynchronous copies (cp.async), four lanes per block; the lanes of a block a row does
-//    not hold store zeros instead (no L2 request).  Each copy warp owns four rows of every
-//    stage: it keeps four stages of its copies in flight and converts the oldest, once its
-//    copies have landed, into the split units of the ring the MMAs read.  The kernel is
-//    bound by the rate of these gathers, not by DRAM: scattered 64-byte blocks come in at
-//    about 1.45 times the block rate of 128-byte ones, so gathering the float32 values and
-//    splitting them in shared memory beats gathering split copies prepared in HBM.  The
-//    block indices a CTA gathers are laid out by the plan as one stream of stage records,
-//    read four stages ahead, so no copy waits on an index load.  (Bulk copies of runs of
-//    consecutive blocks were measured first: at the ~4 blocks a run averages, their request
-//    rate, not the bytes, bounded the kernel.)
-//  * Roles.  Six warps copy and convert, one thread issues the MMAs, four warps read the
-//    accumulator (tcgen05.ld) and write the blocks of C the plan keeps (and, for a
-//    symmetric result, their transposes in the lower triangle).  The tensor core's float32 additions truncate, which biases long sums, so each
+//  * Gathers.  The blocks of a stage (16 k of the list for the 16 rows j and the 8 rows i)
+//    are copied into shared memory by 16-byte asynchronous copies (cp.async), eight lanes
+//    per 128-byte block, so one warp instruction moves four whole cache lines; the lanes of
+//    a block a row does not hold store zeros instead (no L2 request), so every stage lands
+//    whole.  Each copying thread arrives on the stage's mbarrier twice: after its stores of
+//    zeros (with a proxy fence, as the MMAs read through the async proxy) and when its copies
+//    complete.  The block indices a CTA gathers are laid out by the plan as one stream of
+//    stage records, read four stages ahead, so no copy waits on an index load.  The kernel
+//    is bound by the rate of these gathers (about 10 TB/s of scattered 128-byte lines), not
+//    by DRAM.  (Bulk copies of runs of consecutive blocks were measured first: at the ~4
+//    blocks a run averages, their request rate, not the bytes, bounded the kernel.)
+//  * Roles.  Six warps issue the copies through a ring of stages, one thread issues the
+//    MMAs, four warps read the accumulator (tcgen05.ld) and write the blocks of C the plan
+//    keeps.  The tensor core's float32 additions truncate, which biases long sums, so each
 //    stage (8 MMAs) accumulates into a fresh accumulator of a ring of four in tensor memory
 //    and the epilogue adds the stages in float32 with rounding to nearest.  Every wait on an
 //    mbarrier is bounded: past the limit the kernel records an error code in a device word,
@@ -57,16 +55,11 @@ namespace {
 constexpr int kG = 8;                         // atoms i per group
 constexpr int kJT = 16;                       // atoms j per tile
 constexpr int kKS = 16;                       // atoms k per pipeline stage
-constexpr int kStages = 2;                    // stages of the split ring the MMAs read
-constexpr int kAhead = 4;                     // stages of float32 copies in flight per copy warp
-constexpr int kStg = kAhead + 1;              // stages of the float32 staging ring
+constexpr int kStages = 4;                    // stages in the ring
 constexpr int kUnit = 128;                    // bytes of a split block (hi 64, lo 64)
-constexpr int kBlk = 64;                      // bytes of a float32 4 x 4 block
 constexpr int kRows = kJT + kG;               // gathered rows per stage
 constexpr int kPanelX = kJT * kKS * kUnit;    // X rows of a stage (M side), 32 KB
 constexpr int kStageBytes = kRows * kKS * kUnit;  // 48 KB
-constexpr int kStgBytes = kRows * kKS * kBlk;     // 24 KB
-constexpr int kStgWarp = 4 * kKS * kBlk;          // 4 KB: one copy warp's rows of a staging stage
 constexpr int kN = 8 * kG;                    // accumulator columns of a tile
 constexpr int kPartials = 4;                  // ring of per-stage accumulators in tensor memory
 constexpr int kTmemCols = kPartials * kN;
@@ -78,12 +71,11 @@ constexpr uint16_t kAbsent = 0xffff;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait (1 s)
 
 // Index of (row r, block kk) in a stage record.  Rows come in six groups of four, one per
-// copying warp; lane l of warp w loads entries 64 w + 2 l and 64 w + 2 l + 1.  Copy
-// instruction q (0..7) of the warp moves its local blocks b = 8 q + l / 4 (row 4 w + b / 16,
-// block b % 16), four lanes per 64-byte block; lane l finds the index of its block in lane
-// 8 (q / 2) + l / 4, entry q % 2.
+// copying warp; lane l of warp w loads entries 64 w + 2 l and 64 w + 2 l + 1 and, for copy
+// instruction q (row 4 w + q / 4, block 4 (q % 4) + l / 8), finds its block index in lane
+// 8 (l / 8) + q / 2, entry q % 2.
 __host__ __device__ constexpr int rec_index(int r, int kk) {
-    return 64 * (r >> 2) + 16 * (r & 3) + 2 * (kk & 7) + (kk >> 3);
+    return 64 * (r >> 2) + 16 * (kk & 3) + 2 * ((4 * (r & 3) + (kk >> 2)) >> 1) + ((4 * (r & 3) + (kk >> 2)) & 1);
 }
 
 __device__ __forceinline__ bool tri_skip_tc(int tri, int i, int j) {
@@ -134,23 +126,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// Arrives on the mbarrier once every cp.async this thread issued before has completed
+// (the arrival counts against the count the barrier was initialised with).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
     asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Waits until at most kAhead of this thread's most recent copy groups are still in flight.
-__device__ __forceinline__ void cp_async_wait_ahead() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
-}
-__device__ __forceinline__ float4 ld_shared_f4(uint32_t a) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
-                 : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_shared_f4(uint32_t a, float4 v) {
-    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -202,6 +184,26 @@ __device__ __forceinline__ float tf32_round(float v) {
     return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
 }
 
+// Unit p of out: hi and lo of block p of X (MODE 0), of X^T read through the transpose map tm
+// (MODE 1; block (i, j) of X^T is (X_ji)^T), or of X + X^T (MODE 2, X on a symmetric pattern;
+// the sum rounded once in float32, as a separate symmetric sum would).  v - hi is exact in
+// float32.
+template <int MODE>
+__global__ void k_split_tf32(int64_t nnzb, const int64_t *__restrict__ tm, const float *__restrict__ X,
+                             float *__restrict__ out) {
+    const int64_t m = nnzb * 16;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e >> 4;
+        const int rc = (int)(e & 15);
+        const float v = MODE == 0   ? X[e]
+                        : MODE == 1 ? X[16 * tm[p] + (rc & 3) * 4 + (rc >> 2)]
+                                    : X[e] + X[16 * tm[p] + (rc & 3) * 4 + (rc >> 2)];
+        const float hi = tf32_round(v);
+        const float lo = tf32_round(v - hi);
+        out[32 * p + rc] = hi;
+        out[32 * p + 16 + rc] = lo;
+    }
+}
 
 // ---- plan ------------------------------------------------------------------------------
 // Number of entries of pos[0, m) that name a block (>= 0).
@@ -441,7 +443,7 @@ struct TcArgs {
     const int32_t *tile_nk, *cpos, *cta_stages;
     const int64_t *tile_posoff;
     const int32_t *pos;
-    const float *As, *Xs;  // float32 blocks of op(A) and of X = op(B)^T, rows contiguous, 16-byte aligned
+    const char *As, *Xs;  // split units of op(A) and of X = op(B)^T
     float *C;
     const int64_t *c_tm;  // transpose map of C's pattern: also write C_ji = C_ij^T (or null)
     float alpha, beta;
@@ -451,8 +453,7 @@ struct TcArgs {
 
 __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    // [split ring: kStages x 48 KB][float32 staging ring: kStg x 24 KB][barriers, TMEM slot, flag]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes + kStg * kStgBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
     // bars: full[kStages], empty[kStages], tfull[kPartials], tempty[kPartials], drain[1]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 2 * kPartials + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -467,8 +468,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            // one arrival per copying thread, after it has written its part of the stage
-            mbar_init(full(s), 32 * kCopyWarps);
+            // per copying thread and stage: one arrival after its stores of zeros, one when its
+            // copies have landed
+            mbar_init(full(s), 2 * 32 * kCopyWarps);
             mbar_init(empty(s), 1);
         }
         for (int b = 0; b < kPartials; ++b) {
@@ -491,77 +493,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp < kCopyWarps) {
-        // ---- copies.  Warp w owns rows 4w .. 4w + 3 of every stage (rows 0-15: atoms j of the
-        // tile, rows of X; 16-23: atoms i of the group, rows of op(A)).  It gathers their 64
-        // float32 blocks of stage st into its part of staging slot st % kStg (instruction q:
-        // local blocks b = 8 q + l / 4, 16 bytes per lane; zeros stored for absent blocks), then
-        // converts stage st - kAhead, whose copies have landed, into the split ring: hi and lo
-        // TF32 of each value, written where the MMAs read them.  Only this warp touches its part
-        // of the staging ring, so the staging needs no barrier; the split ring is handed to the
-        // MMAs by one arrival per thread on its full barrier.
-        const float *arr = warp < 4 ? p.Xs : p.As;
+        // ---- copies.  Warp w fills rows 4w .. 4w + 3 of every stage (rows 0-15: atoms j of the
+        // tile, rows of X; 16-23: atoms i of the group, rows of op(A)).  One instruction moves
+        // four blocks: lane l copies 16-byte chunk l % 8 of block 4 (q % 4) + l / 8 of row
+        // 4 w + q / 4 (q = 0..15).  The CTA's stage records are read four stages ahead.
+        const char *arr = warp < 4 ? p.Xs : p.As;
+        const int sub = lane >> 3;
         const int S = p.cta_stages[blockIdx.x];
         const int32_t *rec = p.pos + p.tile_posoff[blockIdx.x] + 64 * warp + 2 * lane;
         auto ld = [&](int st) -> int2 {
             return st < S ? *reinterpret_cast<const int2 *>(rec + (int64_t)kRec * st) : make_int2(-1, -1);
         };
         int2 p0 = ld(0), p1 = ld(1), p2 = ld(2), p3 = ld(3);
-        const uint32_t stg0 = sbase + (uint32_t)(kStages * kStageBytes) + (uint32_t)(warp * kStgWarp);
-        const int c4 = lane & 3;  // 16-byte chunk of a copied block: row c4 of the 4 x 4 block
-        for (int st = 0; st < S + kAhead; ++st) {
-            if (st < S) {
-                const int2 p4 = ld(st + 4);
-                const uint32_t dst0 = stg0 + (uint32_t)((st % kStg) * kStgBytes) + 16u * (uint32_t)c4;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int v = __shfl_sync(0xffffffffu, (q & 1) ? p0.y : p0.x, 8 * (q >> 1) + (lane >> 2));
-                    const uint32_t dst = dst0 + (uint32_t)((8 * q + (lane >> 2)) * kBlk);
-                    if (v < 0)
-                        st_shared_zero16(dst);  // a block the row does not hold
-                    else
-                        cp_async16(dst, arr + 16 * (int64_t)v + 4 * c4);
-                }
-                p0 = p1;
-                p1 = p2;
-                p2 = p3;
-                p3 = p4;
-            }
-            cp_async_commit();
-            if (st < kAhead) continue;
-            const int c = st - kAhead;  // the stage to convert
-            cp_async_wait_ahead();      // this thread's copies of stage c have landed
-            __syncwarp();               // and those of the warp's other lanes (and their zeros)
-            const int slot = c % kStages;
-            bool ok = mbar_wait(empty(slot), ((uint32_t)(c / kStages) & 1u) ^ 1u, abort_flag, p.err, 1, p.wait_ns);
+        const uint32_t dlane = (uint32_t)(4 * warp * kKS * kUnit + 16 * (lane & 7));
+        for (int st = 0; st < S; ++st) {
+            const int2 p4 = ld(st + 4);
+            const int slot = st % kStages;
+            const uint32_t ph = (uint32_t)(st / kStages) & 1u;
+            bool ok = mbar_wait(empty(slot), ph ^ 1u, abort_flag, p.err, 1, p.wait_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
-            // lane l writes 16-byte row l % 8 of unit l / 8 of the instruction's four: hi rows 0-3,
-            // lo rows 4-7 of the block (so every store instruction fills 512 contiguous bytes)
-            const int rr = lane & 7;
-            const uint32_t src0 = stg0 + (uint32_t)((c % kStg) * kStgBytes) + 16u * (uint32_t)(rr & 3);
-            const uint32_t out0 = sbase + (uint32_t)slot * kStageBytes + (uint32_t)(4 * warp * kKS * kUnit) +
-                                  16u * (uint32_t)rr;
+            const uint32_t dst0 = sbase + (uint32_t)slot * kStageBytes + dlane;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const int b = 4 * q + (lane >> 3);  // local block: row 4 w + b / 16, block b % 16
-                const float4 x = ld_shared_f4(src0 + (uint32_t)(b * kBlk));
-                float4 y;
-                y.x = tf32_round(x.x);
-                y.y = tf32_round(x.y);
-                y.z = tf32_round(x.z);
-                y.w = tf32_round(x.w);
-                if (rr >= 4) {
-                    y.x = tf32_round(x.x - y.x);
-                    y.y = tf32_round(x.y - y.y);
-                    y.z = tf32_round(x.z - y.z);
-                    y.w = tf32_round(x.w - y.w);
-                }
-                st_shared_f4(out0 + (uint32_t)((b >> 4) * (kKS * kUnit) + (b & 15) * kUnit), y);
+                const int v = __shfl_sync(0xffffffffu, (q & 1) ? p0.y : p0.x, 8 * sub + (q >> 1));
+                const uint32_t dst = dst0 + (uint32_t)((q >> 2) * (kKS * kUnit) + (4 * (q & 3) + sub) * kUnit);
+                if (v < 0)
+                    st_shared_zero16(dst);  // a block the row does not hold
+                else
+                    cp_async16(dst, arr + (int64_t)kUnit * v + 16 * (lane & 7));
             }
-            // the split values are generic-proxy stores that the MMAs read through the async proxy
+            // the zeros are generic-proxy stores that the MMAs read through the async proxy
             fence_proxy_async();
             mbar_arrive(full(slot));
-            __syncwarp();  // every lane has read staging slot c % kStg before it is refilled
+            cp_async_arrive(full(slot));
+            p0 = p1;
+            p1 = p2;
+            p2 = p3;
+            p3 = p4;
         }
         // every copy of this thread has landed before the CTA exits
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -688,9 +657,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_product(TcArgs p) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + (size_t)kStg * kStgBytes + 512;
-static_assert(kSmemBytes <= 232448, "shared memory of one CTA");
-static_assert((2 * kStages + 2 * kPartials + 1) * 8 + 8 <= 512, "barriers, TMEM slot and flag");
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 256;
 
 }  // namespace
 
@@ -830,6 +797,24 @@ int tc_plan_get(lsq_geom g, int ra, int rb, int rc, int upper, TcPlan **out, cud
 
 namespace {
 
+// mode: 0 X, 1 X^T, 2 X + X^T (see k_split_tf32).
+int split_operand(lsq_geom g, int r, int mode, const float *X, DevBuf<char> &buf, cudaStream_t s) {
+    const int64_t nnzb = g->pats[r].nnzb;
+    const size_t need = (size_t)kUnit * (size_t)std::max<int64_t>(nnzb, 1);
+    if (buf.n < need) LSQ_TRY(buf.alloc(need));
+    if (nnzb == 0) return LSQ_OK;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nnzb * 16 + 255) / 256, (int64_t)g->num_sms * 16));
+    float *out = reinterpret_cast<float *>(buf.p);
+    note_launch();
+    if (mode == 1)
+        k_split_tf32<1><<<blocks, 256, 0, s>>>(nnzb, g->pats[r].tmap.p, X, out);
+    else if (mode == 2)
+        k_split_tf32<2><<<blocks, 256, 0, s>>>(nnzb, g->pats[r].tmap.p, X, out);
+    else
+        k_split_tf32<0><<<blocks, 256, 0, s>>>(nnzb, nullptr, X, out);
+    LSQ_CHECK_LAUNCH();
+    return LSQ_OK;
+}
 
 }  // namespace
 
@@ -844,7 +829,7 @@ int dev_err_ptr(lsq_geom g, int **out) {
 
 int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, const float *B, int rc, float *C,
                     double alpha, double beta, int upper, bool mirror, int64_t *triples, cudaStream_t s,
-                    bool b_sym) {
+                    bool b_sym, bool reuse_a) {
     LSQ_TRY(ensure_tmap(g, ra, s));
     LSQ_TRY(ensure_tmap(g, rb, s));
     TcPlan *p = nullptr;
@@ -853,36 +838,18 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     if (g->n == 0 || g->pats[rc].nnzb == 0 || p->ntiles == 0) return LSQ_OK;
     if (!p->pos.p || !p->cpos.p || !p->tile_nk.p || !p->tile_posoff.p || !p->cta_stages.p)
         return set_error(LSQ_ERR_CUDA, "tensor-core plan without its records");
-    // op(A) and X = op(B)^T as float32 blocks with rows contiguous and 16-byte aligned (the
-    // kernel gathers them by 16-byte copies): transposed or symmetrised into scratch held by g
-    // when needed (B + B^T when b_sym), copied there when not aligned
-    const auto aligned = [](const void *q) { return reinterpret_cast<uintptr_t>(q) % 16 == 0; };
-    auto scratch = [&](DevBuf<char> &buf, int r) -> float * {
-        const size_t need = (size_t)kBlk * (size_t)std::max<int64_t>(g->pats[r].nnzb, 1);
-        if (buf.n < need && buf.alloc(need) != LSQ_OK) return nullptr;
-        return reinterpret_cast<float *>(buf.p);
-    };
-    const float *Aop = A, *X = B;
-    if (ta || !aligned(A)) {
-        float *t = scratch(g->scratch_a, ra);
-        if (!t) return LSQ_ERR_OOM;
-        if (ta)
-            LSQ_TRY(transpose_on(g, ra, 4, LSQ_F32, A, t, s));
-        else
-            LSQ_CUDA_TRY(cudaMemcpyAsync(t, A, (size_t)kBlk * g->pats[ra].nnzb, cudaMemcpyDeviceToDevice, s));
-        Aop = t;
+    // op(A) and X = op(B)^T (B's rows when trans_b, else B read through its transpose map; B +
+    // B^T when b_sym) in split form, in buffers held by g.  The split of A is kept when the
+    // caller says A is unchanged since the previous split of the same array.
+    const bool keep = reuse_a && g->tc_a_src == A && g->tc_a_range == ra && g->tc_a_trans == (ta != 0);
+    if (!keep) {
+        g->tc_a_src = nullptr;
+        LSQ_TRY(split_operand(g, ra, ta != 0 ? 1 : 0, A, g->tc_a, s));
+        g->tc_a_src = A;
+        g->tc_a_range = ra;
+        g->tc_a_trans = ta != 0;
     }
-    if (b_sym || !tb || !aligned(B)) {
-        float *t = scratch(g->scratch_x, rb);
-        if (!t) return LSQ_ERR_OOM;
-        if (b_sym)
-            LSQ_TRY(sym_sum_on(g, rb, 4, LSQ_F32, B, t, s));
-        else if (!tb)
-            LSQ_TRY(transpose_on(g, rb, 4, LSQ_F32, B, t, s));
-        else
-            LSQ_CUDA_TRY(cudaMemcpyAsync(t, B, (size_t)kBlk * g->pats[rb].nnzb, cudaMemcpyDeviceToDevice, s));
-        X = t;
-    }
+    LSQ_TRY(split_operand(g, rb, b_sym ? 2 : (tb == 0 ? 1 : 0), B, g->tc_x, s));
     int *err = nullptr;
     LSQ_TRY(dev_err_ptr(g, &err));
     TcArgs a;
@@ -892,8 +859,8 @@ int tc_block_matmul(lsq_geom g, int ra, int ta, const float *A, int rb, int tb, 
     a.tile_posoff = p->tile_posoff.p;
     a.cta_stages = p->cta_stages.p;
     a.pos = p->pos.p;
-    a.As = Aop;
-    a.Xs = X;
+    a.As = g->tc_a.p;
+    a.Xs = g->tc_x.p;
     a.C = C;
     a.c_tm = nullptr;
     if (upper == 1 && mirror) {

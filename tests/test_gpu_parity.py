@@ -448,9 +448,11 @@ def test_lnv_canonical_matches_oracle_trajectory(prec):
 
 def test_lnv_tf32x3_all_products_on_tensor_cores(monkeypatch):
     """Every 4 x 4 product of the mixed step on the tensor cores (LSQ_TC_CHOICE=all=1 fixes the
-    choice instead of the timing): Omega within 1e-6 Ha/atom and G within 2e-5 of max abs G of
-    the oracle at an intermediate L (216 atoms), and the minimum (float64 refinement and final
-    Omega) within 1e-6 Ha/atom of the oracle's."""
+    choice instead of the timing), which also takes the step's fused tensor-core forms: the
+    split copy of Q + Q^T formed from Q, SL's split shared by the two gradient products, and
+    QD^T read through its transpose map.  Omega within 1e-6 Ha/atom and G within 2e-5 of max
+    abs G of the oracle at an intermediate L (216 atoms), and the minimum (float64 refinement
+    and final Omega) within 1e-6 Ha/atom of the oracle's."""
     monkeypatch.setenv("LSQ_TC_CHOICE", "all=1")
     g, ctx, ref, Hb, Sb = _lnv_setup(3, 0.05, config_seed(0), 8.0)
     n = g.n_atoms
