@@ -437,6 +437,14 @@ struct lsq_lnv_s {
     DevBuf<double> b_slots, b_rowsum, b_mu, b_gg_prev, b_beta, b_alpha, b_omega, b_dom;
     DevBuf<int> b_status, b_frozen, b_reset, b_iters, b_natoms, b_step;
     DevBuf<int64_t> b_off;
+    // second stream of the line search (F = P.D beside QD = H'.P) and its two events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    ~lsq_lnv_s() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 
 static int64_t nvals(lsq_lnv c, int r) { return c->g->pats[r].nnzb * c->b * c->b; }
@@ -563,6 +571,10 @@ extern "C" int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double 
         return fail(rc);
     if ((rc = get_posmap(g, c->rH, c->rS, 0, &c->pos_s_in_h, 0))) return fail(rc);
     if ((rc = ensure_tmap(g, c->rL, 0))) return fail(rc);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(set_error(LSQ_ERR_CUDA, "stream or event creation failed"));
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(set_error(LSQ_ERR_CUDA, "sync failed"));
     *out = c;
     return LSQ_OK;
@@ -818,13 +830,30 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
     const bool mat = c->b == 4;  // see energy_gradient
     LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
+    // F = P.D and QD = H'.P both need only P: outside stream capture F runs on the context's
+    // second stream beside QD, so the two kernels can share the SMs (the tensor-core kernel
+    // leaves most warp slots idle).  The transpose maps both may build are built here first.
+    const bool fork = !seg && c->side;
+    cudaStream_t sf = s;
+    if (fork) {
+        LSQ_TRY(ensure_tmap(g, c->r1, s));
+        LSQ_TRY(ensure_tmap(g, c->rL, s));
+        LSQ_TRY(ensure_tmap(g, c->r3, s));
+        LSQ_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+        LSQ_CUDA_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        sf = c->side;
+    }
+    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, sf, 1));
     if (mat) {
         LSQ_TRY(transpose_on(g, c->r1, b, prec, P, PT, s));
         LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rH, 0, o.Hp, c->r1, 1, PT, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
     } else {
         LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rH, 0, o.Hp, c->r1, 0, P, c->r3, c->QD.p, 1.0, 0.0, nullptr, s));
     }
-    LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->r1, 0, P, c->rL, 1, D, c->r3, F, 1.0, 0.0, nullptr, s, 1));
+    if (fork) {
+        LSQ_CUDA_TRY(cudaEventRecord(c->ev_join, sf));
+        LSQ_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+    }
     // Z = QD^T.P is symmetric, so it is formed as P^T.QD: the operand whose rows the kernel
     // walks (and stages in shared memory) is then P^T on L+S's range, not QD^T on R3
     if (mat && mmp(c, prec) == kMixedAuto && mixed_choice(g, c->r1, c->r3, c->rL, 1, 0.0) == 1) {
