@@ -832,8 +832,11 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
     // F = P.D and QD = H'.P both need only P: outside stream capture F runs on the context's
     // second stream beside QD, so the two kernels can share the SMs (the tensor-core kernel
-    // leaves most warp slots idle).  The transpose maps both may build are built here first.
-    const bool fork = !seg && c->side;
+    // leaves most warp slots idle).  Two tensor-core products would share g's split buffers,
+    // so this happens only when QD is known to run on the FMA kernels.  The transpose maps
+    // both may build are built here first.
+    const bool qd_fma = mmp(c, prec) != kMixedAuto || mixed_choice(g, c->rH, c->r1, c->r3, 0, 0.0) == 0;
+    const bool fork = !seg && c->side && qd_fma;
     cudaStream_t sf = s;
     if (fork) {
         LSQ_TRY(ensure_tmap(g, c->r1, s));
