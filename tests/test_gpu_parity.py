@@ -446,14 +446,17 @@ def test_lnv_canonical_matches_oracle_trajectory(prec):
         assert abs(rep["ne"] - n0) <= 1e-5 * n0  # N_e held at the start of the last step
 
 
-def test_lnv_tf32x3_all_products_on_tensor_cores(monkeypatch):
-    """Every 4 x 4 product of the mixed step on the tensor cores (LSQ_TC_CHOICE=all=1 fixes the
-    choice instead of the timing), which also takes the step's fused tensor-core forms: the
-    split copy of Q + Q^T formed from Q, SL's split shared by the two gradient products, and
-    QD^T read through its transpose map.  Omega within 1e-6 Ha/atom and G within 2e-5 of max
-    abs G of the oracle at an intermediate L (216 atoms), and the minimum (float64 refinement
-    and final Omega) within 1e-6 Ha/atom of the oracle's."""
-    monkeypatch.setenv("LSQ_TC_CHOICE", "all=1")
+@pytest.mark.parametrize("setting", ["all=1", "3:2:5:1=1,all=0"])
+def test_lnv_tf32x3_all_products_on_tensor_cores(monkeypatch, setting):
+    """Kernel choices fixed by LSQ_TC_CHOICE instead of the timing.  "all=1": every 4 x 4
+    product of the mixed step on the tensor cores, which also takes the step's fused
+    tensor-core forms (the split copy of Q + Q^T formed from Q, SL's split shared by the two
+    gradient products, QD^T read through its transpose map).  "3:2:5:1=1,all=0": only
+    F = P.D on the tensor cores, run on the context's second stream beside QD = H'.P on the
+    FMA kernels.  Omega within 1e-6 Ha/atom and G within 2e-5 of max abs G of the oracle at an
+    intermediate L (216 atoms), and the minimum (float64 refinement and final Omega) within
+    1e-6 Ha/atom of the oracle's."""
+    monkeypatch.setenv("LSQ_TC_CHOICE", setting)
     g, ctx, ref, Hb, Sb = _lnv_setup(3, 0.05, config_seed(0), 8.0)
     n = g.n_atoms
     L0 = OL.onsite_inverse_half(Sb, ref.pat_L)
@@ -463,7 +466,7 @@ def test_lnv_tf32x3_all_products_on_tensor_cores(monkeypatch):
         om, _ = ctx.energy_gradient(cuda(L1.val), cuda(Sb.val), cuda(Hb.val), MU, G=G, precision=lsq.TF32X3)
     g.device_status()
     for ra, rb, rc, tri in ((3, 5, 2, 3), (3, 5, 2, 2), (2, 0, 3, 0)):
-        assert g.product_plan_info(ra, rb, rc, tri)["auto_choice"] == 1
+        assert g.product_plan_info(ra, rb, rc, tri)["auto_choice"] == (1 if setting == "all=1" else 0)
     om_ref, _ = ref.energy(L1)
     assert abs(om - om_ref) / lsq.HARTREE_EV / n < 1e-6
     Gr = ref.gradient(L1)
