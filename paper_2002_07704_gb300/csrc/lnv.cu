@@ -830,13 +830,15 @@ int line_coeffs(lsq_lnv c, const double *L, const double *S, double spin, int pr
     void *P = c->LS.p, *PT = c->SL.p, *F = c->LSL.p, *QDT = c->QT.p, *Z = c->G2.p;
     const bool mat = c->b == 4;  // see energy_gradient
     LSQ_TRY(block_matmul(g, b, mmp(c, prec), c->rL, 0, D, c->rS, 1, o.S, c->r1, P, 1.0, 0.0, nullptr, s));
-    // F = P.D and QD = H'.P both need only P: outside stream capture F runs on the context's
-    // second stream beside QD, so the two kernels can share the SMs (the tensor-core kernel
-    // leaves most warp slots idle).  Two tensor-core products would share g's split buffers,
-    // so this happens only when QD is known to run on the FMA kernels.  The transpose maps
-    // both may build are built here first.
-    const bool qd_fma = mmp(c, prec) != kMixedAuto || mixed_choice(g, c->rH, c->r1, c->r3, 0, 0.0) == 0;
-    const bool fork = !seg && c->side && qd_fma;
+    // F = P.D and QD = H'.P both need only P: outside stream capture, when both run on the FMA
+    // kernels, F runs on the context's second stream beside QD so that the two share the SMs
+    // (measured: the float32 step 22.15 -> 21.78 ms at 4096 atoms).  With F on the tensor
+    // cores the overlap was slower (17.7 -> 18.1 ms), and two tensor-core products would share
+    // g's split buffers, so then the products run in turn.  The transpose maps both may build
+    // are built here first.
+    const bool fma_both = mmp(c, prec) != kMixedAuto || (mixed_choice(g, c->rH, c->r1, c->r3, 0, 0.0) == 0 &&
+                                                         mixed_choice(g, c->r1, c->rL, c->r3, 1, 0.0) == 0);
+    const bool fork = !seg && c->side && fma_both;
     cudaStream_t sf = s;
     if (fork) {
         LSQ_TRY(ensure_tmap(g, c->r1, s));

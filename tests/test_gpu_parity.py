@@ -452,8 +452,7 @@ def test_lnv_tf32x3_all_products_on_tensor_cores(monkeypatch, setting):
     product of the mixed step on the tensor cores, which also takes the step's fused
     tensor-core forms (the split copy of Q + Q^T formed from Q, SL's split shared by the two
     gradient products, QD^T read through its transpose map).  "3:2:5:1=1,all=0": only
-    F = P.D on the tensor cores, run on the context's second stream beside QD = H'.P on the
-    FMA kernels.  Omega within 1e-6 Ha/atom and G within 2e-5 of max abs G of the oracle at an
+    F = P.D on the tensor cores, every other product on the FMA kernels.  Omega within 1e-6 Ha/atom and G within 2e-5 of max abs G of the oracle at an
     intermediate L (216 atoms), and the minimum (float64 refinement and final Omega) within
     1e-6 Ha/atom of the oracle's."""
     monkeypatch.setenv("LSQ_TC_CHOICE", setting)
