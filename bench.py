@@ -1013,32 +1013,40 @@ def run_sizes(args):
         ctx = lsq.Lnv(geom, B, R_S, R_H, R_L)
         L0 = torch.zeros((geom.nnzb(2), B, B), dtype=torch.float64, device="cuda")
         ctx.init_L(Sd, L0)
-        L = L0.clone()
-        ctx.minimise(L, Sd, Hd, MU, max_iter=args.warmup, precision=lsq.F32, refine_iter=0, final_eval=False)
-        L = L0.clone()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        rep = ctx.minimise(L, Sd, Hd, MU, max_iter=args.steps, precision=lsq.F32, refine_iter=0,
-                           final_eval=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        done = max(int(rep["iterations"]), 1)
-        ms = e0.elapsed_time(e1) / done
+
+        def timed(prec):
+            L = L0.clone()
+            ctx.minimise(L, Sd, Hd, MU, max_iter=max(args.warmup, 2), precision=prec, refine_iter=0,
+                         final_eval=False)
+            L = L0.clone()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rep = ctx.minimise(L, Sd, Hd, MU, max_iter=args.steps, precision=prec, refine_iter=0,
+                               final_eval=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            done = max(int(rep["iterations"]), 1)
+            return e0.elapsed_time(e1) / done, done
+
+        ms, done = timed(lsq.F32)
+        ms_tc, _ = timed(lsq.TF32X3)
         free1, _ = torch.cuda.mem_get_info()
         n = geom.n_atoms
         out.append({"atoms": n, "cells": nc, "steps": done, "ms_per_step": ms,
                     "us_per_atom_step": ms * 1e3 / n,
+                    "tf32x3": {"ms_per_step": ms_tc, "us_per_atom_step": ms_tc * 1e3 / n},
                     "nnzb": {"S": geom.nnzb(0), "L": geom.nnzb(2), "LSL": geom.nnzb(5)},
                     "device_gb": (free0 - free1) / 1e9})
-        print("sizes: %d atoms, %.3f ms/step, %.3f us/atom-step, %.1f GB" %
-              (n, ms, ms * 1e3 / n, (free0 - free1) / 1e9), file=sys.stderr)
+        print("sizes: %d atoms, F32 %.3f ms/step (%.3f us/atom-step), TF32X3 %.3f ms/step (%.3f), %.1f GB" %
+              (n, ms, ms * 1e3 / n, ms_tc, ms_tc * 1e3 / n, (free0 - free1) / 1e9), file=sys.stderr)
         ctx.close()
         geom.close()
-        del ctx, geom, L, L0, Hd, Sd
+        del ctx, geom, L0, Hd, Sd
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": "mixed-precision LNV ms/step against atoms (O(N))", "unit": "ms/step",
+    print(json.dumps({"metric": "mixed-precision LNV ms/step against atoms (O(N)); ms_per_step is float32 FMA "
+                                "products, tf32x3 the configuration's mode", "unit": "ms/step",
                       "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
                       "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "Si diamond n x n x n cells, sigma 0.05 A, R_S=R_H=6.6 A, "
