@@ -63,23 +63,25 @@ def batch_workload(n_sys=48, n_min=2, n_max=7):
 
 
 def diamond_si_positions(n, sigma, seed, a=A_SI):
-    """n x n x n conventional cells of diamond Si with Gaussian displacements.
+    """n x n x n conventional cells of diamond Si with Gaussian displacements;
+    n = (nx, ny, nz) gives an orthorhombic box of nx x ny x nz cells.
 
-    Returns (pos [8 n^3, 3] float64 wrapped into [0, L), cell [3] float64).
+    Returns (pos [8 nx ny nz, 3] float64 wrapped into [0, L), cell [3] float64).
     Atoms are ordered cell by cell (ix slowest, then iy, iz) and within a
     cell by the 8 basis sites, so consecutive indices are spatially close.
     """
-    idx = np.arange(n)
-    cells = np.stack(np.meshgrid(idx, idx, idx, indexing="ij"), axis=-1).reshape(-1, 3)
+    shape = (int(n),) * 3 if np.isscalar(n) else tuple(int(v) for v in n)
+    axes = [np.arange(m) for m in shape]
+    cells = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 3)
     frac = (cells[:, None, :] + _BASIS[None, :, :]).reshape(-1, 3)
-    L = n * a
+    L = np.array(shape, dtype=np.float64) * a
     pos = frac * a
     rng = np.random.default_rng(seed)
     pos = pos + rng.normal(0.0, sigma, size=pos.shape)
     pos = np.mod(pos, L)
-    pos[pos >= L] -= L
+    pos = np.where(pos >= L, pos - L, pos)
     pos[pos < 0.0] = 0.0
-    cell = np.array([L, L, L], dtype=np.float64)
+    cell = np.ascontiguousarray(L)
     return np.ascontiguousarray(pos, dtype=np.float64), cell
 
 
