@@ -726,22 +726,32 @@ def run_ours(args):
     Sh = Sd.cpu().pin_memory()
     Hh = Hd.cpu().pin_memory()
     Lout = torch.empty_like(Lh).pin_memory()
-    barrier()
-    t0 = time.perf_counter()
-    Ldev = Lh.to("cuda", non_blocking=True)
-    Sdev = Sh.to("cuda", non_blocking=True)
-    Hdev = Hh.to("cuda", non_blocking=True)
-    rep_e2e = ctx.minimise(Ldev, Sdev, Hdev, MU, max_iter=args.steps, precision=lsq.TF32X3,
-                           refine_iter=0, final_eval=True)
-    Lout.copy_(Ldev, non_blocking=True)
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+
+    def run_e2e(final_eval):
+        barrier()
+        t0 = time.perf_counter()
+        Ldev = Lh.to("cuda", non_blocking=True)
+        Sdev = Sh.to("cuda", non_blocking=True)
+        Hdev = Hh.to("cuda", non_blocking=True)
+        rep_ = ctx.minimise(Ldev, Sdev, Hdev, MU, max_iter=args.steps, precision=lsq.TF32X3,
+                            refine_iter=0, final_eval=final_eval)
+        Lout.copy_(Ldev, non_blocking=True)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, rep_
+
+    # the same call the device-timed value makes, with the copies in and out and the report
+    t_e2e, rep_e2e = run_e2e(False)
     e2e = {"value": world * args.steps / t_e2e, "unit": "steps/s",
            "h2d_bytes_per_step": int((Lh.numel() + Sh.numel() + Hh.numel()) * 8 / args.steps),
            "d2h_bytes_per_step": int(Lout.numel() * 8 / args.steps),
-           "definition": ("one lnv_minimise call of %d mixed steps from pinned host L, S, H, "
-                          "with the float64 evaluation of the result and the copy of L back"
+           "omega_ev": rep_e2e["omega_ev"],
+           "definition": ("one lnv_minimise call of %d mixed steps from pinned host L, S, H (the call "
+                          "the device-timed value makes), with the copy of L back and the report"
                           % args.steps)}
+    # the same with the float64 evaluation of Omega and N_e at the result
+    t_e2e64, rep_e2e64 = run_e2e(True)
+    e2e_fp64_eval = {"value": world * args.steps / t_e2e64, "unit": "steps/s", "omega_ev": rep_e2e64["omega_ev"],
+                     "definition": "as e2e, plus the float64 evaluation of Omega and N_e at the result"}
 
     # --- the 48-system batched workload (uneven sizes, 4x4 and 13x13 blocks), float32 products:
     # one grouped call over both halves against the halves run separately; single GPU only ---
@@ -749,7 +759,7 @@ def run_ours(args):
     if world == 1 and args.batch_steps > 0:
         ctx.close()
         geom.close()
-        del ctx, geom, L, L0, Lt, Lm, L64, Hd, Sd, Ldev, Sdev, Hdev
+        del ctx, geom, L, L0, Lt, Lm, L64, Hd, Sd
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         batch = batch_section(lsq, torch, stream, args.batch_steps, 2, 0)
@@ -845,10 +855,12 @@ def run_ours(args):
                                                "on the 6.6 A range"),
             "clocks": clocks,
             "e2e": e2e,
+            "e2e_with_fp64_eval": e2e_fp64_eval,
             "batch": batch,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "last_report": {"mixed": rep, "fp64": rep64, "mixed_f32": rep_f32, "e2e": rep_e2e},
+            "last_report": {"mixed": rep, "fp64": rep64, "mixed_f32": rep_f32, "e2e": rep_e2e,
+                            "e2e_with_fp64_eval": rep_e2e64},
         }
         print(json.dumps(line))
     if dist is not None:
