@@ -408,8 +408,10 @@ int lsq_lnv_init_purify(lsq_lnv ctx, const double *S_dev, const double *H_dev, d
  * line search is unchanged.  X_dev: float64 blocks on range_x, symmetric;
  * the context keeps its own copy.  range_xg: pattern for X G, covering
  * R_X + R_L (else LSQ_ERR_INVALID_ARG).  X_dev = NULL removes the metric.
- * The batched minimiser does not take a metric (LSQ_ERR_UNSUPPORTED while
- * one is set).  Allocates; synchronises stream.
+ * The batched minimisers use it too: on a batch geometry X is block diagonal
+ * over the systems, and each system's Polak-Ribiere sums are its own.  The
+ * contexts of one lsq_lnv_minimise_batch_group call take a metric all or
+ * none (else LSQ_ERR_INVALID_ARG).  Allocates; synchronises stream.
  */
 int lsq_lnv_set_metric(lsq_lnv ctx, int range_x, const double *X_dev, int range_xg, void *stream);
 

@@ -364,7 +364,7 @@ __global__ void k_batch_alpha(int nsys, double spin, double tol, BatchDev d) {
     }
 }
 
-// warp per row: D = -G + beta_sys D ; L += alpha_sys D ; Gp = G
+// warp per row: D = -P + beta_sys D (P = G, or X G X in a metric)
 __global__ void k_batch_dir(int n, int bb, const int64_t *__restrict__ rp, const int *__restrict__ atom_sys,
                             const double *__restrict__ beta, const double *__restrict__ G, double *__restrict__ D) {
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -374,6 +374,7 @@ __global__ void k_batch_dir(int n, int bb, const int64_t *__restrict__ rp, const
     for (int64_t e = rp[warp] * bb + lane; e < rp[warp + 1] * bb; e += 32) D[e] = b == 0.0 ? -G[e] : -G[e] + b * D[e];
 }
 
+// warp per row: L += alpha_sys D ; Gp = G (with a metric the caller passes P and P_prev)
 __global__ void k_batch_update(int n, int bb, const int64_t *__restrict__ rp, const int *__restrict__ atom_sys,
                                const double *__restrict__ alpha, const double *__restrict__ D,
                                double *__restrict__ L, const double *__restrict__ G, double *__restrict__ Gp) {
@@ -1499,12 +1500,17 @@ int batch_step(lsq_lnv c, double *L, const double *S, double spin, int prec, dou
     const int *asys = g->n_sys > 1 ? g->atom_sys.p : nullptr;
     BatchDev d = batch_dev(c);
     LSQ_TRY(energy_gradient(c, L, S, spin, prec, c->G.p, nullptr, nullptr, s, true, false, reuse_q));
-    LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
-    LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
+    // in a metric X the directions come from P = X G X (block diagonal over the systems, as X is)
+    // and each system's Polak-Ribiere sums are <G, P> and <G, P_prev>
+    const bool metric = c->rX >= 0;
+    if (metric) LSQ_TRY(metric_apply(c, prec, c->G.p, s));
+    double *Pdir = metric ? c->Pm.p : c->G.p, *Pprev = metric ? c->Pmp.p : c->Gp.p;
+    LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, Pdir, 10, s));
+    LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, Pprev, 11, s));
     note_launch();
     k_batch_beta<<<(ns + 127) / 128, 128, 0, s>>>(ns, spin, cg_reset, d);
     note_launch();
-    k_batch_dir<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rL].row_ptr.p, asys, c->b_beta.p, c->G.p, c->D.p);
+    k_batch_dir<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rL].row_ptr.p, asys, c->b_beta.p, Pdir, c->D.p);
     LSQ_CHECK_LAUNCH();
     double unused[3];
     LSQ_TRY(line_coeffs(c, L, S, spin, prec, unused, s, true));
@@ -1512,7 +1518,7 @@ int batch_step(lsq_lnv c, double *L, const double *S, double spin, int prec, dou
     k_batch_alpha<<<(ns + 127) / 128, 128, 0, s>>>(ns, spin, tol, d);
     note_launch();
     k_batch_update<<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->rL].row_ptr.p, asys, c->b_alpha.p, c->D.p, L,
-                                        c->G.p, c->Gp.p);
+                                        Pdir, Pprev);
     note_launch();
     if (prec == LSQ_F64)
         k_batch_axpy_rows<double><<<rows, 256, 0, s>>>(g->n, bb, g->pats[c->r3].row_ptr.p, asys, c->b_alpha.p,
@@ -1650,8 +1656,8 @@ int minimise_batch_impl(int nctx, lsq_lnv *cs, double **L, const double **S, con
     if (nctx < 1 || !cs || !L || !S || !H || !mu_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
     for (int c = 0; c < nctx; ++c) {
         if (!cs[c] || !L[c] || !S[c] || !H[c] || !mu_host[c]) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
-        if (cs[c]->rX >= 0)
-            return set_error(LSQ_ERR_UNSUPPORTED, "the batched minimiser has no metric; clear it with a null X");
+        if ((cs[c]->rX >= 0) != (cs[0]->rX >= 0))
+            return set_error(LSQ_ERR_INVALID_ARG, "the contexts of a batch take a metric all or none");
         for (int d = 0; d < c; ++d)
             if (cs[d]->g == cs[c]->g)
                 return set_error(LSQ_ERR_INVALID_ARG, "the contexts of a grouped batch need distinct geometries");
@@ -1707,6 +1713,7 @@ int minimise_batch_impl(int nctx, lsq_lnv *cs, double **L, const double **S, con
         LSQ_TRY(batch_prepare_hs(x, S[c], H[c], LSQ_F64, s));
         if (o.precision == LSQ_F32) LSQ_TRY(batch_prepare_hs(x, S[c], H[c], LSQ_F32, s));
         LSQ_CUDA_TRY(cudaMemsetAsync(x->Gp.p, 0, sizeof(double) * nl, s));
+        if (x->rX >= 0) LSQ_CUDA_TRY(cudaMemsetAsync(x->Pmp.p, 0, sizeof(double) * nl, s));
         LSQ_CUDA_TRY(cudaMemsetAsync(x->b_frozen.p, 0, sizeof(int) * ns, s));
         LSQ_CUDA_TRY(cudaMemsetAsync(x->b_iters.p, 0, sizeof(int) * ns, s));
         LSQ_CUDA_TRY(cudaMemsetAsync(x->b_gg_prev.p, 0, sizeof(double) * ns, s));

@@ -199,3 +199,66 @@ def test_grouped_batch_argument_checks():
                                  precision=lsq.TF32X3)
     with pytest.raises(ValueError):
         lsq.minimise_batch_group([ctx], [L], [cuda(S)], [], [[-2.0] * 3], max_iter=1)
+
+
+def _metric_X(systems, b):
+    """Per system the oracle's Hotelling inverse of S on S's range (30 steps); the blocks of
+    all systems in the batch geometry's order."""
+    from oracle import hotelling as OH
+    Xs = []
+    for (pos, cell, g, pH, Hk, Sk) in systems:
+        m = OL.System(pos, cell)
+        pHo = m.pattern(R_H)
+        X, _ = OH.hotelling(m, oracle.Bsr(pHo, b, Sk), R_S, 30)
+        Xs.append(X.val)
+    return Xs
+
+
+def test_batch_metric_matches_single_systems_float64():
+    """CG in the inverse-overlap metric (lsq_lnv_set_metric on the batch context, X block
+    diagonal over the systems): every system follows its own single-system metric trajectory
+    (1e-9 relative in Omega and N_e after 12 steps)."""
+    lsq.build()
+    specs = [(2, 0.05, batch_system_seed(0), None), (1, 0.1, batch_system_seed(1), None),
+             (3, 0.15, batch_system_seed(2), None)]
+    mus = [-2.0, -1.5, -2.2]
+    systems, bg, H, S = _batch(specs, 4)
+    Xs = _metric_X(systems, 4)
+    ctx = lsq.Lnv(bg, 4, R_S, R_H, R_L)
+    r_x, r_xg = bg.range_id(R_S), 3          # X on S's range; X G on L + S's range
+    ctx.set_metric(cuda(np.concatenate(Xs)), r_x, r_xg)
+    L = _init_L(ctx, bg, S, 4)
+    reps = ctx.minimise_batch(L, cuda(S), cuda(H), mus, max_iter=12)
+    for k, (pos, cell, g, pH, Hk, Sk) in enumerate(systems):
+        c1 = lsq.Lnv(g, 4, R_S, R_H, R_L)
+        c1.set_metric(cuda(Xs[k]), g.range_id(R_S), 3)
+        Lk = _init_L(c1, g, Sk, 4)
+        rep = c1.minimise(Lk, cuda(Sk), cuda(Hk), mus[k], max_iter=12)
+        assert reps[k]["iterations"] == rep["iterations"] == 12
+        assert abs(reps[k]["omega_ev"] - rep["omega_ev"]) <= 1e-9 * abs(rep["omega_ev"])
+        assert abs(reps[k]["ne"] - rep["ne"]) <= 1e-9 * abs(rep["ne"])
+
+
+def test_grouped_batch_metric_matches_separate_batches_float64():
+    """The grouped call with a metric on both contexts (4 x 4 and 13 x 13 batches; the metric's
+    two products of each step grouped like the others) against the two batches run separately
+    with the same metric: 1e-9 relative in Omega and N_e after 10 steps, L to 1e-7."""
+    lsq.build()
+    mus = [[-2.0, -1.5, -2.2], [-2.0, -1.8]]
+    parts, Ls, Ss, Hs = _group_setup(mus)
+    for systems, bg, ctx, H, S, b in parts:
+        ctx.set_metric(cuda(np.concatenate(_metric_X(systems, b))), bg.range_id(R_S), 3)
+    L_sep = [L.clone() for L in Ls]
+    reps = lsq.minimise_batch_group([p[2] for p in parts], Ls, Ss, Hs, mus, max_iter=10)
+    for c, (systems, bg, ctx, H, S, b) in enumerate(parts):
+        sep = ctx.minimise_batch(L_sep[c], Ss[c], Hs[c], mus[c], max_iter=10)
+        for a, r in zip(reps[c], sep):
+            assert a["iterations"] == r["iterations"] == 10
+            assert abs(a["omega_ev"] - r["omega_ev"]) <= 1e-9 * abs(r["omega_ev"])
+            assert abs(a["ne"] - r["ne"]) <= 1e-9 * abs(r["ne"])
+        scale = L_sep[c].abs().max().item()
+        assert (Ls[c] - L_sep[c]).abs().max().item() <= 1e-7 * scale
+    # a metric on one context of a grouped call but not the other is refused
+    parts[1][2].set_metric(None, parts[1][1].range_id(R_S), 3)
+    with pytest.raises(lsq.LsqError):
+        lsq.minimise_batch_group([p[2] for p in parts], [L.clone() for L in Ls], Ss, Hs, mus, max_iter=1)

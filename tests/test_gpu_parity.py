@@ -365,7 +365,7 @@ def test_lnv_tf32x3_energy_gradient_and_minimum():
 
 def test_lnv_metric_cg_matches_oracle_trajectory():
     """CG in the inverse-overlap metric (lsq_lnv_set_metric): 15 steps against the oracle;
-    the identity metric reproduces plain CG; the batched minimiser refuses a metric."""
+    the identity metric reproduces plain CG; the batched minimiser follows it too."""
     from oracle import hotelling as OH
     g, ctx, ref, Hb, Sb = _lnv_setup(2, 0.05, config_seed(0), 8.0)
     X, _ = OH.hotelling(ref.sys, Sb, R_S, 30)
@@ -379,8 +379,12 @@ def test_lnv_metric_cg_matches_oracle_trajectory():
     assert rep["iterations"] == 15
     assert abs(rep["omega_ev"] - om_ref) <= 1e-9 * abs(om_ref)
     assert rel_err(Lg.cpu().numpy(), Lr.val) <= 1e-7
-    with pytest.raises(lsq.LsqError):
-        ctx.minimise_batch(cuda(L0.val), cuda(Sb.val), cuda(Hb.val), [MU], max_iter=1)
+    # the batched minimiser (one system) takes the metric too and follows the same trajectory
+    Lb = cuda(L0.val)
+    repb = ctx.minimise_batch(Lb, cuda(Sb.val), cuda(Hb.val), [MU], max_iter=15)
+    assert repb[0]["iterations"] == 15
+    assert abs(repb[0]["omega_ev"] - om_ref) <= 1e-9 * abs(om_ref)
+    assert rel_err(Lb.cpu().numpy(), Lr.val) <= 1e-7
     # identity blocks as the metric: the plain trajectory
     pX = ref.sys.pattern(R_S)
     eye = np.zeros((pX.nnzb, 4, 4))
