@@ -449,6 +449,28 @@ int lsq_lnv_minimise_batch(lsq_lnv ctx, double *L_dev, const double *S_dev, cons
                            void *stream);
 
 /*
+ * The canonical minimisation (lsq_lnv_minimise_canonical: E_band at fixed
+ * N_e, Sec. 2.3.2) for every system of a geometry made by lsq_geom_concat,
+ * all systems at once.  n_electrons_host[n_sys]: each system's electron
+ * count (positive).  Each step restores every system's N_e by Newton moves
+ * along its own dN_e/dL (at most 5, until |N_e - N0| <= tol N0 with tol
+ * 1e-9 for LSQ_F64 products and 1e-6 otherwise; the host reads one count
+ * per round to know whether any system still moves), then projects the
+ * energy gradient and the Polak-Ribiere direction on constant N_e, with
+ * each system's multiplier lambda = <G_E, G_N> / <G_N, G_N> (its chemical
+ * potential), and takes each system's exact cubic step of E_band.  As in
+ * lsq_lnv_minimise_batch, a direction that is not descent restarts on the
+ * next step, and a converged system is frozen.  No metric (else
+ * LSQ_ERR_UNSUPPORTED); no float64 refinement phase.  reps[n_sys] (optional)
+ * receives E_band (omega_ev), N_e and the step counts; lambda_host[n_sys]
+ * (optional) the multipliers.  Allocates; synchronises the stream after
+ * every correction round.
+ */
+int lsq_lnv_minimise_batch_canonical(lsq_lnv ctx, double *L_dev, const double *S_dev, const double *H_dev,
+                                     const double *n_electrons_host, const lsq_lnv_opts *opts,
+                                     lsq_lnv_report *reps, double *lambda_host, void *stream);
+
+/*
  * lsq_lnv_minimise_batch over n_ctx contexts at once (1 <= n_ctx <= 16), each on its own
  * lsq_geom_concat geometry with its own block size: a batch of uneven systems whose block
  * sizes differ (4 x 4 and 13 x 13, say) in one call.  Arrays are per context: L_dev[c],

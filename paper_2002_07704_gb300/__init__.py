@@ -90,6 +90,7 @@ def load():
         "lsq_lnv_set_metric": (I, [P, I, P, I, P]),
         "lsq_lnv_init_purify": (I, [P, P, P, D, I, P, I, I, I, P, P, P]),
         "lsq_lnv_minimise_canonical": (I, [P, P, P, P, D, P, P, P, P]),
+        "lsq_lnv_minimise_batch_canonical": (I, [P, P, P, P, P, P, P, P, P]),
         "lsq_pattern_remap": (I, [P, I, P, I, I, I, P, P, P]),
         "lsq_geom_adopt_schedules": (I, [P, P]),
         "lsq_xl_propagate": (I, [P, I, I, I, P, P, D, D, P, I, P, P]),
@@ -115,7 +116,7 @@ def exported_symbols():
             "lsq_lnv_default_opts", "lsq_lnv_required_ranges", "lsq_lnv_create",
             "lsq_lnv_destroy", "lsq_lnv_init_L", "lsq_lnv_energy_gradient", "lsq_lnv_minimise",
             "lsq_lnv_minimise_batch", "lsq_lnv_minimise_batch_group", "lsq_lnv_set_metric", "lsq_lnv_init_purify",
-            "lsq_lnv_minimise_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L",
+            "lsq_lnv_minimise_canonical", "lsq_lnv_minimise_batch_canonical", "lsq_pattern_remap", "lsq_xl_propagate", "lsq_xl_initial_L",
             "lsq_geom_adopt_schedules", "lsq_device_status", "lsq_measure_peak", "lsq_product_plan_info"]
 
 
@@ -485,6 +486,8 @@ class Lnv:
         """Minimises every system of a concatenated geometry; mu: one value per system."""
         import torch
         mu = [float(m) for m in mu]
+        if len(mu) != len(self.geom.systems()) - 1:
+            raise LsqError(1, "mu needs one value per system of the geometry")
         o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
                     int(bool(final_eval)), 0, int(bool(graph)))
         reps = (LnvReport * len(mu))()
@@ -495,6 +498,25 @@ class Lnv:
         if rc != 0 and (raise_on_status or rc not in (5, 6)):
             _check(rc)
         return [r.as_dict() for r in reps]
+
+    def minimise_batch_canonical(self, L, S, H, n_electrons, max_iter=100, tol_ha_per_atom=0.0, cg_reset=40,
+                                 precision=F64, spin=2.0, stream=None, raise_on_status=False):
+        """E_band at fixed N_e for every system of a concatenated geometry (n_electrons: one
+        value per system).  Returns (reports, lambdas), one of each per system."""
+        import torch
+        ne = [float(v) for v in n_electrons]
+        if len(ne) != len(self.geom.systems()) - 1:
+            raise LsqError(1, "n_electrons needs one value per system of the geometry")
+        o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, 0, spin, 0, 0, 0)
+        self._need_lsh(L=L, S=S, H=H)
+        reps = (LnvReport * len(ne))()
+        lam = (ctypes.c_double * len(ne))()
+        f = torch.float64
+        rc = _lib.lsq_lnv_minimise_batch_canonical(self.handle, _dev(L, f), _dev(S, f), _dev(H, f),
+                                                   _darr(ne), ctypes.byref(o), reps, lam, _stream(stream))
+        if rc != 0 and (raise_on_status or rc not in (5, 6)):
+            _check(rc)
+        return [r.as_dict() for r in reps], [lam[k] for k in range(len(ne))]
 
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
@@ -519,6 +541,9 @@ def minimise_batch_group(ctxs, Ls, Ss, Hs, mus, max_iter=100, tol_ha_per_atom=0.
     n = len(ctxs)
     if not (len(Ls) == len(Ss) == len(Hs) == len(mus) == n):
         raise ValueError("one L, S, H and mu list per context")
+    for c, mu in zip(ctxs, mus):
+        if len(mu) != len(c.geom.systems()) - 1:
+            raise LsqError(1, "each mu list needs one value per system of its context's geometry")
     o = LnvOpts(max_iter, tol_ha_per_atom, cg_reset, precision, refine_iter, spin,
                 int(bool(final_eval)), 0, 1)
     f = torch.float64

@@ -1860,3 +1860,188 @@ extern "C" int lsq_lnv_minimise_batch_group(int n_ctx, lsq_lnv *ctx, double **L_
         return set_error(LSQ_ERR_INVALID_ARG, "n_ctx must be in [1, " + std::to_string(kMaxGroupContexts) + "]");
     return minimise_batch_impl(n_ctx, ctx, L_dev, S_dev, H_dev, mu_host, opts, reps, (cudaStream_t)stream, true);
 }
+
+namespace {
+
+// Canonical batch, after an evaluation with S in place of H' (slots 0, 1: N_e's traces; slot 10:
+// <G_N, G_N>): N_e of every system, and the Newton move (N0 - N_e) / <G_N, G_N> along G_N for each
+// system still off by more than tol_rel N0 (0 for the others, for frozen systems and on the last
+// evaluation of a step).  pending counts the systems that move.
+__global__ void k_bcan_ne(int nsys, double spin, const double *__restrict__ n0, double tol_rel, int last,
+                          BatchDev d, double *__restrict__ ne, double *__restrict__ gnn, double *__restrict__ coef,
+                          int *__restrict__ pending) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    const double *sl = d.slots + (int64_t)s * kSlots;
+    const double N = spin * (3.0 * sl[0] - 2.0 * sl[1]);
+    double cf = 0.0;
+    if (!d.frozen[s]) {
+        ne[s] = N;
+        gnn[s] = sl[10];
+        if (!(sl[10] > 0.0)) {  // the electron-number gradient vanished
+            d.status[s] = LSQ_ERR_UNSTABLE;
+            d.frozen[s] = 1;
+        } else if (!last && fabs(N - n0[s]) > tol_rel * n0[s]) {
+            cf = (n0[s] - N) / sl[10];
+            atomicAdd(pending, 1);
+        }
+    }
+    coef[s] = cf;
+}
+
+// coef = -<X, G_N> / <G_N, G_N> of every system (slot 12 holds <X, G_N>); with lam != null the
+// ratio itself is the system's multiplier lambda (X = the energy gradient).
+__global__ void k_bcan_proj(int nsys, BatchDev d, const double *__restrict__ gnn, double *__restrict__ lam,
+                            double *__restrict__ coef) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    const double r = d.frozen[s] ? 0.0 : d.slots[(int64_t)s * kSlots + 12] / gnn[s];
+    if (lam && !d.frozen[s]) lam[s] = r;
+    coef[s] = -r;
+}
+
+}  // namespace
+
+extern "C" int lsq_lnv_minimise_batch_canonical(lsq_lnv c, double *L, const double *S, const double *H,
+                                                const double *n_electrons_host, const lsq_lnv_opts *opts,
+                                                lsq_lnv_report *reps, double *lambda_host, void *stream) {
+    clear_error();
+    if (!c || !L || !S || !H || !n_electrons_host) return set_error(LSQ_ERR_INVALID_ARG, "null argument");
+    lsq_lnv_opts o;
+    lsq_lnv_default_opts(&o);
+    if (opts) o = *opts;
+    LSQ_TRY(take_precision(c, &o.precision));
+    if (o.max_iter < 0 || o.cg_reset < 1) return set_error(LSQ_ERR_INVALID_ARG, "bad iteration options");
+    if (c->rX >= 0) return set_error(LSQ_ERR_UNSUPPORTED, "the canonical minimiser has no metric; clear it");
+    lsq_geom g = c->g;
+    const int ns = g->n_sys, bb = c->b * c->b;
+    for (int k = 0; k < ns; ++k)
+        if (!(n_electrons_host[k] > 0.0)) return set_error(LSQ_ERR_INVALID_ARG, "n_electrons must be positive");
+    LSQ_TRY(ensure_ws(c, widest(o)));
+    LSQ_TRY(batch_alloc(c));
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const int prec = o.precision;
+    const double tol_ne = prec == LSQ_F64 ? 1e-9 : 1e-6;  // relative, as lsq_lnv_minimise_canonical
+    const int max_correct = 5;
+    const int64_t nl = nvals(c, c->rL);
+    const int rows = (int)(((int64_t)g->n * 32 + 255) / 256);
+    const int *asys = ns > 1 ? g->atom_sys.p : nullptr;
+    const int64_t *rpL = g->pats[c->rL].row_ptr.p;
+    DevBuf<double> GN, n0, ne, gnn, lam, coef;
+    DevBuf<int> pending;
+    LSQ_TRY(GN.alloc((size_t)std::max<int64_t>(nl, 1)));
+    LSQ_TRY(n0.alloc(ns));
+    LSQ_TRY(ne.alloc(ns));
+    LSQ_TRY(gnn.alloc(ns));
+    LSQ_TRY(lam.alloc(ns));
+    LSQ_TRY(coef.alloc(ns));
+    LSQ_TRY(pending.alloc(1));
+    // mu = 0 for every system: H' = H, so the grand potential of an evaluation is E_band
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_mu.p, 0, sizeof(double) * ns, s));
+    LSQ_TRY(batch_prepare_hs(c, S, H, LSQ_F64, s));
+    if (prec == LSQ_F32) LSQ_TRY(batch_prepare_hs(c, S, H, LSQ_F32, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(n0.p, n_electrons_host, sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->Gp.p, 0, sizeof(double) * nl, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_frozen.p, 0, sizeof(int) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_iters.p, 0, sizeof(int) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_gg_prev.p, 0, sizeof(double) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_dom.p, 0, sizeof(double) * ns, s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(c->b_step.p, 0, sizeof(int), s));
+    LSQ_CUDA_TRY(cudaMemsetAsync(lam.p, 0, sizeof(double) * ns, s));
+    {
+        std::vector<int> one(ns, 1), st(ns, o.tol_ha_per_atom > 0.0 ? LSQ_ERR_NOT_CONVERGED : LSQ_OK);
+        LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_reset.p, one.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_CUDA_TRY(cudaMemcpyAsync(c->b_status.p, st.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+        LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    BatchDev d = batch_dev(c);
+    std::vector<int> frozen(ns);
+    const int sb = (ns + 127) / 128;
+    for (int it = 0; it < o.max_iter; ++it) {
+        // restore every system's N_e along its dN_e/dL (Newton moves, at most max_correct)
+        for (int corr = 0; corr <= max_correct; ++corr) {
+            LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, GN.p, nullptr, nullptr, s, true, false, false, true));
+            LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, GN.p, GN.p, 10, s));
+            LSQ_CUDA_TRY(cudaMemsetAsync(pending.p, 0, sizeof(int), s));
+            note_launch();
+            k_bcan_ne<<<sb, 128, 0, s>>>(ns, o.spin, n0.p, tol_ne, corr == max_correct ? 1 : 0, d, ne.p, gnn.p,
+                                         coef.p, pending.p);
+            LSQ_CHECK_LAUNCH();
+            int np = 0;
+            LSQ_CUDA_TRY(cudaMemcpyAsync(&np, pending.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+            if (np == 0) break;
+            note_launch();
+            k_batch_axpy_rows<double><<<rows, 256, 0, s>>>(g->n, bb, rpL, asys, coef.p, GN.p, L);
+            LSQ_CHECK_LAUNCH();
+        }
+        // the energy gradient projected on constant N_e (lambda = <G_E, G_N> / <G_N, G_N>, the
+        // chemical potential), Polak-Ribiere directions projected the same way, the cubic step
+        LSQ_TRY(energy_gradient(c, L, S, o.spin, prec, c->G.p, nullptr, nullptr, s, true));
+        LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, GN.p, 12, s));
+        note_launch();
+        k_bcan_proj<<<sb, 128, 0, s>>>(ns, d, gnn.p, lam.p, coef.p);
+        note_launch();
+        k_batch_axpy_rows<double><<<rows, 256, 0, s>>>(g->n, bb, rpL, asys, coef.p, GN.p, c->G.p);
+        LSQ_CHECK_LAUNCH();
+        LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->G.p, 10, s));
+        LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->G.p, c->Gp.p, 11, s));
+        note_launch();
+        k_batch_beta<<<sb, 128, 0, s>>>(ns, o.spin, o.cg_reset, d);
+        note_launch();
+        k_batch_dir<<<rows, 256, 0, s>>>(g->n, bb, rpL, asys, c->b_beta.p, c->G.p, c->D.p);
+        LSQ_CHECK_LAUNCH();
+        LSQ_TRY(seg_dot(c, LSQ_F64, c->rL, c->D.p, GN.p, 12, s));
+        note_launch();
+        k_bcan_proj<<<sb, 128, 0, s>>>(ns, d, gnn.p, nullptr, coef.p);
+        note_launch();
+        k_batch_axpy_rows<double><<<rows, 256, 0, s>>>(g->n, bb, rpL, asys, coef.p, GN.p, c->D.p);
+        LSQ_CHECK_LAUNCH();
+        double unused[3];
+        LSQ_TRY(line_coeffs(c, L, S, o.spin, prec, unused, s, true));
+        note_launch();
+        k_batch_alpha<<<sb, 128, 0, s>>>(ns, o.spin, o.tol_ha_per_atom, d);
+        note_launch();
+        k_batch_update<<<rows, 256, 0, s>>>(g->n, bb, rpL, asys, c->b_alpha.p, c->D.p, L, c->G.p, c->Gp.p);
+        LSQ_CHECK_LAUNCH();
+        if (o.tol_ha_per_atom > 0.0) {
+            LSQ_CUDA_TRY(cudaMemcpyAsync(frozen.data(), c->b_frozen.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+            LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+            bool all = true;
+            for (int k = 0; k < ns; ++k) all = all && frozen[k];
+            if (all) break;
+        }
+    }
+    std::vector<double> om(ns), nev(ns), lv(ns), dom(ns);
+    std::vector<int> iters(ns), status(ns);
+    LSQ_CUDA_TRY(cudaMemcpyAsync(om.data(), c->b_omega.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(nev.data(), ne.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(lv.data(), lam.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(dom.data(), c->b_dom.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(iters.data(), c->b_iters.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaMemcpyAsync(status.data(), c->b_status.p, sizeof(int) * ns, cudaMemcpyDeviceToHost, s));
+    LSQ_CUDA_TRY(cudaStreamSynchronize(s));
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int worst = LSQ_OK;
+    for (int k = 0; k < ns; ++k) {
+        const int na = (int)(g->sys_atom_off[k + 1] - g->sys_atom_off[k]);
+        if (reps) {
+            lsq_lnv_report &r = reps[k];
+            r.iterations = iters[k];
+            r.iterations_fp64 = prec == LSQ_F64 ? iters[k] : 0;
+            r.status = status[k];
+            r.omega_ev = om[k];
+            r.ne = nev[k];
+            r.omega_ha_per_atom = om[k] / kHartreeEv / std::max(na, 1);
+            r.last_domega_ha_per_atom = dom[k];
+            r.seconds = sec;
+        }
+        if (lambda_host) lambda_host[k] = lv[k];
+        if (status[k] == LSQ_ERR_UNSTABLE) worst = LSQ_ERR_UNSTABLE;
+        else if (status[k] != LSQ_OK && worst == LSQ_OK) worst = status[k];
+    }
+    if (worst == LSQ_ERR_UNSTABLE) return set_error(worst, "a system found no local minimum or lost dN_e/dL");
+    if (worst == LSQ_ERR_NOT_CONVERGED) return set_error(worst, "iteration limit reached");
+    return LSQ_OK;
+}

@@ -262,3 +262,56 @@ def test_grouped_batch_metric_matches_separate_batches_float64():
     parts[1][2].set_metric(None, parts[1][1].range_id(R_S), 3)
     with pytest.raises(lsq.LsqError):
         lsq.minimise_batch_group([p[2] for p in parts], [L.clone() for L in Ls], Ss, Hs, mus, max_iter=1)
+
+
+def _canonical_specs():
+    specs = [(2, 0.05, batch_system_seed(0), None), (1, 0.1, batch_system_seed(1), None),
+             (3, 0.15, batch_system_seed(2), None)]
+    systems, bg, H, S = _batch(specs, 4)
+    # 174 electrons for 64 atoms (between the grand-canonical start's count and the minimum's)
+    n0 = [174.0 / 64.0 * s[0].shape[0] for s in systems]
+    return systems, bg, H, S, n0
+
+
+@pytest.mark.parametrize("prec", [lsq.F64, lsq.F32])
+def test_batch_canonical_matches_single_systems(prec):
+    """lsq_lnv_minimise_batch_canonical: every system follows its own single-system canonical
+    trajectory (lsq_lnv_minimise_canonical, itself checked against the oracle): float64 to 1e-9
+    relative in E_band and N_e and 1e-7 in lambda after 12 steps; float32 products within 1e-4
+    of the float64 batch in E_band with N_e held to 1e-5, the single-system float32 bars."""
+    lsq.build()
+    systems, bg, H, S, n0 = _canonical_specs()
+    ctx = lsq.Lnv(bg, 4, R_S, R_H, R_L)
+    L = _init_L(ctx, bg, S, 4)
+    reps, lams = ctx.minimise_batch_canonical(L, cuda(S), cuda(H), n0, max_iter=12, precision=prec)
+    if prec == lsq.F32:
+        L64 = _init_L(ctx, bg, S, 4)
+        r64, _ = ctx.minimise_batch_canonical(L64, cuda(S), cuda(H), n0, max_iter=12)
+        for k, (a, r) in enumerate(zip(reps, r64)):
+            assert a["iterations"] == 12
+            assert abs(a["ne"] - n0[k]) <= 1e-5 * n0[k]
+            assert abs(a["omega_ev"] - r["omega_ev"]) <= 1e-4 * abs(r["omega_ev"])
+        return
+    for k, (pos, cell, g, pH, Hk, Sk) in enumerate(systems):
+        c1 = lsq.Lnv(g, 4, R_S, R_H, R_L)
+        Lk = _init_L(c1, g, Sk, 4)
+        rep, lam = c1.minimise_canonical(Lk, cuda(Sk), cuda(Hk), n0[k], max_iter=12)
+        assert reps[k]["iterations"] == rep["iterations"] == 12
+        assert abs(reps[k]["omega_ev"] - rep["omega_ev"]) <= 1e-9 * abs(rep["omega_ev"])
+        assert abs(reps[k]["ne"] - rep["ne"]) <= 1e-9 * abs(rep["ne"])
+        assert abs(lams[k] - lam) <= 1e-7 * abs(lam)
+
+
+def test_batch_canonical_argument_checks():
+    """One electron count per system, each positive; no metric."""
+    lsq.build()
+    systems, bg, H, S, n0 = _canonical_specs()
+    ctx = lsq.Lnv(bg, 4, R_S, R_H, R_L)
+    L = _init_L(ctx, bg, S, 4)
+    with pytest.raises(lsq.LsqError):
+        ctx.minimise_batch_canonical(L, cuda(S), cuda(H), n0[:2], max_iter=1)
+    with pytest.raises(lsq.LsqError):
+        ctx.minimise_batch_canonical(L, cuda(S), cuda(H), [n0[0], -1.0, n0[2]], max_iter=1)
+    ctx.set_metric(cuda(np.concatenate(_metric_X(systems, 4))), bg.range_id(R_S), 3)
+    with pytest.raises(lsq.LsqError):
+        ctx.minimise_batch_canonical(L, cuda(S), cuda(H), n0, max_iter=1)
