@@ -211,7 +211,7 @@ def _check(ref, res, world):
         assert np.max(np.abs(full - ref[refkey])) <= tol * np.max(np.abs(ref[refkey]))
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_gloo_ranks_match_single_process(ref, world):
     res = _run(world, ref["L2"], ref["L0"])
     _check(ref, res, world)
