@@ -39,6 +39,9 @@ __device__ __forceinline__ bool tri_skip(int tri, int i, int j) {
 
 
 constexpr int kMaxPlanRow = 8192;  // longest row of C a plan handles (shared-memory sort)
+// The plan builder's atom map holds 16-bit positions within a row of A (plan items pack them in
+// 16 bits too), so rows of A and B hold at most 65535 blocks and 0xffff marks an absent atom.
+constexpr uint16_t kNoAtom = 0xffff;
 
 // ---- symbolic product: item count of every block of C -----------------------
 __global__ void __launch_bounds__(512) k_plan_count(int n, const int64_t *__restrict__ a_ptr,
@@ -48,25 +51,25 @@ __global__ void __launch_bounds__(512) k_plan_count(int n, const int64_t *__rest
                                                     const int64_t *__restrict__ c_ptr,
                                                     const int32_t *__restrict__ c_col,
                                                     int upper, int32_t *__restrict__ cnt) {
-    extern __shared__ int amap[];  // [n]
+    extern __shared__ uint16_t amap[];  // [n]: position of atom k in row i of A, kNoAtom if absent
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    for (int j = tid; j < n; j += nth) amap[j] = -1;
+    for (int j = tid; j < n; j += nth) amap[j] = kNoAtom;
     __syncthreads();
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const int64_t a0 = a_ptr[i], a1 = a_ptr[i + 1];
-        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = (int)(p - a0);
+        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = (uint16_t)(p - a0);
         __syncthreads();
         for (int64_t s = c_ptr[i] + warp; s < c_ptr[i + 1]; s += nwarps) {
             const int j = c_col[s];
             int c = 0;
             if (!tri_skip(upper, i, j))
-                for (int64_t q = x_ptr[j] + lane; q < x_ptr[j + 1]; q += 32) c += amap[x_col[q]] >= 0;
+                for (int64_t q = x_ptr[j] + lane; q < x_ptr[j + 1]; q += 32) c += amap[x_col[q]] != kNoAtom;
             for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
             if (lane == 0) cnt[s] = c;
         }
         __syncthreads();
-        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = -1;
+        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = kNoAtom;
         __syncthreads();
     }
 }
@@ -144,14 +147,14 @@ __global__ void __launch_bounds__(512) k_plan_fill(int n, const int64_t *__restr
                                                    const int32_t *__restrict__ c_col,
                                                    const int64_t *__restrict__ item_ptr, int upper,
                                                    uint32_t *__restrict__ items) {
-    extern __shared__ int amap[];
+    extern __shared__ uint16_t amap[];  // as in k_plan_count
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    for (int j = tid; j < n; j += nth) amap[j] = -1;
+    for (int j = tid; j < n; j += nth) amap[j] = kNoAtom;
     __syncthreads();
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const int64_t a0 = a_ptr[i], a1 = a_ptr[i + 1];
-        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = (int)(p - a0);
+        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = (uint16_t)(p - a0);
         __syncthreads();
         for (int64_t s = c_ptr[i] + warp; s < c_ptr[i + 1]; s += nwarps) {
             const int j = c_col[s];
@@ -160,15 +163,15 @@ __global__ void __launch_bounds__(512) k_plan_fill(int n, const int64_t *__restr
             int64_t w = item_ptr[s];
             for (int64_t qb = x0; qb < x1; qb += 32) {
                 const int64_t q = qb + lane;
-                const int ao = q < x1 ? amap[x_col[q]] : -1;
-                const unsigned m = __ballot_sync(0xffffffffu, ao >= 0);
-                if (ao >= 0)
+                const int ao = q < x1 ? (int)amap[x_col[q]] : (int)kNoAtom;
+                const unsigned m = __ballot_sync(0xffffffffu, ao != kNoAtom);
+                if (ao != kNoAtom)
                     items[w + __popc(m & ((1u << lane) - 1u))] = (uint32_t)ao | ((uint32_t)(q - x0) << 16);
                 w += __popc(m);
             }
         }
         __syncthreads();
-        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = -1;
+        for (int64_t p = a0 + tid; p < a1; p += nth) amap[a_col[p]] = kNoAtom;
         __syncthreads();
     }
 }
@@ -856,13 +859,15 @@ int plan_count_triples(lsq_geom g, int ra, int rb, int rc, int upper, int64_t *o
         *out = it->second.triples;
         return LSQ_OK;
     }
-    if ((size_t)n * sizeof(int) + 1024 > g->smem_optin)
+    if (PA.max_row > 65535 || PB.max_row > 65535)
+        return set_error(LSQ_ERR_UNSUPPORTED, "row too long for a product plan");
+    if ((size_t)n * sizeof(uint16_t) + 1024 > g->smem_optin)
         return set_error(LSQ_ERR_UNSUPPORTED, "too many atoms for the shared-memory atom map");
     DevBuf<int32_t> cnt;
     DevBuf<unsigned long long> tot;
     LSQ_TRY(cnt.alloc(PC.nnzb));
     LSQ_TRY(tot.alloc(1));
-    const size_t smem_map = (size_t)n * sizeof(int);
+    const size_t smem_map = (size_t)n * sizeof(uint16_t);
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_plan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_map));
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_count, 512, smem_map);
@@ -899,7 +904,7 @@ int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out,
     const int n = g->n;
     if (PA.max_row > 65535 || PB.max_row > 65535 || PC.max_row > kMaxPlanRow)
         return set_error(LSQ_ERR_UNSUPPORTED, "row too long for a product plan");
-    if ((size_t)n * sizeof(int) + 1024 > g->smem_optin)
+    if ((size_t)n * sizeof(uint16_t) + 1024 > g->smem_optin)
         return set_error(LSQ_ERR_UNSUPPORTED, "too many atoms for the shared-memory atom map");
     ProductPlan p;
     const int64_t nc = PC.nnzb;
@@ -908,7 +913,7 @@ int plan_build(lsq_geom g, int ra, int rb, int rc, int upper, ProductPlan **out,
     LSQ_TRY(p.item_ptr.alloc((size_t)nc + 1));
     LSQ_TRY(p.c_row.alloc(nc));
     int per_sm = 1;
-    size_t smem_map = (size_t)n * sizeof(int);
+    size_t smem_map = (size_t)n * sizeof(uint16_t);
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_plan_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_map));
     LSQ_CUDA_TRY(cudaFuncSetAttribute(k_plan_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_map));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_count, 512, smem_map);

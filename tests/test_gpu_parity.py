@@ -242,6 +242,46 @@ def test_block_matmul_full_size_float32_sampled_rows(shape):
     assert np.abs(got[sel] - ref.val[sel]).max() <= 1e-5 * bnd.val[sel].max()
 
 
+@pytest.mark.parametrize("prec", [lsq.F64, lsq.F32, lsq.TF32X3])
+def test_block_matmul_64000_atoms_sampled_rows(prec):
+    """64,000-atom Si (20 x 20 x 20 cells), beyond the 57,856 atoms a 32-bit shared-memory
+    atom map allowed the plan builder: L-like (4 A) . S-like (2.6 A) on the natural 6.6 A range,
+    32 sampled rows against the oracle (float64 within 1e-12 of the largest reference element;
+    float32 and split-TF32 within 1e-5 of max |A|.|B| over those rows)."""
+    pos, cell = si(20, 0.05, config_seed(1) + 20)
+    ranges = [2.6, 4.0, 6.6]
+    g = gpu_geometry(pos, cell, ranges)
+    assert g.n_atoms == 64000
+    P = {R: oracle.neighbour_list(pos, cell, R) for R in ranges}
+    rng = np.random.default_rng(21)
+    f32 = prec != lsq.F64
+    A = _rand(P[4.0], 4, rng)
+    B = _rand(P[2.6], 4, rng)
+    if f32:
+        A, B = A.astype(np.float32).astype(np.float64), B.astype(np.float32).astype(np.float64)
+    A, B = oracle.Bsr(P[4.0], 4, A), oracle.Bsr(P[2.6], 4, B)
+    dt = torch.float32 if f32 else torch.float64
+    Cg = torch.zeros((P[6.6].nnzb, 4, 4), dtype=dt, device="cuda")
+    args = (g, 4, cuda(A.val, dt), 1, cuda(B.val, dt), 0, Cg, 2)
+    lsq.block_matmul(*args, precision=prec)     # first call: plans (and the kernel choice)
+    Cg.zero_()
+    lsq.block_matmul(*args, precision=prec)
+    g.device_status()
+    rows = np.sort(rng.choice(64000, size=32, replace=False))
+    rows[0], rows[-1] = 0, 63999
+    ref, _ = oracle.matmul(A, B, P[6.6], rows=rows)
+    pc = P[6.6]
+    prow = np.repeat(np.arange(pc.n), np.diff(pc.ptr))
+    sel = np.isin(prow, rows)
+    got = Cg.double().cpu().numpy()
+    if not f32:
+        assert np.abs(got[sel] - ref.val[sel]).max() <= 1e-12 * np.abs(ref.val[sel]).max()
+    else:
+        bnd, _ = oracle.matmul(oracle.Bsr(P[4.0], 4, np.abs(A.val)), oracle.Bsr(P[2.6], 4, np.abs(B.val)),
+                               P[6.6], rows=rows)
+        assert np.abs(got[sel] - ref.val[sel]).max() <= 1e-5 * bnd.val[sel].max()
+
+
 def test_trace_matches_oracle():
     pos, cell = si(2, 0.1, 5)
     g = gpu_geometry(pos, cell, [6.6, 10.0])
