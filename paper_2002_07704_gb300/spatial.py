@@ -44,13 +44,20 @@ def slab_held_atoms(pos, cell, owners, rank, nranks, depth, axis=0):
     return np.nonzero(held)[0].astype(np.int64)
 
 
+def row_blocks(ptr, rows):
+    """Block indices of the given rows of a CSR pattern, row after row."""
+    ptr = np.asarray(ptr, dtype=np.int64)
+    rows = np.asarray(rows, dtype=np.int64)
+    starts = ptr[rows]
+    lens = ptr[rows + 1] - starts
+    first = np.cumsum(lens) - lens
+    return np.repeat(starts - first, lens) + np.arange(int(lens.sum()), dtype=np.int64)
+
+
 def reach(ptr, col, rows):
     """Columns of a CSR pattern over the given rows (sorted, unique): the rows of B that
     those rows of A reach in a product A.B."""
-    rows = np.asarray(rows, dtype=np.int64)
-    if rows.size == 0:
-        return np.zeros(0, dtype=np.int64)
-    return np.unique(np.concatenate([col[ptr[i]:ptr[i + 1]] for i in rows])).astype(np.int64)
+    return np.unique(np.asarray(col)[row_blocks(ptr, rows)]).astype(np.int64)
 
 
 def lnv_ranges(R_S, R_H, R_L):
@@ -80,10 +87,8 @@ class HeldPattern:
         gptr = np.asarray(gptr, dtype=np.int64)
         gcol = np.asarray(gcol, dtype=np.int64)
         self.gptr = gptr
-        starts, ends = gptr[held], gptr[held + 1]
-        idx = np.concatenate([np.arange(s, e) for s, e in zip(starts, ends)]) if held.size else \
-            np.zeros(0, dtype=np.int64)
-        rows = np.repeat(np.arange(held.size), ends - starts)
+        idx = row_blocks(gptr, held)
+        rows = np.repeat(np.arange(held.size), gptr[held + 1] - gptr[held])
         keep = g2l[gcol[idx]] >= 0
         self.gpos = idx[keep].astype(np.int64)
         self.col = g2l[gcol[self.gpos]].astype(np.int32)
@@ -195,10 +200,13 @@ class Slabs:
             req.wait()
             full = buf.numpy().reshape(-1, self.b, self.b)
             lrows = self.g2l[rows_in]
-            start = np.concatenate([[0], np.cumsum(hp.gptr[rows_in + 1] - hp.gptr[rows_in])])
-            pick = np.concatenate([start[q] + hp.gpos[hp.ptr[l]:hp.ptr[l + 1]] - hp.gptr[g]
-                                   for q, (l, g) in enumerate(zip(lrows, rows_in))])
-            engine.set_rows(X, lrows, full[pick.astype(np.int64)])
+            # the held blocks of each received row: their offsets in the owner's full row,
+            # shifted to where that row starts in the message
+            glen = hp.gptr[rows_in + 1] - hp.gptr[rows_in]
+            llen = hp.ptr[lrows + 1] - hp.ptr[lrows]
+            shift = np.repeat(np.cumsum(glen) - glen - hp.gptr[rows_in], llen)
+            pick = hp.gpos[row_blocks(hp.ptr, lrows)] + shift
+            engine.set_rows(X, lrows, full[pick])
             self.received_rows += int(rows_in.size)
         for _, req in sends:
             req.wait()
@@ -430,10 +438,7 @@ class GpuEngine:
 
     def _blocks(self, R, rows):
         import torch
-        hp = self.sl.pattern(R)
-        idx = np.concatenate([np.arange(hp.ptr[l], hp.ptr[l + 1]) for l in rows]) if len(rows) else \
-            np.zeros(0, dtype=np.int64)
-        return torch.from_numpy(idx.astype(np.int64)).cuda()
+        return torch.from_numpy(row_blocks(self.sl.pattern(R).ptr, rows)).cuda()
 
     def get_rows(self, X, rows):
         return X.data.view(-1, self.b, self.b)[self._blocks(X.R, rows)].cpu().numpy()

@@ -99,8 +99,7 @@ class OracleEngine:
         return float(np.sum(X.data.val[p] * Y.data.val[p]))
 
     def _idx(self, R, rows):
-        hp = self.sl.pattern(R)
-        return np.concatenate([np.arange(hp.ptr[l], hp.ptr[l + 1]) for l in rows]).astype(np.int64)
+        return SP.row_blocks(self.sl.pattern(R).ptr, rows)
 
     def get_rows(self, X, rows):
         return X.data.val[self._idx(X.R, rows)]
@@ -122,7 +121,7 @@ class DroppingSlabs(SP.Slabs):
 
 def _owned_global(sl, X_host, R):
     hp = sl.pattern(R)
-    p = np.concatenate([np.arange(hp.ptr[l], hp.ptr[l + 1]) for l in sl.own]).astype(np.int64)
+    p = SP.row_blocks(hp.ptr, sl.own)
     return hp.gpos[p], X_host[p]
 
 
@@ -258,6 +257,15 @@ def test_lnv_ranges_are_the_product_sums():
     for want in (2.6, 4.0, 6.6, 10.6, 9.2, 13.2):
         assert min(abs(v - want) for v in r) < 1e-12
     assert len(r) == 6
+
+
+def test_row_blocks_and_reach():
+    ptr = np.array([0, 2, 2, 5, 6])
+    col = np.array([1, 3, 0, 2, 3, 1])
+    assert list(SP.row_blocks(ptr, [2, 0, 1, 3])) == [2, 3, 4, 0, 1, 5]
+    assert list(SP.row_blocks(ptr, [])) == []
+    assert list(SP.reach(ptr, col, [0, 3])) == [1, 3]
+    assert list(SP.reach(ptr, col, [1])) == []
 
 
 def test_cubic_step_closed_forms():
