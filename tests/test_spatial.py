@@ -163,7 +163,7 @@ def _free_port():
 
 
 def _run(world, L2, L0, drop=False):
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), L2, L0, out, drop), nprocs=world, join=True)
         return dict(out)
@@ -327,7 +327,7 @@ def test_gpu_engine_two_gloo_ranks_match_single_process(ref):
     """The library's FP64 products as each rank's engine (both ranks on cuda:0: their
     kernels never wait on one another; the halo rows travel through gloo on the host)."""
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_gpu_rank, args=(world, _free_port(), ref["L2"], ref["L0"], out), nprocs=world, join=True)
         res = dict(out)
