@@ -10,13 +10,15 @@ with FP32 accumulation (per product the faster of those and the FP32 FMA
 schedules, timed by the first steps), float32 storage, float64 traces and
 CG.  Beside it: FP32-FMA-only mixed steps, the float64 path, the runs to
 |dOmega|/N < 1e-6 Ha/atom with their time to solution, the dominant
-product's tensor-core and FMA rooflines against measured peaks, an
-end-to-end number through the public API with host buffers, and the CPU
-oracle timed on a row sample of the same workload.
+product's tensor-core and FMA rooflines against measured peaks, the
+end-to-end number through the public API with host buffers (the call the
+device-timed value makes, with its copies; and the same call with the
+float64 evaluation of the result), and the CPU oracle timed on a row
+sample of the same workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch     # 48 independent systems, 4x4 and 13x13 blocks
-  python bench.py --workload sizes     # ms/step against atoms, 512 ... 32768 (O(N))
+  python bench.py --workload sizes     # ms/step against atoms, 512 ... 32768 by default (O(N))
   python bench.py --workload oracle    # the CPU oracle on this host's cores (no GPU)
 
 With N > 1 (torchrun) every rank runs an independent replica of the
