@@ -1,11 +1,12 @@
-"""Spatial decomposition of the LNV minimisation over ranks: slabs of atoms, halo rows.
+"""Spatial decomposition of the LNV minimisation over ranks: regions of atoms, halo rows.
 
 Sec. 4.2 of the paper spreads the matrix work over processes by space: each process
 owns the atoms of a region, and each product stays O(N) because a block of the result
 needs only blocks of atoms within the product's reach (Sec. 2.3.2).  Here the cell is
-cut into slabs along one axis and rank r owns the block rows of the atoms in slab r.
+cut into slabs along one axis, or into a px x py x pz grid of boxes, and rank r owns the
+block rows of the atoms in region r.
 
-Each rank holds its atoms and every atom within `depth` of its slab (the largest range
+Each rank holds its atoms and every atom within `depth` of its region (the largest range
 of any matrix in the step), in global order, with the global range patterns restricted
 to them.  A matrix is valid on the owned rows.  Before a product C = A.B the rank fetches
 from their owners the rows of B that its rows of A reach: the halo rows.  The rows of
@@ -22,26 +23,51 @@ and only the owned rows are read.
 import numpy as np
 
 
+def grid_owners(pos, cell, grid):
+    """Owner rank of each atom on a px x py x pz grid of boxes of the orthorhombic cell:
+    rank (ix py + iy) pz + iz, with i_a = floor(p_a x_a / L_a) of the wrapped coordinate."""
+    pos = np.asarray(pos, dtype=np.float64)
+    idx = []
+    for a in range(3):
+        f = np.mod(pos[:, a] / float(cell[a]), 1.0)
+        idx.append(np.minimum((f * grid[a]).astype(np.int64), int(grid[a]) - 1))
+    return (idx[0] * int(grid[1]) + idx[1]) * int(grid[2]) + idx[2]
+
+
+def grid_held_atoms(pos, cell, owners, rank, grid, depth):
+    """Global ids (ascending) of the atoms rank `rank` holds: its own, and every atom whose
+    coordinate along each axis lies within `depth` of the rank's box (periodic).  Any atom
+    within distance depth of an owned atom is among them."""
+    pos = np.asarray(pos, dtype=np.float64)
+    box = (rank // (grid[1] * grid[2]), (rank // grid[2]) % grid[1], rank % grid[2])
+    near = np.ones(pos.shape[0], dtype=bool)
+    for a in range(3):
+        L = float(cell[a])
+        x = np.mod(pos[:, a], L)
+        lo, hi = box[a] * L / grid[a], (box[a] + 1) * L / grid[a]
+        inside = np.mod(x - lo, L) < hi - lo
+        d = np.minimum(np.mod(lo - x, L), np.mod(x - hi, L))   # below and above the box
+        near &= inside | (d <= depth + 1e-9 * L)
+    held = near | (np.asarray(owners) == rank)
+    return np.nonzero(held)[0].astype(np.int64)
+
+
+def _slab_grid(nranks, axis):
+    g = [1, 1, 1]
+    g[axis] = int(nranks)
+    return tuple(g)
+
+
 def slab_owners(pos, cell, nranks, axis=0):
     """Owner rank of each atom: slab floor(nranks x / L) of its coordinate x along the
     axis of the orthorhombic cell (x wrapped into [0, L))."""
-    pos = np.asarray(pos, dtype=np.float64)
-    f = np.mod(pos[:, axis] / float(cell[axis]), 1.0)
-    return np.minimum((f * nranks).astype(np.int64), nranks - 1)
+    return grid_owners(pos, cell, _slab_grid(nranks, axis))
 
 
 def slab_held_atoms(pos, cell, owners, rank, nranks, depth, axis=0):
     """Global ids (ascending) of the atoms rank `rank` holds: its own, and every atom whose
-    periodic distance along the axis from the slab is at most `depth`.  Any atom within
-    distance depth of an owned atom is among them."""
-    L = float(cell[axis])
-    x = np.mod(np.asarray(pos, dtype=np.float64)[:, axis], L)
-    lo, hi = rank * L / nranks, (rank + 1) * L / nranks
-    d_lo = np.mod(lo - x, L)          # distance below the slab
-    d_hi = np.mod(x - hi, L)          # distance above it
-    near = np.minimum(d_lo, d_hi) <= depth + 1e-9 * L
-    held = near | (np.asarray(owners) == rank)
-    return np.nonzero(held)[0].astype(np.int64)
+    periodic distance along the axis from the slab is at most `depth`."""
+    return grid_held_atoms(pos, cell, owners, rank, _slab_grid(nranks, axis), depth)
 
 
 def row_blocks(ptr, rows):
@@ -121,18 +147,22 @@ class Slabs:
 
     pos, cell: the whole system (orthorhombic cell); patterns: {R: (ptr, col)}, the global
     range patterns of every range in `ranges` (CSR, columns ascending); b: block size.
-    Rank `rank` owns the atoms of slab `rank` and holds every atom within the largest
-    range of its slab.  `sent_rows` and `received_rows` count the block rows exchanged.
+    Rank `rank` owns the atoms of slab `rank` along `axis` or, with grid = (px, py, pz),
+    of box `rank` of that grid, and holds every atom within the largest range of its
+    region.  `sent_rows` and `received_rows` count the block rows exchanged.
     """
 
-    def __init__(self, pos, cell, nranks, rank, patterns, b, axis=0, group=None):
+    def __init__(self, pos, cell, nranks, rank, patterns, b, axis=0, group=None, grid=None):
         self.nranks, self.rank, self.group, self.b = int(nranks), int(rank), group, int(b)
         self.cell = np.asarray(cell, dtype=np.float64)
         self.ranges = sorted(float(r) for r in patterns)
         self.depth = max(self.ranges)
         n = np.asarray(pos).shape[0]
-        self.owners = slab_owners(pos, cell, nranks, axis)
-        self.held = slab_held_atoms(pos, cell, self.owners, rank, nranks, self.depth, axis)
+        self.grid = _slab_grid(nranks, axis) if grid is None else tuple(int(v) for v in grid)
+        if int(np.prod(self.grid)) != self.nranks:
+            raise ValueError("the grid's boxes must number the ranks")
+        self.owners = grid_owners(pos, cell, self.grid)
+        self.held = grid_held_atoms(pos, cell, self.owners, rank, self.grid, self.depth)
         self.g2l = np.full(n, -1, dtype=np.int64)
         self.g2l[self.held] = np.arange(self.held.size)
         self.pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64)[self.held])

@@ -27,8 +27,11 @@ SHAPE = (16, 2, 2)        # conventional cells; slabs cut along the long x axis
 B = 4
 
 
-def _geometry():
-    return diamond_si_positions(SHAPE, 0.05, config_seed(0) + 40)
+GRID_SHAPE = (12, 12, 2)   # for a 2 x 2 x 1 grid of boxes
+
+
+def _geometry(shape=SHAPE):
+    return diamond_si_positions(shape, 0.05, config_seed(0) + 40)
 
 
 def _patterns(pos, cell):
@@ -125,17 +128,17 @@ def _owned_global(sl, X_host, R):
     return hp.gpos[p], X_host[p]
 
 
-def _rank(rank, world, port, L2g, L0g, out, drop):
+def _rank(rank, world, port, L2g, L0g, out, drop, shape=SHAPE, grid=None, cg_steps=3):
     import datetime
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
     try:
-        pos, cell = _geometry()
+        pos, cell = _geometry(shape)
         pats = _patterns(pos, cell)
         _, H, S = _inputs(pos, cell, pats)
         cls = DroppingSlabs if drop else SP.Slabs
-        sl = cls(pos, cell, world, rank, {R: (p.ptr, p.col) for R, p in pats.items()}, B)
+        sl = cls(pos, cell, world, rank, {R: (p.ptr, p.col) for R, p in pats.items()}, B, grid=grid)
         en = OracleEngine(sl)
         dl = SP.DistributedLnv(sl, en, SP.Mat(R_S, en.from_global(R_S, S), complete=True),
                                SP.Mat(R_H, en.from_global(R_H, H), complete=True), R_L, MU)
@@ -147,7 +150,7 @@ def _rank(rank, world, port, L2g, L0g, out, drop):
             D = SP.Mat(R_L, en.lincomb([(-1.0, G)], R_L))
             res["c"] = dl.cubic(L2, D, G)
             res["gpos"], res["gval"] = _owned_global(sl, en.to_host(G), R_L)
-            L3, hist = dl.minimise(SP.Mat(R_L, en._poison(en.from_global(R_L, L0g))), 3)
+            L3, hist = dl.minimise(SP.Mat(R_L, en._poison(en.from_global(R_L, L0g))), cg_steps)
             res["lpos"], res["lval"] = _owned_global(sl, en.to_host(L3), R_L)
             res["hist"] = hist
             res["sent"], res["received"] = sl.sent_rows, sl.received_rows
@@ -162,18 +165,16 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _run(world, L2, L0, drop=False):
+def _run(world, L2, L0, drop=False, shape=SHAPE, grid=None, cg_steps=3):
     with mp.get_context("spawn").Manager() as m:
         out = m.dict()
-        mp.spawn(_rank, args=(world, _free_port(), L2, L0, out, drop), nprocs=world, join=True)
+        mp.spawn(_rank, args=(world, _free_port(), L2, L0, out, drop, shape, grid, cg_steps), nprocs=world,
+                 join=True)
         return dict(out)
 
 
-@pytest.fixture(scope="module")
-def ref():
-    """The single-process oracle: L after 2 CG steps, its Omega, N_e, symmetric gradient
-    and cubic along -G, and 3 CG steps from the on-site start."""
-    pos, cell = _geometry()
+def _reference(shape, cg_steps):
+    pos, cell = _geometry(shape)
     m = OL.System(pos, cell)
     pH = m.pattern(R_H)
     H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
@@ -184,8 +185,21 @@ def ref():
     G = lnv.gradient(L2)
     G = 0.5 * (G + oracle.transpose(G, G.pat))
     c = lnv.cubic(L2, -1.0 * G, G)
-    L3, hist = OL.minimise(lnv, L0, 3)
+    L3, hist = OL.minimise(lnv, L0, cg_steps)
     return dict(n=pos.shape[0], L0=L0.val, L2=L2.val, omega=om, ne=ne, G=G.val, c=c, L3=L3.val, hist=hist)
+
+
+@pytest.fixture(scope="module")
+def ref():
+    """The single-process oracle: L after 2 CG steps, its Omega, N_e, symmetric gradient
+    and cubic along -G, and 3 CG steps from the on-site start."""
+    return _reference(SHAPE, 3)
+
+
+@pytest.fixture(scope="module")
+def ref_grid():
+    """The same on the 12 x 12 x 2-cell box, with 2 CG steps from the on-site start."""
+    return _reference(GRID_SHAPE, 2)
 
 
 def _check(ref, res, world):
@@ -216,6 +230,14 @@ def test_gloo_ranks_match_single_process(ref, world):
     _check(ref, res, world)
     # the halo does not cover the whole box: rows beyond it are never held
     assert all(r["n_held"] < ref["n"] for r in res.values())
+
+
+def test_gloo_box_grid_matches_single_process(ref_grid):
+    """Four ranks on a 2 x 2 x 1 grid of boxes: each holds the atoms within the depth of its
+    box along x and along y, fewer than the whole; same bar as the slabs."""
+    res = _run(4, ref_grid["L2"], ref_grid["L0"], shape=GRID_SHAPE, grid=(2, 2, 1), cg_steps=2)
+    _check(ref_grid, res, 4)
+    assert all(r["n_held"] < 0.9 * ref_grid["n"] for r in res.values())
 
 
 def test_forgotten_halo_row_poisons_the_energy(ref):
@@ -249,6 +271,30 @@ def test_slabs_partition_and_held_atoms_cover_every_reach():
         assert np.all(seen == 1)
         if world == 1:
             assert sl.held.size == n
+
+
+def test_box_grid_partition_and_held_atoms_cover_every_reach():
+    pos, cell = _geometry(GRID_SHAPE)
+    pats = _patterns(pos, cell)
+    gp = {R: (p.ptr, p.col) for R, p in pats.items()}
+    deep = pats[max(pats)]
+    n = pos.shape[0]
+    for grid in ((2, 2, 1), (1, 3, 1), (3, 1, 2)):
+        world = grid[0] * grid[1] * grid[2]
+        seen = np.zeros(n, dtype=np.int64)
+        for rank in range(world):
+            sl = SP.Slabs(pos, cell, world, rank, gp, B, grid=grid)
+            g_own = sl.held[sl.own]
+            seen[g_own] += 1
+            box = (rank // (grid[1] * grid[2]), (rank // grid[2]) % grid[1], rank % grid[2])
+            for a in range(3):
+                x = np.mod(pos[g_own, a], cell[a])
+                assert np.all(x >= box[a] * cell[a] / grid[a] - 1e-9)
+                assert np.all(x <= (box[a] + 1) * cell[a] / grid[a] + 1e-9)
+            assert np.all(sl.g2l[SP.reach(deep.ptr, deep.col, g_own)] >= 0)
+        assert np.all(seen == 1)
+    with pytest.raises(ValueError):
+        SP.Slabs(pos, cell, 3, 0, gp, B, grid=(2, 2, 1))
 
 
 def test_lnv_ranges_are_the_product_sums():
