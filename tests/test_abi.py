@@ -90,3 +90,39 @@ def test_binding_rejects_wrong_sizes_without_gpu():
     with pytest.raises(lsq.LsqError) as e:
         lsq.transpose(FakeGeom(), 13, torch.zeros(10 * 169), 0, torch.zeros(7 * 16), 1)
     assert e.value.code == 1
+
+
+def _prototypes():
+    """{name: [parameter kind]} of every entry point of include/*.h: 'ptr', 'int', 'i64',
+    'size' or 'double' (the opaque handles lsq_geom and lsq_lnv are pointers)."""
+    out = {}
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+        for name, params in re.findall(r"^int\s+(lsq_\w+)\s*\(([^;]*?)\)\s*;", txt, flags=re.M | re.S):
+            kinds = []
+            for p in [q.strip() for q in params.split(",")]:
+                if p in ("", "void"):
+                    continue
+                words = p.replace("const ", "").split()
+                if "*" in p or words[0] in ("lsq_geom", "lsq_lnv"):
+                    kinds.append("ptr")
+                else:
+                    kinds.append({"int": "int", "int64_t": "i64", "size_t": "size", "double": "double"}[words[0]])
+            out[name] = kinds
+    return out
+
+
+def test_binding_argtypes_match_the_header(lib):
+    """Every ctypes signature the binding sets has the header's parameter count and kinds, so no
+    argument is passed with the wrong width."""
+    kind = {ctypes.c_void_p: "ptr", ctypes.c_char_p: "ptr", ctypes.c_int: "int", ctypes.c_int64: "i64",
+            ctypes.c_size_t: "size", ctypes.c_double: "double"}
+    L = lsq.load()
+    protos = _prototypes()
+    assert set(protos) == _declared()
+    for name, params in protos.items():
+        got = [kind[t] for t in getattr(L, name).argtypes]
+        assert got == params, name
