@@ -76,8 +76,8 @@ int lsq_launch_count(int64_t *out_host);
 /*
  * Builds, on the GPU, the range pattern of every requested range: all
  * ordered atom pairs (i, j), self pairs included, whose minimum-image
- * distance satisfies d^2 <= R^2 (the paper zeroes elements with R_ij
- * greater than the cutoff).  d = r_j - r_i, each component folded as
+ * distance satisfies d^2 <= R^2 (Sec. 2.3.2: a matrix's range is set by the
+ * interatomic distance, and elements with R_ij beyond the cutoff are zero).  d = r_j - r_i, each component folded as
  * s - L rint(s / L), d^2 = (dx dx + dy dy) + dz dz, every operation
  * correctly rounded and none fused, so the set is reproducible bit for
  * bit on any IEEE host.
@@ -115,7 +115,8 @@ int lsq_geom_concat(int n_sys, const lsq_geom *geoms, lsq_geom *out, void *strea
 int lsq_geom_systems(lsq_geom g, int *n_sys, int64_t *atom_off_host);
 
 /*
- * Device views of pattern range_id: row_ptr_dev [n_atoms+1] int64,
+ * Device views of pattern range_id (the stored pairs of a range, Sec. 2.3.2):
+ * row_ptr_dev [n_atoms+1] int64,
  * col_dev [nnzb] int32 (sorted ascending within a row).  Owned by the
  * geometry; valid until lsq_geom_destroy.  nnzb is returned on the host.
  */
@@ -230,7 +231,8 @@ int lsq_transpose(lsq_geom g, int b, int precision, int range_x, const void *X_d
                   int range_out, void *out_dev, double alpha, void *stream);
 
 /* Tr[X Y] = sum over stored (i, j) of X, with (j, i) stored in Y, of
- * <X_ij, (Y_ji)^T>, accumulated in float64.  Synchronises the stream. */
+ * <X_ij, (Y_ji)^T>, accumulated in float64 (the traces of Sec. 2.3.2's band
+ * energy and electron count).  Synchronises the stream. */
 int lsq_trace(lsq_geom g, int b, int precision, int range_x, const void *X_dev,
               int range_y, const void *Y_dev, double *out_host, void *stream);
 
@@ -265,7 +267,7 @@ int lsq_trace_static(lsq_geom g, int b, int precision, int range_x, const void *
 
 /*
  * Approximate sparse inverse of the overlap S by the Hotelling iteration,
- * the metric the paper's LNV minimisation uses:
+ * the metric the paper's LNV minimisation uses (Sec. 2.3.2, after Eq. 8):
  *     X_{n+1} = 2 X_n - (X_n S) X_n,
  * with X S formed on pattern range_xs (which must cover the natural range
  * R_X + R_S, else LSQ_ERR_INVALID_ARG) and X S X restricted to range_x.
@@ -320,14 +322,16 @@ typedef struct {
 int lsq_lnv_default_opts(lsq_lnv_opts *opts);
 
 /*
- * The ranges an LNV context needs in its geometry, in this order:
+ * The ranges an LNV context needs in its geometry (a product of ranges R_A
+ * and R_B reaches R_A + R_B, Sec. 2.3.2), in this order:
  * R_S, R_H, R_L, R_L + R_S (LS), R_L + R_S + R_L (LSL), R_H + R_L + R_S
  * (H'LS), each computed in float64 exactly as written.  out_host[6].
  */
 int lsq_lnv_required_ranges(double R_S, double R_H, double R_L, double *out_host);
 
 /*
- * Creates an LNV context (workspace for all products of one CG step) on
+ * Creates an LNV context (workspace for all products of one CG step of the
+ * LNV minimisation, Sec. 2.3.2) on
  * geometry g, whose ranges must include lsq_lnv_required_ranges(...)
  * (looked up by exact value).  Requires R_S <= R_H.  b: orbitals per atom.
  * Allocates the small, fixed part of the workspace.  The product buffers (LS,
@@ -344,11 +348,11 @@ int lsq_lnv_create(lsq_geom g, int b, double R_S, double R_H, double R_L, lsq_ln
 int lsq_lnv_destroy(lsq_lnv ctx);
 
 /* Initial L = 1/2 (S_ii)^-1 on the diagonal blocks, zero elsewhere
- * (symmetrised).  S_dev on R_S's pattern, L_dev on R_L's, float64. */
+ * (symmetrised): a start for the minimisation of Sec. 2.3.2, which gives none.  S_dev on R_S's pattern, L_dev on R_L's, float64. */
 int lsq_lnv_init_L(lsq_lnv ctx, const double *S_dev, double *L_dev, void *stream);
 
 /*
- * Omega = spin Tr[K (H - mu S)], N_e = spin Tr[K S], K = 3LSL - 2LSLSL on
+ * Omega = spin Tr[K (H - mu S)], N_e = spin Tr[K S], K = 3LSL - 2LSLSL (Eq. 8) on
  * H's range, and G_ab = dOmega/dL_ab on L's range (symmetrised), for
  * float64 L_dev (R_L), S_dev (R_S), H_dev (R_H).  precision LSQ_F64 or
  * LSQ_F32 (products in FP32, traces accumulated in float64).  G_dev may
@@ -416,9 +420,9 @@ int lsq_lnv_init_purify(lsq_lnv ctx, const double *S_dev, const double *H_dev, d
 int lsq_lnv_set_metric(lsq_lnv ctx, int range_x, const double *X_dev, int range_xg, void *stream);
 
 /*
- * Conjugate-gradient minimisation of Omega over symmetric L on L's range:
- * Polak-Ribiere direction (beta = max(0, beta_PR)) restarted every
- * cg_reset steps, exact line minimisation of the cubic Omega(L + a D).
+ * Conjugate-gradient minimisation of Omega over symmetric L on L's range
+ * (Sec. 2.3.2): Polak-Ribiere direction (beta = max(0, beta_PR)) restarted
+ * every cg_reset steps (40 in the convergence figure of Sec. 5.3), exact line minimisation of the cubic Omega(L + a D).
  * L_dev (float64, R_L) holds the start on entry and the result on exit.
  * Returns LSQ_OK when converged (or max_iter steps were taken with
  * tol = 0), LSQ_ERR_NOT_CONVERGED, or LSQ_ERR_UNSTABLE; rep (optional)
@@ -428,7 +432,7 @@ int lsq_lnv_minimise(lsq_lnv ctx, double *L_dev, const double *S_dev, const doub
                      double mu, const lsq_lnv_opts *opts, lsq_lnv_report *rep, void *stream);
 
 /*
- * The same minimisation for every system of a geometry made by
+ * The same minimisation (Sec. 2.3.2) for every system of a geometry made by
  * lsq_geom_concat, all systems at once: each CG step is one sequence of
  * launches over all systems, with each system's Omega, beta, line
  * coefficients and step length reduced and computed on the device, so no
