@@ -1,7 +1,8 @@
 """The spatial decomposition of the LNV step over gloo ranks on CPU (Sec. 4.2).
 
-Each rank owns a slab of an elongated Si box, holds the atoms within the halo depth of
-it, and runs the distributed energy, gradient, line-search cubic and CG of
+Each rank owns a slab of an elongated Si box (or a box of a 2 x 2 x 1 grid over a
+wider one), holds the atoms within the halo depth of it, and runs the distributed
+energy, gradient, line-search cubic and CG of
 paper_2002_07704_gb300.spatial with the oracle's block algebra as its engine.  That
 engine computes the owned rows only and fills every other row of each result with NaN,
 so a halo row that the decomposition forgot to fetch poisons the answer.  The results
