@@ -23,6 +23,7 @@ from synth import config_seed, diamond_si_positions, sk_blocks
 
 R_S = R_H = 2.6           # first neighbour shell of Si (2.35 A)
 R_L = 4.0                 # second shell (3.84 A)
+RANGES = (R_S, R_H, R_L)
 MU = -2.0
 SHAPE = (16, 2, 2)        # conventional cells; slabs cut along the long x axis
 B = 4
@@ -35,13 +36,15 @@ def _geometry(shape=SHAPE):
     return diamond_si_positions(shape, 0.05, config_seed(0) + 40)
 
 
-def _patterns(pos, cell):
-    return {R: oracle.neighbour_list(pos, cell, R) for R in SP.lnv_ranges(R_S, R_H, R_L)}
+def _patterns(pos, cell, rg=RANGES):
+    return {R: oracle.neighbour_list(pos, cell, R) for R in SP.lnv_ranges(*rg)}
 
 
-def _inputs(pos, cell, pats):
-    pH = pats[SP.lnv_ranges(R_S, R_H, R_L)[0]]
-    H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
+def _inputs(pos, cell, pats, rg=RANGES):
+    """H on R_H's pattern and S on R_S's (the model's blocks of each listed pair)."""
+    pS, pH = pats[rg[0]], pats[rg[1]]
+    H, _ = sk_blocks(pos, cell, pH.rows(), pH.col)
+    _, S = sk_blocks(pos, cell, pS.rows(), pS.col)
     return pH, H, S
 
 
@@ -129,15 +132,16 @@ def _owned_global(sl, X_host, R):
     return hp.gpos[p], X_host[p]
 
 
-def _rank(rank, world, port, L2g, L0g, out, drop, shape=SHAPE, grid=None, cg_steps=3):
+def _rank(rank, world, port, L2g, L0g, out, drop, shape=SHAPE, grid=None, cg_steps=3, rg=RANGES):
     import datetime
+    R_S, R_H, R_L = rg
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
     try:
         pos, cell = _geometry(shape)
-        pats = _patterns(pos, cell)
-        _, H, S = _inputs(pos, cell, pats)
+        pats = _patterns(pos, cell, rg)
+        _, H, S = _inputs(pos, cell, pats, rg)
         cls = DroppingSlabs if drop else SP.Slabs
         sl = cls(pos, cell, world, rank, {R: (p.ptr, p.col) for R, p in pats.items()}, B, grid=grid)
         en = OracleEngine(sl)
@@ -166,20 +170,23 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _run(world, L2, L0, drop=False, shape=SHAPE, grid=None, cg_steps=3):
+def _run(world, L2, L0, drop=False, shape=SHAPE, grid=None, cg_steps=3, rg=RANGES):
     with mp.get_context("spawn").Manager() as m:
         out = m.dict()
-        mp.spawn(_rank, args=(world, _free_port(), L2, L0, out, drop, shape, grid, cg_steps), nprocs=world,
-                 join=True)
+        mp.spawn(_rank, args=(world, _free_port(), L2, L0, out, drop, shape, grid, cg_steps, rg),
+                 nprocs=world, join=True)
         return dict(out)
 
 
-def _reference(shape, cg_steps):
+def _reference(shape, cg_steps, rg=RANGES):
+    R_S, R_H, R_L = rg
     pos, cell = _geometry(shape)
     m = OL.System(pos, cell)
-    pH = m.pattern(R_H)
-    H, S = sk_blocks(pos, cell, pH.rows(), pH.col)
-    lnv = OL.Lnv(m, oracle.Bsr(pH, B, S), oracle.Bsr(pH, B, H), R_L, MU)
+    pS, pH = m.pattern(R_S), m.pattern(R_H)
+    H, _ = sk_blocks(pos, cell, pH.rows(), pH.col)
+    _, S = sk_blocks(pos, cell, pS.rows(), pS.col)
+    # the oracle holds S on H's pattern: zero blocks where R_S < R_ij <= R_H
+    lnv = OL.Lnv(m, oracle.Bsr(pS, B, S), oracle.Bsr(pH, B, H), R_L, MU)
     L0 = OL.onsite_inverse_half(lnv.S, lnv.pat_L)
     L2, _ = OL.minimise(lnv, L0, 2)
     om, ne = lnv.energy(L2)
@@ -195,6 +202,12 @@ def ref():
     """The single-process oracle: L after 2 CG steps, its Omega, N_e, symmetric gradient
     and cubic along -G, and 3 CG steps from the on-site start."""
     return _reference(SHAPE, 3)
+
+
+@pytest.fixture(scope="module")
+def ref_short_s():
+    """The same with S on a shorter range than H: R_S = 2.6 A, R_H = R_L = 4.0 A."""
+    return _reference(SHAPE, 2, (2.6, 4.0, 4.0))
 
 
 @pytest.fixture(scope="module")
@@ -239,6 +252,12 @@ def test_gloo_box_grid_matches_single_process(ref_grid):
     res = _run(4, ref_grid["L2"], ref_grid["L0"], shape=GRID_SHAPE, grid=(2, 2, 1), cg_steps=2)
     _check(ref_grid, res, 4)
     assert all(r["n_held"] < 0.9 * ref_grid["n"] for r in res.values())
+
+
+def test_gloo_ranks_with_s_shorter_than_h(ref_short_s):
+    """R_S < R_H: S and H on their own ranges, H' = H - mu S on H's; same bar."""
+    res = _run(2, ref_short_s["L2"], ref_short_s["L0"], cg_steps=2, rg=(2.6, 4.0, 4.0))
+    _check(ref_short_s, res, 2)
 
 
 def test_forgotten_halo_row_poisons_the_energy(ref):
